@@ -1,0 +1,332 @@
+#!/usr/bin/env python3
+"""Benchmark of the road-stereo hot path on GB300.
+
+One step = the whole hot path on one 1920 x 1080 stereo pair, D = 128, w = 9, k = 11:
+perspective warp (§3.1) -> fused cost + bilateral aggregation + WTA + sub-pixel
+(eq. c, eq. fbs, eq. subpixel) -> disparity transformation (§3.3), inputs resident in
+device memory.  L2 is flushed (a 256 MiB write) before every timed step, outside its
+events.  Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+instead, on bounded row bands of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gpix·disp/s of cost+bilateral+WTA and stereo pairs/s at 1080p, D=128, vs plain FP32"
+UNIT = "Gpix*disp/s"
+WORKLOAD = "road-stereo 1920x1080 D=128 w=9 k=11 sigma0=3 sigma1=10, warp + fused cost/agg/WTA + DT"
+SM_COUNT_GB300 = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+# DRAM traffic of one fused-kernel launch on this workload, from the ncu capture summarised
+# in profiles/ (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the kernel
+# source with this SHA-256 prefix.
+FUSED_TRAFFIC = {"sha256": None, "bytes": None}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def kernel_sha():
+    p = os.path.join(ROOT, "paper_1904_06017_gb300", "csrc", "k_fused.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_inputs():
+    import synth
+    s = synth.make_config_scene("hd")
+    return s
+
+
+def cpu_baseline_sample(s, seconds):
+    """The oracle on a bounded band of rows of the same pair, on all host cores."""
+    import numpy as np
+    import oracle
+    p = s.params
+    H, W, D = s.height, s.width, p["D"]
+    tw = oracle.warp(s.tgt, s.shift)
+    rows = 8
+    v0 = H // 2 - rows // 2
+    t = time.perf_counter()
+    oracle.stereo(s.ref, tw, s.shift, D, p["win"], p["bil"], p["sigma0"], p["sigma1"], rows=(v0, v0 + rows))
+    dt8 = time.perf_counter() - t
+    rows = int(max(8, min(H - 2 * 16, round(rows * seconds / max(dt8, 1e-3)))))
+    v0 = max(0, H // 2 - rows // 2)
+    t = time.perf_counter()
+    oracle.stereo(s.ref, tw, s.shift, D, p["win"], p["bil"], p["sigma0"], p["sigma1"], rows=(v0, v0 + rows))
+    el = time.perf_counter() - t
+    val = rows * W * D / el / 1e9
+    return {"value": val, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": "rows %d..%d of the 1920x1080 D=128 pair (%d x %d x %d disparity evaluations), "
+                      "FP64 C oracle (cost, aggregation, WTA, sub-pixel), %.1f s" % (v0, v0 + rows, rows, W, D, el)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    from oracle import dt
+    oracle.build()
+    s = make_inputs()
+    p = s.params
+    H, W, D = s.height, s.width, p["D"]
+    rows = 16
+    times = []
+    for it in range(args.warmup + args.steps):
+        v0 = 16 + (it * 37) % (H - 32 - rows)
+        t = time.perf_counter()
+        tw = oracle.warp(s.tgt, s.shift)
+        disp, _, _, _ = oracle.stereo(s.ref, tw, s.shift, D, p["win"], p["bil"], p["sigma0"], p["sigma1"],
+                                      rows=(v0, v0 + rows))
+        uu, vv = np.meshgrid(np.arange(W, dtype=np.float64), np.arange(v0, v0 + rows, dtype=np.float64))
+        dt.estimate_roll(disp.ravel(), uu.ravel(), vv.ravel())
+        el = time.perf_counter() - t
+        if it >= args.warmup:
+            times.append(el)
+    tot = sum(times)
+    val = args.steps * rows * W * D / tot / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD + " (oracle on 16-row bands)",
+                                            "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+                             "sample": "per step: warp of the full target, then cost/aggregation/WTA/"
+                                       "sub-pixel on a 16-row band and the roll fit of that band"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_1904_06017_gb300 as sg
+    from paper_1904_06017_gb300 import build as sgbuild
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    sgbuild.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    s = make_inputs()
+    p = s.params
+    H, W, D, win, bil = s.height, s.width, p["D"], p["win"], p["bil"]
+    pitch = (W + 15) // 16 * 16
+
+    def img(a):
+        t = torch.zeros((H, pitch), dtype=torch.uint8)
+        t[:, :W] = torch.from_numpy(a)
+        return t
+
+    ref_h, tgt_h = img(s.ref).pin_memory(), img(s.tgt).pin_memory()
+    shift_h = torch.from_numpy(s.shift).pin_memory()
+    ref, tgt, shift = ref_h.to(dev), tgt_h.to(dev), shift_h.to(dev)
+    tw = torch.empty_like(tgt)
+    disp = torch.empty((H, W), dtype=torch.float32, device=dev)
+    valid = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    out = torch.empty_like(disp)
+    res = torch.zeros(64, dtype=torch.uint8, device=dev)
+    out_h = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    res_h = torch.empty(64, dtype=torch.uint8).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    st = sg.Stereo(W, H, D, win=win, bil=bil, sigma0=p["sigma0"], sigma1=p["sigma1"], pitch=pitch)
+    stream = torch.cuda.current_stream()
+    launches_per_step = 6   # k_warp, k_prep, k_fused, k_dt_moments, k_dt_solve, k_dt_apply
+
+    def step():
+        st.warp_target(tgt, shift, tw)
+        st.cost_aggregate_wta(ref, tw, shift, disp, None, valid)
+        st.disparity_transform(disp, valid, 0.0, 0.0, out, res=res)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    st.check_device_status()
+
+    # ---- device-resident timing, L2 flushed before each step (outside the events)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    sg.stereo_profile_enable(st.ctx, True)
+    barrier()
+    clocks.start()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    barrier()
+    clk = clocks.stop()
+    n_fused, fused_ms = sg.stereo_profile_read(st.ctx)
+    sg.stereo_profile_enable(st.ctx, False)
+    st.check_device_status()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_local = sum(step_ms)
+    t_max = t_local
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    units = world * args.steps * W * H * D
+    value = units / (t_max * 1e-3) / 1e9
+    pairs_per_s = world * args.steps / (t_max * 1e-3)
+
+    # ---- end to end through the public API: pinned host inputs in, transformed map out
+    e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        e_ev[i][0].record(stream)
+        ref.copy_(ref_h, non_blocking=True)
+        tgt.copy_(tgt_h, non_blocking=True)
+        shift.copy_(shift_h, non_blocking=True)
+        step()
+        out_h.copy_(out, non_blocking=True)
+        res_h.copy_(res, non_blocking=True)
+        e_ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    e_ms = sum(a.elapsed_time(b) for a, b in e_ev)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e_ms = float(tt.item())
+    e2e = {"value": world * args.steps * W * H * D / (e_ms * 1e-3) / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": 2 * H * pitch + 4 * H, "d2h_bytes_per_step": 4 * H * W + 64,
+           "pairs_per_s": world * args.steps / (e_ms * 1e-3)}
+    r = sg.stereo_dt_result.from_buffer_copy(res.cpu().numpy().tobytes()[:48])
+
+    if rank != 0:
+        st.close()
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the fused kernel: aggregation arithmetic, 2 k^2 flops per (pixel, d)
+    fused_avg_ms = fused_ms / max(n_fused, 1)
+    agg_flops = 2.0 * bil * bil * W * H * D
+    achieved = agg_flops / (fused_avg_ms * 1e-3) / 1e12
+    peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = FUSED_TRAFFIC["bytes"] if FUSED_TRAFFIC["sha256"] == kernel_sha() else None
+    probe_s, probe_p = sg.stereo_fp32_peak_probe(2)
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": "k_fused (cost + bilateral aggregation + WTA + sub-pixel)",
+            "flops_per_launch": agg_flops, "avg_launch_ms": fused_avg_ms, "launches": n_fused,
+            "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal, derived)",
+            "fp32_probe_tflops": {"scalar_fma": probe_s / 1e3, "packed_f32x2_fma": probe_p / 1e3},
+            "fused_gpix_disp_per_s": W * H * D / (fused_avg_ms * 1e-3) / 1e9}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "width": W, "height": H, "max_disp": D, "win": win, "bil": bil,
+                       "pairs_per_step_per_gpu": 1, "l2": "flushed before each step (256 MiB write, untimed)"},
+            "pairs_per_s": pairs_per_s, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+            "roofline": roof, "clocks": clk,
+            "dt": {"psi": r.psi, "alpha0": r.alpha0, "alpha1": r.alpha1, "iters": r.iters, "status": r.status,
+                   "true_roll": s.roll}}
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline_sample(s, args.cpu_seconds)
+    st.close()
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

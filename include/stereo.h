@@ -1,0 +1,199 @@
+/*
+ * stereo.h -- C ABI of the GB300 (sm_103a) road-stereo library.
+ *
+ * The library computes the data-parallel hot path of Fan et al., "Real-Time Dense
+ * Stereo Embedded in A UAV for Road Inspection" (arXiv 1904.06017):
+ *   1. the perspective transformation of the target image (§3.1, eq. relation_vd),
+ *   2. the matching cost c(p, d) of eq. (c),
+ *   3. the bilateral aggregation of eq. (omega_s) / eq. (fbs),
+ *   4. winner-take-all, the add-back of the row shift and the parabola step of
+ *      eq. (subpixel) (§3.2.2),
+ *   5. the disparity transformation of §3.3: roll angle (eq. e_min_gd,
+ *      eq. adaptive_lambda), line fit (eq. alpha3) and the per-pixel map of
+ *      eq. (disparity_transformation).
+ * Steps 2-4 run in one fused kernel; the cost volume never reaches device memory.
+ *
+ * Conventions shared by every call:
+ *   - Images are row-major uint8 (grey levels), width W, height H, row pitch in
+ *     bytes (a multiple of 16, >= W).  u is the column, v the row, origin top-left.
+ *   - Disparity maps are row-major float32 [H][W] (pitch W elements).
+ *   - Every pointer argument named *_dev is device memory the caller owns; the
+ *     library never frees or keeps it.  Host pointers are named *_host.
+ *   - Calls are asynchronous on the given stream (a cudaStream_t; NULL is the
+ *     legacy default stream) unless stated otherwise.
+ *   - Every call returns STEREO_OK (0) or a negative STEREO_E* code and never
+ *     aborts; stereo_last_error() then describes the failure (thread-local).
+ *   - Numeric readings where the paper is silent (rounding of the row shift,
+ *     clamp-to-edge reads, population statistics, sigma used without a factor 2,
+ *     out-of-image neighbours left out, lowest d wins a tie) follow the plain
+ *     definitions stated at each call.
+ */
+#ifndef STEREO_GB300_H
+#define STEREO_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define STEREO_OK 0
+#define STEREO_EINVAL (-1)    /* bad argument (null pointer, size, alignment, parameter) */
+#define STEREO_ENOMEM (-2)    /* device allocation failed */
+#define STEREO_ECUDA (-3)     /* a CUDA runtime / driver call failed */
+#define STEREO_ETIMEOUT (-4)  /* a kernel gave up a bounded wait (device status word) */
+#define STEREO_ENOCONV (-5)   /* the roll search hit max_iters before |dpsi| < delta_psi */
+#define STEREO_ENOTSUP (-6)   /* the configuration is not supported by the kernels */
+
+/* cost storage type inside the fused kernel (aggregation always accumulates in FP32) */
+#define STEREO_F32 0
+#define STEREO_F16 1
+#define STEREO_BF16 2
+
+typedef struct CUstream_st *stereo_stream_t;   /* same type as cudaStream_t */
+typedef struct stereo_ctx stereo_ctx;
+
+/* Problem parameters, fixed for the life of a context. */
+typedef struct {
+    int32_t width, height;   /* W, H in pixels; 1 <= W, H <= 16384 */
+    int32_t pitch;           /* bytes per image row; multiple of 16, >= width */
+    int32_t max_disp;        /* D: residual disparities 0..D-1 after the warp; 1..256 */
+    int32_t win;             /* NCC block size w (odd, 3..11): n = w*w in eq. (c) */
+    int32_t bil;             /* bilateral window k (odd, 1..15); 11 is the paper's
+                                120-connected neighbourhood (§4.4.1) */
+    float sigma0, sigma1;    /* eq. (omega_s), used exactly as printed (no factor 2) */
+    int32_t cost_dtype;      /* STEREO_F32 | STEREO_F16 | STEREO_BF16 */
+    double lambda0;          /* initial rate of eq. (e_min_gd); paper: 10 (§4.4.2) */
+    double delta_psi;        /* stop when |psi_k+1 - psi_k| < delta_psi; paper: pi/1.8e6 */
+    int32_t max_iters;       /* cap on the roll iterations (default 100) */
+} stereo_params;
+
+/* Result of the disparity transformation (§3.3).  alpha0 is in raw pixel
+ * coordinates, so the fitted road is alpha0 + alpha1 * (v cos psi - u sin psi). */
+typedef struct {
+    double psi;       /* roll angle in (-pi/2, pi/2], eq. (e_min_min) */
+    double alpha0;    /* eq. (alpha3) at psi */
+    double alpha1;
+    double e_min;     /* eq. (E_min2) at psi, summed over the fitted pixels */
+    int32_t iters;    /* roll iterations taken */
+    int32_t status;   /* STEREO_OK, STEREO_ENOCONV, or STEREO_EINVAL (< 2 pixels) */
+    int64_t n;        /* number of fitted pixels */
+} stereo_dt_result;
+
+/* Fill *p with the defaults: sigma0 = 1.5, sigma1 = 5.5, bil = 11 (§4.4.1),
+ * win = 9, lambda0 = 10, delta_psi = pi / 1.8e6 (§4.4.2), max_iters = 100,
+ * cost_dtype = STEREO_F32.  Sizes are left 0 for the caller to set. */
+int stereo_params_default(stereo_params *p);
+
+/* Validate *p and create a context on the current CUDA device.  The context owns
+ * padded image staging buffers, window statistics, tensor maps and the small
+ * scratch of the disparity transformation (all allocated here, none later).
+ * Errors: STEREO_EINVAL for bad parameters, STEREO_ENOMEM, STEREO_ECUDA. */
+int stereo_create(const stereo_params *p, stereo_ctx **out);
+
+/* Free a context and everything it owns (synchronises the device).  NULL is a no-op. */
+int stereo_destroy(stereo_ctx *ctx);
+
+/* §3.1, eq. (relation_vd): road disparity is affine in the row, du(v) = c0 + c1 v.
+ * Writes the row shift s(v) = c0 + c1 v - delta_p for v = 0..height-1 to host
+ * memory.  Pure host helper (no CUDA). */
+int stereo_row_shift_affine(int32_t height, double c0, double c1, double delta_p,
+                            float *shift_host_out);
+
+/* §3.1: perspective transformation of the target image.  Every point of target
+ * row v moves s_i(v) = floor(s(v) + 0.5) pixels to the right:
+ *     tgt_warped(u, v) = tgt(clamp(u - s_i(v), 0, W-1), v).
+ * tgt_dev, tgt_warped_dev: uint8 [H][pitch] (must not overlap); shift_dev: float [H].
+ * Bytes u >= W of each output row are left untouched. */
+int stereo_warp_target(stereo_ctx *ctx, const uint8_t *tgt_dev, const float *shift_dev,
+                       uint8_t *tgt_warped_dev, stereo_stream_t stream);
+
+/* §3.2: fused cost (eq. c) + bilateral aggregation (eq. fbs) + WTA + eq. (subpixel).
+ *   c(p,d)  = 1 - NCC of the w x w reference block at p and the warped-target block
+ *             at p - [d,0] (population statistics, clamp-to-edge reads; c = 1 when a
+ *             block has zero variance);
+ *   E(p,d)  = sum_q w(p,q) c(q,d) / sum_q w(p,q) over in-image q of the k x k window,
+ *             w(p,q) = exp(-|p-q|^2/sigma0^2 - (I_ref(p) - I_ref(q))^2/sigma1^2);
+ *   d*(p)   = lowest argmin_d E(p,d), d in [0, D);
+ *   disp(p) = d* + delta + s_i(v), delta per eq. (subpixel) on E (0 at d* in
+ *             {0, D-1} or when the denominator is not positive).
+ * ref_dev, tgt_warped_dev: uint8 [H][pitch]; shift_dev: float [H] (the shift used by
+ * the warp); disp_dev: float [H][W].  Optional (may be NULL): wta_dev int32 [H][W]
+ * receives d*; valid_dev uint8 [H][W] receives 1 where no read behind any disparity
+ * (block and bilateral window, radius m = w/2 + k/2) is clamped, in the reference,
+ * the warped target, or the original target behind the warp.
+ * The call launches a staging kernel (replicate padding and window statistics into
+ * the context's buffers) and the fused kernel; calls on one context must not overlap. */
+int stereo_cost_aggregate_wta(stereo_ctx *ctx, const uint8_t *ref_dev,
+                              const uint8_t *tgt_warped_dev, const float *shift_dev,
+                              float *disp_dev, int32_t *wta_dev, uint8_t *valid_dev,
+                              stereo_stream_t stream);
+
+/* §3.3: disparity transformation of a disparity map.
+ * Fits over the pixels with mask_dev != 0 (all pixels when mask_dev is NULL) and a
+ * finite disparity: 10 FP64 moments on the device, then the roll search of
+ * eq. (e_min_gd) with the rate of eq. (adaptive_lambda) from psi_init, with the
+ * rate applied to the energy per pixel, backtracking (a step that raises the
+ * energy is halved, at most 60 times), psi wrapped into (-pi/2, pi/2], stop at
+ * |dpsi| < delta_psi or max_iters; then alpha = J(psi) d (eq. alpha3) and
+ *     disp_out(p) = disp(p) - alpha0 + alpha1 (u sin psi - v cos psi) + delta_t
+ * (eq. disparity_transformation) for every pixel.
+ * disp_dev, disp_out_dev: float [H][W] (may be the same buffer); mask_dev: uint8 [H][W].
+ * res: a stereo_dt_result in device memory (the call stays asynchronous) or in
+ * host memory (the call synchronises the stream and copies it back); may be NULL.
+ * A non-converged search still transforms the map with the last iterate and
+ * reports status STEREO_ENOCONV in res; the call itself returns STEREO_OK. */
+int stereo_disparity_transform(stereo_ctx *ctx, const float *disp_dev, const uint8_t *mask_dev,
+                               double psi_init, float delta_t, float *disp_out_dev,
+                               stereo_dt_result *res, stereo_stream_t stream);
+
+/* ---------------------------------------------------------- unfused reference path
+ * The same arithmetic as stereo_cost_aggregate_wta, one stage per kernel, with the
+ * FP32 volumes in device memory (the "plain FP32" form, and a way to inspect
+ * costs and aggregated costs).  Volumes are float [H][W][D] (d fastest). */
+
+/* eq. (c) for every pixel and d in [0, D): cost_dev float [H][W][D]. */
+int stereo_cost_volume(stereo_ctx *ctx, const uint8_t *ref_dev, const uint8_t *tgt_warped_dev,
+                       float *cost_dev, stereo_stream_t stream);
+
+/* eq. (fbs) of a cost volume: agg_dev float [H][W][D] (must not alias cost_dev). */
+int stereo_aggregate_volume(stereo_ctx *ctx, const uint8_t *ref_dev, const float *cost_dev,
+                            float *agg_dev, stereo_stream_t stream);
+
+/* WTA + eq. (subpixel) on an aggregated volume.  disp_dev float [H][W]; optional
+ * wta_dev int32 [H][W] (d*) and best2_dev float [H][W][2] (E at d*, and the smallest
+ * E over d != d*). */
+int stereo_wta_volume(stereo_ctx *ctx, const float *agg_dev, const float *shift_dev,
+                      float *disp_dev, int32_t *wta_dev, float *best2_dev,
+                      stereo_stream_t stream);
+
+/* ---------------------------------------------------------------- diagnostics */
+
+/* Synchronise the stream, read and clear the context's device status word.
+ * Returns STEREO_OK, or STEREO_ETIMEOUT when a kernel gave up a bounded wait. */
+int stereo_check_device_status(stereo_ctx *ctx, stereo_stream_t stream);
+
+/* Timing of the fused kernel alone: when enabled (on != 0), every later
+ * stereo_cost_aggregate_wta records CUDA events on its stream around the fused
+ * launch (up to 4096 launches).  stereo_profile_read synchronises and returns the
+ * number of launches timed and their total milliseconds, then resets the log. */
+int stereo_profile_enable(stereo_ctx *ctx, int32_t on);
+int stereo_profile_read(stereo_ctx *ctx, int32_t *launches, double *total_ms);
+
+/* FP32 FMA throughput probe (a measurement aid): runs independent chains of scalar
+ * FMAs, then of packed f32x2 FMAs, on every SM (blocks_per_sm CTAs of 256 threads
+ * per SM) and returns the achieved GFLOP/s of each (2 flops per FMA lane).
+ * Synchronous on the legacy default stream. */
+int stereo_fp32_peak_probe(int32_t blocks_per_sm, double *gflops_scalar, double *gflops_packed);
+
+/* Description of the last error on this thread (never NULL). */
+const char *stereo_last_error(void);
+
+/* Library version string. */
+const char *stereo_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STEREO_GB300_H */

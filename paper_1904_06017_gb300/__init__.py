@@ -1,0 +1,282 @@
+"""GB300 (sm_103a) road-stereo library: Python binding of the C ABI in include/stereo.h.
+
+Thin marshalling only: every function has the name of the C entry point it calls,
+turns tensors into device pointers and streams into cudaStream_t handles, and raises
+``StereoError`` on a non-zero status.  All arithmetic runs in the CUDA kernels of
+``libstereo_gb300.so``; there is no CPU or PyTorch fallback, and importing a function
+that needs the library fails loudly when it has not been built.
+
+Hot path (Fan et al., arXiv 1904.06017): stereo_warp_target (§3.1) ->
+stereo_cost_aggregate_wta (eq. c, eq. fbs, WTA, eq. subpixel; §3.2) ->
+stereo_disparity_transform (§3.3).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+__all__ = [
+    "StereoError", "stereo_params", "stereo_dt_result", "load_library", "library_path",
+    "stereo_params_default", "stereo_create", "stereo_destroy", "stereo_row_shift_affine",
+    "stereo_warp_target", "stereo_cost_aggregate_wta", "stereo_disparity_transform",
+    "stereo_cost_volume", "stereo_aggregate_volume", "stereo_wta_volume",
+    "stereo_check_device_status", "stereo_profile_enable", "stereo_profile_read",
+    "stereo_fp32_peak_probe", "stereo_last_error", "stereo_version", "Stereo",
+    "STEREO_OK", "STEREO_EINVAL", "STEREO_ENOMEM", "STEREO_ECUDA", "STEREO_ETIMEOUT",
+    "STEREO_ENOCONV", "STEREO_ENOTSUP", "STEREO_F32", "STEREO_F16", "STEREO_BF16",
+]
+
+STEREO_OK = 0
+STEREO_EINVAL = -1
+STEREO_ENOMEM = -2
+STEREO_ECUDA = -3
+STEREO_ETIMEOUT = -4
+STEREO_ENOCONV = -5
+STEREO_ENOTSUP = -6
+STEREO_F32, STEREO_F16, STEREO_BF16 = 0, 1, 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_lib", "libstereo_gb300.so")
+_lib = None
+
+
+class StereoError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (status %d)" % (msg, code))
+        self.code = code
+
+
+class stereo_params(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("pitch", ctypes.c_int32),
+                ("max_disp", ctypes.c_int32), ("win", ctypes.c_int32), ("bil", ctypes.c_int32),
+                ("sigma0", ctypes.c_float), ("sigma1", ctypes.c_float),
+                ("cost_dtype", ctypes.c_int32), ("lambda0", ctypes.c_double),
+                ("delta_psi", ctypes.c_double), ("max_iters", ctypes.c_int32)]
+
+
+class stereo_dt_result(ctypes.Structure):
+    _fields_ = [("psi", ctypes.c_double), ("alpha0", ctypes.c_double), ("alpha1", ctypes.c_double),
+                ("e_min", ctypes.c_double), ("iters", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("n", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library():
+    """Load libstereo_gb300.so (build it first with ``paper_1904_06017_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError("libstereo_gb300.so is not built (%s); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`" % _LIB_PATH)
+    lib = ctypes.CDLL(_LIB_PATH)
+    P, I32, D, F = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_float
+    sigs = {
+        "stereo_params_default": [P],
+        "stereo_create": [P, P],
+        "stereo_destroy": [P],
+        "stereo_row_shift_affine": [I32, D, D, D, P],
+        "stereo_warp_target": [P, P, P, P, P],
+        "stereo_cost_aggregate_wta": [P, P, P, P, P, P, P, P],
+        "stereo_disparity_transform": [P, P, P, D, F, P, P, P],
+        "stereo_cost_volume": [P, P, P, P, P],
+        "stereo_aggregate_volume": [P, P, P, P, P],
+        "stereo_wta_volume": [P, P, P, P, P, P, P],
+        "stereo_check_device_status": [P, P],
+        "stereo_profile_enable": [P, I32],
+        "stereo_profile_read": [P, P, P],
+        "stereo_fp32_peak_probe": [I32, P, P],
+    }
+    for name, args in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.stereo_last_error.restype = ctypes.c_char_p
+    lib.stereo_last_error.argtypes = []
+    lib.stereo_version.restype = ctypes.c_char_p
+    lib.stereo_version.argtypes = []
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != STEREO_OK:
+        raise StereoError(rc, load_library().stereo_last_error().decode())
+    return rc
+
+
+def _ptr(x):
+    """Device pointer of a CUDA tensor (or a raw integer address); None is NULL."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda:
+            raise StereoError(STEREO_EINVAL, "tensor must be on a CUDA device")
+        if not x.is_contiguous():
+            raise StereoError(STEREO_EINVAL, "tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError("expected a CUDA tensor, an integer address or None")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def stereo_version() -> str:
+    return load_library().stereo_version().decode()
+
+
+def stereo_last_error() -> str:
+    return load_library().stereo_last_error().decode()
+
+
+def stereo_params_default(**overrides) -> stereo_params:
+    p = stereo_params()
+    _check(load_library().stereo_params_default(ctypes.byref(p)))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def stereo_create(params: stereo_params):
+    ctx = ctypes.c_void_p()
+    _check(load_library().stereo_create(ctypes.byref(params), ctypes.byref(ctx)))
+    return ctx
+
+
+def stereo_destroy(ctx):
+    _check(load_library().stereo_destroy(ctx))
+
+
+def stereo_row_shift_affine(height, c0, c1, delta_p):
+    import numpy as np
+    out = np.empty(int(height), dtype=np.float32)
+    _check(load_library().stereo_row_shift_affine(int(height), float(c0), float(c1), float(delta_p),
+                                                  out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def stereo_warp_target(ctx, tgt, shift, tgt_warped, stream=None):
+    _check(load_library().stereo_warp_target(ctx, _ptr(tgt), _ptr(shift), _ptr(tgt_warped),
+                                             _stream(stream)))
+
+
+def stereo_cost_aggregate_wta(ctx, ref, tgt_warped, shift, disp, wta=None, valid=None, stream=None):
+    _check(load_library().stereo_cost_aggregate_wta(ctx, _ptr(ref), _ptr(tgt_warped), _ptr(shift),
+                                                    _ptr(disp), _ptr(wta), _ptr(valid),
+                                                    _stream(stream)))
+
+
+def stereo_disparity_transform(ctx, disp, mask, psi_init, delta_t, disp_out, res=None, stream=None):
+    """res: None -> the call synchronises and returns a stereo_dt_result (host);
+    a CUDA uint8 tensor of >= 48 bytes -> the result stays on the device (asynchronous)."""
+    lib = load_library()
+    if res is None:
+        r = stereo_dt_result()
+        _check(lib.stereo_disparity_transform(ctx, _ptr(disp), _ptr(mask), float(psi_init),
+                                              float(delta_t), _ptr(disp_out), ctypes.byref(r),
+                                              _stream(stream)))
+        return r
+    _check(lib.stereo_disparity_transform(ctx, _ptr(disp), _ptr(mask), float(psi_init), float(delta_t),
+                                          _ptr(disp_out), _ptr(res), _stream(stream)))
+    return None
+
+
+def stereo_cost_volume(ctx, ref, tgt_warped, cost, stream=None):
+    _check(load_library().stereo_cost_volume(ctx, _ptr(ref), _ptr(tgt_warped), _ptr(cost),
+                                             _stream(stream)))
+
+
+def stereo_aggregate_volume(ctx, ref, cost, agg, stream=None):
+    _check(load_library().stereo_aggregate_volume(ctx, _ptr(ref), _ptr(cost), _ptr(agg),
+                                                  _stream(stream)))
+
+
+def stereo_wta_volume(ctx, agg, shift, disp, wta=None, best2=None, stream=None):
+    _check(load_library().stereo_wta_volume(ctx, _ptr(agg), _ptr(shift), _ptr(disp), _ptr(wta),
+                                            _ptr(best2), _stream(stream)))
+
+
+def stereo_check_device_status(ctx, stream=None):
+    _check(load_library().stereo_check_device_status(ctx, _stream(stream)))
+
+
+def stereo_profile_enable(ctx, on=True):
+    _check(load_library().stereo_profile_enable(ctx, 1 if on else 0))
+
+
+def stereo_profile_read(ctx):
+    n = ctypes.c_int32()
+    ms = ctypes.c_double()
+    _check(load_library().stereo_profile_read(ctx, ctypes.byref(n), ctypes.byref(ms)))
+    return int(n.value), float(ms.value)
+
+
+def stereo_fp32_peak_probe(blocks_per_sm=2):
+    gs = ctypes.c_double()
+    gp = ctypes.c_double()
+    _check(load_library().stereo_fp32_peak_probe(int(blocks_per_sm), ctypes.byref(gs), ctypes.byref(gp)))
+    return float(gs.value), float(gp.value)
+
+
+class Stereo:
+    """Owns one context; methods are the C calls with this context bound."""
+
+    def __init__(self, width, height, max_disp, win=9, bil=11, sigma0=1.5, sigma1=5.5,
+                 pitch=None, cost_dtype=STEREO_F32, **extra):
+        pitch = pitch if pitch is not None else (width + 15) // 16 * 16
+        self.params = stereo_params_default(width=width, height=height, pitch=pitch,
+                                            max_disp=max_disp, win=win, bil=bil, sigma0=sigma0,
+                                            sigma1=sigma1, cost_dtype=cost_dtype, **extra)
+        self.ctx = stereo_create(self.params)
+
+    def close(self):
+        if self.ctx is not None:
+            stereo_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def warp_target(self, tgt, shift, out, stream=None):
+        stereo_warp_target(self.ctx, tgt, shift, out, stream)
+
+    def cost_aggregate_wta(self, ref, tgt_warped, shift, disp, wta=None, valid=None, stream=None):
+        stereo_cost_aggregate_wta(self.ctx, ref, tgt_warped, shift, disp, wta, valid, stream)
+
+    def disparity_transform(self, disp, mask, psi_init, delta_t, out, res=None, stream=None):
+        return stereo_disparity_transform(self.ctx, disp, mask, psi_init, delta_t, out, res, stream)
+
+    def cost_volume(self, ref, tgt_warped, cost, stream=None):
+        stereo_cost_volume(self.ctx, ref, tgt_warped, cost, stream)
+
+    def aggregate_volume(self, ref, cost, agg, stream=None):
+        stereo_aggregate_volume(self.ctx, ref, cost, agg, stream)
+
+    def wta_volume(self, agg, shift, disp, wta=None, best2=None, stream=None):
+        stereo_wta_volume(self.ctx, agg, shift, disp, wta, best2, stream)
+
+    def check_device_status(self, stream=None):
+        stereo_check_device_status(self.ctx, stream)

@@ -1,0 +1,84 @@
+// internal.cuh -- declarations shared by the translation units of the library.
+// Not part of the C ABI (include/stereo.h is).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "stereo.h"
+
+namespace sgb {
+
+// Tiling of the fused kernel: a CTA of 8 warps owns a kTileX x kTileY block of output
+// pixels; lane = column, each warp covers 32 columns x kPY rows.
+constexpr int kTileX = 64;
+constexpr int kPY = 8;
+constexpr int kTileY = 4 * kPY;
+constexpr int kThreads = 256;
+constexpr int kMaxRB = 7;          // bil <= 15
+constexpr int kMaxRW = 5;          // win <= 11
+constexpr int kMaxD = 256;
+constexpr int kMaxDim = 16384;
+constexpr int kProfSlots = 4096;
+constexpr int kDtThreads = 256;
+constexpr int kDtMaxBlocks = 1024;   // partial-moment blocks of the disparity transformation
+
+// Derived geometry of a context (all sizes in pixels / bytes).
+struct Geometry {
+    int W, H, pitch, D, rw, rb, m, n;
+    int dc;            // disparities per chunk of the fused kernel
+    int Dp;            // D rounded up to a multiple of dc
+    int ntx, nty;      // tiles
+    int pad_left, pad_top, pad_w, pad_h, pad_pitch;   // replicate-padded staging images
+    int ref_box_w, tgt_box_w, box_h;                  // TMA boxes (bytes x rows)
+    int ref_e, tgt_e;  // column offset of image column x0 - m (resp. x0 - m - (Dp-1)) in the box
+    size_t smem_bytes; // dynamic shared memory of the fused kernel
+};
+
+}  // namespace sgb
+
+struct stereo_ctx {
+    stereo_params p;
+    sgb::Geometry g;
+    int device;
+    uint8_t *ref_pad, *tgt_pad;    // replicate-padded copies (pad_pitch x pad_h)
+    int2 *ref_stats, *tgt_stats;   // per padded position: {sum, bits of 1/sqrt(n*sumsq - sum^2)}
+    CUtensorMap tmap_ref, tmap_tgt;
+    float kspatial[(2 * sgb::kMaxRB + 1) * (2 * sgb::kMaxRB + 1)];  // -log2(e) |dq|^2 / sigma0^2
+    float iscale;                  // sqrt(log2(e)) / sigma1
+    double *mom_part;              // [kDtMaxBlocks][10] partial moments
+    float *dt_coef;                // 3 FP32 coefficients of the final per-pixel map
+    stereo_dt_result *res_dev;     // device-side result when the caller passes none
+    int *status_dev;               // device status word (bounded waits)
+    // fused-kernel timing
+    int prof_on;
+    int prof_n;
+    std::vector<cudaEvent_t> prof_ev;
+};
+
+namespace sgb {
+
+int set_error(int code, const char *fmt, ...);
+int cuda_error(cudaError_t e, const char *what);
+
+// Launchers (each returns STEREO_OK or an error code; they only enqueue work).
+int launch_warp(stereo_ctx *ctx, const uint8_t *tgt, const float *shift, uint8_t *out,
+                cudaStream_t s);
+int launch_prep(stereo_ctx *ctx, const uint8_t *ref, const uint8_t *tgtw, cudaStream_t s);
+int launch_fused(stereo_ctx *ctx, const float *shift, float *disp, int32_t *wta, uint8_t *valid,
+                 cudaStream_t s);
+size_t fused_smem_bytes(const Geometry &g);
+int fused_configure(stereo_ctx *ctx);
+int launch_cost_volume(stereo_ctx *ctx, float *cost, cudaStream_t s);
+int launch_aggregate_volume(stereo_ctx *ctx, const uint8_t *ref, const float *cost, float *agg,
+                            cudaStream_t s);
+int launch_wta_volume(stereo_ctx *ctx, const float *agg, const float *shift, float *disp,
+                      int32_t *wta, float *best2, cudaStream_t s);
+int launch_dt(stereo_ctx *ctx, const float *disp, const uint8_t *mask, double psi_init,
+              float delta_t, float *out, stereo_dt_result *res_dev, cudaStream_t s);
+int run_fp32_probe(int blocks_per_sm, double *gflops_scalar, double *gflops_packed);
+
+}  // namespace sgb

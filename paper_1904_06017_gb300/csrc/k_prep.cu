@@ -1,0 +1,196 @@
+// k_prep.cu -- the perspective warp of the target image (§3.1), the staging kernel that
+// builds replicate-padded copies and per-position window statistics for the fused
+// kernel, and an FP32 FMA throughput probe.
+#include "internal.cuh"
+
+namespace sgb {
+
+// §3.1: tgt_warped(u, v) = tgt(clamp(u - s_i(v), 0, W-1), v), s_i = floor(s + 0.5).
+// One thread writes 16 consecutive bytes of an output row.
+__global__ void k_warp(const uint8_t *__restrict__ tgt, const float *__restrict__ shift,
+                       uint8_t *__restrict__ out, int W, int H, int pitch)
+{
+    const int v = blockIdx.y;
+    const int u0 = (blockIdx.x * blockDim.x + threadIdx.x) * 16;
+    if (v >= H || u0 >= W) return;
+    const int si = (int)floor((double)shift[v] + 0.5);
+    const uint8_t *row = tgt + (size_t)v * pitch;
+    uint8_t *orow = out + (size_t)v * pitch;
+    const int a = u0 - si;
+    if (u0 + 16 <= W && a >= 0 && a + 16 <= W && (a & 15) == 0) {
+        *reinterpret_cast<uint4 *>(orow + u0) = __ldg(reinterpret_cast<const uint4 *>(row + a));
+        return;
+    }
+    if (u0 + 16 <= W) {
+        uint32_t w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t x = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                int src = min(max(a + 4 * k + b, 0), W - 1);
+                x |= (uint32_t)__ldg(row + src) << (8 * b);
+            }
+            w[k] = x;
+        }
+        *reinterpret_cast<uint4 *>(orow + u0) = make_uint4(w[0], w[1], w[2], w[3]);
+        return;
+    }
+    for (int u = u0; u < W; ++u) orow[u] = __ldg(row + min(max(u - si, 0), W - 1));
+}
+
+int launch_warp(stereo_ctx *ctx, const uint8_t *tgt, const float *shift, uint8_t *out, cudaStream_t s)
+{
+    const Geometry &g = ctx->g;
+    const int chunks = (g.W + 15) / 16;
+    dim3 block(128), grid((chunks + 127) / 128, g.H);
+    k_warp<<<grid, block, 0, s>>>(tgt, shift, out, g.W, g.H, g.pitch);
+    return cuda_error(cudaGetLastError(), "k_warp launch");
+}
+
+// Staging: for every position (x, y) of the padded frame (image column x - pad_left,
+// row y - pad_top, reads clamped to the image) write the pixel to the padded copy and
+// the window statistics of the w x w block centred there:
+//     {S = sum I, bits of r = 1/sqrt(n * sum I^2 - S^2)}, r = 0 for a flat block.
+// These are the mu / sigma of eq. (c), kept as exact integer sums (§4.3 precomputes
+// mu and sigma in global memory as well).  Block: 32 x 8 positions.
+constexpr int kPrepX = 32, kPrepY = 8;
+
+__global__ void __launch_bounds__(kPrepX *kPrepY)
+k_prep(const uint8_t *__restrict__ ref, const uint8_t *__restrict__ tgt, int W, int H, int pitch,
+       int rw, int pad_left, int pad_top, int pad_w, int pad_h, int pad_pitch,
+       uint8_t *__restrict__ ref_pad, uint8_t *__restrict__ tgt_pad,
+       int2 *__restrict__ ref_stats, int2 *__restrict__ tgt_stats)
+{
+    constexpr int SX = kPrepX + 2 * kMaxRW, SY = kPrepY + 2 * kMaxRW;
+    __shared__ uint8_t sr[SY][SX], st[SY][SX];
+    __shared__ int hs[2][SY][kPrepX], hq[2][SY][kPrepX];
+    const int x0 = blockIdx.x * kPrepX, y0 = blockIdx.y * kPrepY;
+    const int tid = threadIdx.y * kPrepX + threadIdx.x;
+    const int sx = kPrepX + 2 * rw, sy = kPrepY + 2 * rw;
+    for (int i = tid; i < sx * sy; i += kPrepX * kPrepY) {
+        int ly = i / sx, lx = i % sx;
+        int ix = min(max(x0 - rw + lx - pad_left, 0), W - 1);
+        int iy = min(max(y0 - rw + ly - pad_top, 0), H - 1);
+        sr[ly][lx] = ref[(size_t)iy * pitch + ix];
+        st[ly][lx] = tgt[(size_t)iy * pitch + ix];
+    }
+    __syncthreads();
+    // horizontal sums over 2rw+1 columns
+    for (int i = tid; i < sy * kPrepX; i += kPrepX * kPrepY) {
+        int ly = i / kPrepX, lx = i % kPrepX;
+        int a = 0, aa = 0, b = 0, bb = 0;
+        for (int j = 0; j <= 2 * rw; ++j) {
+            int r = sr[ly][lx + j], t = st[ly][lx + j];
+            a += r;
+            aa += r * r;
+            b += t;
+            bb += t * t;
+        }
+        hs[0][ly][lx] = a;
+        hq[0][ly][lx] = aa;
+        hs[1][ly][lx] = b;
+        hq[1][ly][lx] = bb;
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= pad_w || y >= pad_h) return;
+    const int n = (2 * rw + 1) * (2 * rw + 1);
+    int S[2] = {0, 0}, Q[2] = {0, 0};
+    for (int j = 0; j <= 2 * rw; ++j)
+        for (int k = 0; k < 2; ++k) {
+            S[k] += hs[k][threadIdx.y + j][threadIdx.x];
+            Q[k] += hq[k][threadIdx.y + j][threadIdx.x];
+        }
+    int2 *dst[2] = {ref_stats, tgt_stats};
+    for (int k = 0; k < 2; ++k) {
+        int A = n * Q[k] - S[k] * S[k];   // n^2 sigma^2, exact (< 2^31 for w <= 11)
+        float r = A > 0 ? 1.0f / sqrtf((float)A) : 0.0f;
+        dst[k][(size_t)y * pad_w + x] = make_int2(S[k], __float_as_int(r));
+    }
+    ref_pad[(size_t)y * pad_pitch + x] = sr[threadIdx.y + rw][threadIdx.x + rw];
+    tgt_pad[(size_t)y * pad_pitch + x] = st[threadIdx.y + rw][threadIdx.x + rw];
+}
+
+int launch_prep(stereo_ctx *ctx, const uint8_t *ref, const uint8_t *tgtw, cudaStream_t s)
+{
+    const Geometry &g = ctx->g;
+    if (((uintptr_t)ref | (uintptr_t)tgtw) % 16)
+        return set_error(STEREO_EINVAL, "images must be 16-byte aligned");
+    dim3 block(kPrepX, kPrepY), grid((g.pad_w + kPrepX - 1) / kPrepX, (g.pad_h + kPrepY - 1) / kPrepY);
+    k_prep<<<grid, block, 0, s>>>(ref, tgtw, g.W, g.H, g.pitch, g.rw, g.pad_left, g.pad_top, g.pad_w,
+                                  g.pad_h, g.pad_pitch, ctx->ref_pad, ctx->tgt_pad, ctx->ref_stats,
+                                  ctx->tgt_stats);
+    return cuda_error(cudaGetLastError(), "k_prep launch");
+}
+
+// ------------------------------------------------------------------ FP32 probe
+constexpr int kProbeChains = 8;
+
+__global__ void __launch_bounds__(256) k_probe_scalar(float *out, int iters, float m)
+{
+    float acc[kProbeChains];
+#pragma unroll
+    for (int j = 0; j < kProbeChains; ++j) acc[j] = threadIdx.x * 1e-3f + j;
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int j = 0; j < kProbeChains; ++j) acc[j] = fmaf(acc[j], m, 1e-3f);
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < kProbeChains; ++j) s += acc[j];
+    if (s == 1234.5f) out[0] = s;
+}
+
+__global__ void __launch_bounds__(256) k_probe_packed(float *out, int iters, float m)
+{
+    float2 acc[kProbeChains];
+#pragma unroll
+    for (int j = 0; j < kProbeChains; ++j) acc[j] = make_float2(threadIdx.x * 1e-3f + j, j - 1.f);
+    const float2 mm = make_float2(m, m), cc = make_float2(1e-3f, 1e-3f);
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int j = 0; j < kProbeChains; ++j) acc[j] = __ffma2_rn(acc[j], mm, cc);
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < kProbeChains; ++j) s += acc[j].x + acc[j].y;
+    if (s == 1234.5f) out[0] = s;
+}
+
+int run_fp32_probe(int blocks_per_sm, double *gs, double *gp)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    float *out = nullptr;
+    int rc = cuda_error(cudaMalloc(&out, sizeof(float)), "probe alloc");
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int iters = 1 << 16, blocks = sms * blocks_per_sm;
+    double res[2] = {0, 0};
+    for (int kind = 0; kind < 2; ++kind) {
+        float best = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(e0, 0);
+            if (kind == 0) k_probe_scalar<<<blocks, 256>>>(out, iters, 0.999f);
+            else k_probe_packed<<<blocks, 256>>>(out, iters, 0.999f);
+            cudaEventRecord(e1, 0);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && ms < best) best = ms;
+        }
+        double fma_lanes = (double)blocks * 256 * iters * kProbeChains * (kind == 0 ? 1 : 2);
+        res[kind] = 2.0 * fma_lanes / (best * 1e-3) * 1e-9;
+    }
+    rc = cuda_error(cudaGetLastError(), "probe kernels");
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    *gs = res[0];
+    *gp = res[1];
+    return rc;
+}
+
+}  // namespace sgb

@@ -1,0 +1,109 @@
+"""C-ABI checks that need no GPU: the library builds, loads and exports every entry
+point include/stereo.h declares; the ctypes structures match the C layout; host-only
+helpers and argument validation behave as documented."""
+import ctypes
+import json
+import math
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_1904_06017_gb300 as sg
+from paper_1904_06017_gb300 import build as sgbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "stereo.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    sgbuild.build()
+    return sg.load_library()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(stereo_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", sg.library_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (stereo_[a-z0-9_]+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert hasattr(lib, n)
+
+
+def test_struct_layout_matches_header(tmp_path):
+    prog = tmp_path / "layout.c"
+    prog.write_text(r'''
+#include <stddef.h>
+#include <stdio.h>
+#include "stereo.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\n", sizeof(stereo_params), offsetof(stereo_params, lambda0),
+         offsetof(stereo_params, max_iters), sizeof(stereo_dt_result), offsetof(stereo_dt_result, n));
+  return 0;
+}''')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    vals = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                           check=True).stdout.split()]
+    assert vals == [ctypes.sizeof(sg.stereo_params), sg.stereo_params.lambda0.offset,
+                    sg.stereo_params.max_iters.offset, ctypes.sizeof(sg.stereo_dt_result),
+                    sg.stereo_dt_result.n.offset]
+
+
+def test_defaults_are_the_paper_constants(lib):
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_constants.json")))
+    p = sg.stereo_params_default()
+    assert p.sigma0 == pytest.approx(g["sigma0"]["value"])
+    assert p.sigma1 == pytest.approx(g["sigma1"]["value"])
+    assert p.bil == g["bilateral_window"]["value"]
+    assert p.bil * p.bil - 1 == g["neighbourhood_size"]["value"]
+    assert p.lambda0 == g["lambda0"]["value"]
+    assert p.delta_psi == pytest.approx(g["delta_psi_rad"]["value"], rel=1e-15)
+    assert p.delta_psi == pytest.approx(math.pi / 1.8e6, rel=1e-15)
+
+
+def test_row_shift_affine(lib):
+    s = sg.stereo_row_shift_affine(5, 2.0, 0.5, 1.0)
+    assert np.allclose(s, [1.0, 1.5, 2.0, 2.5, 3.0])
+    with pytest.raises(sg.StereoError) as e:
+        sg.stereo_row_shift_affine(0, 0, 0, 0)
+    assert e.value.code == sg.STEREO_EINVAL
+
+
+@pytest.mark.parametrize("field,value", [("width", 0), ("height", -3), ("pitch", 100),
+                                         ("max_disp", 0), ("max_disp", 1000), ("win", 4),
+                                         ("win", 13), ("bil", 17), ("bil", 2), ("sigma0", 0.0),
+                                         ("sigma1", float("nan")), ("cost_dtype", 7),
+                                         ("lambda0", -1.0), ("max_iters", 0)])
+def test_create_rejects_bad_parameters(lib, field, value):
+    p = sg.stereo_params_default(width=320, height=240, pitch=320, max_disp=64)
+    setattr(p, field, value)
+    with pytest.raises(sg.StereoError) as e:
+        sg.stereo_create(p)
+    assert e.value.code == sg.STEREO_EINVAL
+    assert "stereo_create" in sg.stereo_last_error()
+
+
+def test_null_pointers_rejected(lib):
+    rc = lib.stereo_create(None, None)
+    assert rc == sg.STEREO_EINVAL
+    assert lib.stereo_warp_target(None, None, None, None, None) == sg.STEREO_EINVAL
+    assert lib.stereo_cost_aggregate_wta(None, None, None, None, None, None, None, None) == sg.STEREO_EINVAL
+    assert lib.stereo_disparity_transform(None, None, None, 0.0, 0.0, None, None, None) == sg.STEREO_EINVAL
+    assert lib.stereo_destroy(None) == sg.STEREO_OK
+
+
+def test_version(lib):
+    assert "sm_103a" in sg.stereo_version()
