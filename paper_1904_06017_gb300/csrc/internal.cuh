@@ -46,6 +46,7 @@ struct stereo_ctx {
     int device;
     uint8_t *ref_pad, *tgt_pad;    // replicate-padded copies (pad_pitch x pad_h)
     int2 *ref_stats, *tgt_stats;   // per padded position: {sum, bits of 1/sqrt(n*sumsq - sum^2)}
+    int4 *row_tab;                 // per image row: {s_i(v), max and min of s_i over rows v-m..v+m, 0}
     CUtensorMap tmap_ref, tmap_tgt;
     float kspatial[(2 * sgb::kMaxRB + 1) * (2 * sgb::kMaxRB + 1)];  // -log2(e) |dq|^2 / sigma0^2
     float iscale;                  // sqrt(log2(e)) / sigma1
@@ -68,6 +69,7 @@ int cuda_error(cudaError_t e, const char *what);
 int launch_warp(stereo_ctx *ctx, const uint8_t *tgt, const float *shift, uint8_t *out,
                 cudaStream_t s);
 int launch_prep(stereo_ctx *ctx, const uint8_t *ref, const uint8_t *tgtw, cudaStream_t s);
+int launch_row_tables(stereo_ctx *ctx, const float *shift, cudaStream_t s);
 int launch_fused(stereo_ctx *ctx, const float *shift, float *disp, int32_t *wta, uint8_t *valid,
                  cudaStream_t s);
 size_t fused_smem_bytes(const Geometry &g);

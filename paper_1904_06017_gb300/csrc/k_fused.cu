@@ -4,18 +4,19 @@
 // One CTA (8 warps) owns a 64 x 32 block of output pixels and all D disparities:
 //  1. TMA (cp.async.bulk.tensor) stages the reference tile and the warped-target strip
 //     (replicate-padded copies) into shared memory, one box each, on an mbarrier.
-//  2. For each chunk of DC disparities:
+//  2. For each chunk of DC disparities, band by band of kBand cost rows:
 //     a. vertical running sums of the products I_ref(x,y) I_tar(x-d,y) over the w rows
-//        of the block (exact integers), one walker per (column, d);
-//     b. horizontal running sums of those (the full w x w correlation sum of eq. c),
-//        then c = 1 - (n S - S_ref S_tar) / sqrt(A_ref A_tar), written in place: the
-//        chunk's cost volume for the tile plus its bilateral halo lives only in shared
-//        memory, never in device memory;
+//        of the block (exact integers), one walker per (product column, d), the sum
+//        carried in a register from band to band;
+//     b. horizontal sums of those over the w columns (the full w x w correlation sum of
+//        eq. c), four disparities per work item, then
+//        c = 1 - (n S - S_ref S_tar) / sqrt(A_ref A_tar): the chunk's costs at the tile
+//        plus its bilateral halo live only in shared memory, never in device memory;
 //     c. aggregation: each thread owns a column of kPY pixels x DC disparities in
-//        registers; for every neighbour row it loads the DC costs once (LDS.128) and
-//        applies them to every pixel whose window holds it, with the weight
-//        w = 2^(K[dx][dy] - (s I_q - s I_p)^2) (eq. omega0 x eq. omega1 in one base-2
-//        exponent, MUFU ex2) and packed f32x2 FMAs over pairs of disparities;
+//        registers; for every neighbour row it loads the DC costs once (LDS.128, the
+//        next row prefetched) and applies them to every pixel whose window holds it,
+//        with the weight w = 2^(K[dx][dy] - (s I_q - s I_p)^2) (eq. omega0 x eq. omega1
+//        in one base-2 exponent, MUFU ex2) and packed f32x2 FMAs over disparity pairs;
 //     d. running WTA over d (lowest d wins ties) keeping the neighbours of the best d.
 //  3. Epilogue: eq. (subpixel) on the winner's neighbours, add back s_i(v), write.
 // Normalising by sum_q w(p,q) is skipped: it is a positive per-pixel constant, so the
@@ -27,7 +28,7 @@ namespace sgb {
 struct FusedArgs {
     const int2 *ref_stats;
     const int2 *tgt_stats;
-    const float *shift;
+    const int4 *row_tab;
     float *disp;
     int32_t *wta;
     uint8_t *valid;
@@ -38,6 +39,9 @@ struct FusedArgs {
     float iscale;
     float K[(2 * kMaxRB + 1) * (2 * kMaxRB + 1)];
 };
+
+constexpr int kBand = 6;   // cost rows per band of the two-pass window sums
+constexpr int kSeg = 7;    // cost columns per horizontal-pass work item
 
 __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -91,9 +95,17 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
-// Shared-memory layout (all offsets from the dynamic base, which is 128-byte aligned).
+// Shared-memory layout (offsets from the dynamic base, which is 128-byte aligned):
+//   sref  [box_h][ref_box_w] u8     reference tile (TMA)
+//   stgt  [box_h][tgt_box_w] u8     warped-target strip (TMA)
+//   cbuf  [QH][QW][DC] f32          the chunk's costs at the tile + bilateral halo
+//   vband [kBand][CW][DC] i32       vertical window sums of one band of cost rows
+//   sstr  [kBand][QW] int2          window statistics of the reference, this band
+//   sstt  [kBand][QW+DC-1] int2     window statistics of the target behind the band's costs
+//   sI    [QH][QW] f32              scaled reference intensity at the cost positions
+//   sK    [KB][KB] f32              spatial part of the weight exponent
 struct SmemLayout {
-    size_t sref, stgt, cbuf, sI, sK, bar, flag, total;
+    size_t sref, stgt, cbuf, vband, sstr, sstt, sI, sK, bar, flag, total;
 };
 
 __host__ __device__ inline SmemLayout smem_layout(int rb, int m, int dc, int ref_box_w,
@@ -104,7 +116,10 @@ __host__ __device__ inline SmemLayout smem_layout(int rb, int m, int dc, int ref
     L.sref = 0;
     L.stgt = align_up(L.sref + (size_t)box_h * ref_box_w, 128);
     L.cbuf = align_up(L.stgt + (size_t)box_h * tgt_box_w, 128);
-    L.sI = align_up(L.cbuf + (size_t)QH * CW * dc * 4, 16);
+    L.vband = align_up(L.cbuf + (size_t)QH * QW * dc * 4, 128);
+    L.sstr = align_up(L.vband + (size_t)kBand * CW * dc * 4, 16);
+    L.sstt = align_up(L.sstr + (size_t)kBand * QW * 8, 16);
+    L.sI = align_up(L.sstt + (size_t)kBand * (QW + dc - 1) * 8, 16);
     L.sK = align_up(L.sI + (size_t)QH * QW * 4, 16);
     L.bar = align_up(L.sK + (size_t)KB * KB * 4, 8);
     L.flag = L.bar + 8;
@@ -117,6 +132,162 @@ size_t fused_smem_bytes(const Geometry &g)
     return smem_layout(g.rb, g.m, g.dc, g.ref_box_w, g.tgt_box_w, g.box_h).total;
 }
 
+// The costs of one chunk of DC disparities at the tile plus its bilateral halo (QH x QW
+// positions), eq. (c), into cbuf[QH][QW][DC], band by band of kBand cost rows:
+//  vertical pass: V(x, y, d) = sum_{i < w} I_ref(x, y+i) I_tar(x-d, y+i), one walker per
+//      (product column x, d), a running sum carried in a register from band to band;
+//  horizontal pass: S = sum_{j < w} V(x+j, y, d) for four d per work item, then
+//      c = 1 - (n S - S_ref S_tar) r_ref r_tar with the staged window statistics.
+// Every pass issues all of its shared-memory loads before its stores, so the loads of a
+// band are in flight together instead of waiting behind stores they might alias.
+template <int RB, int DC, int RW>
+__device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sref, const uint8_t *stgt,
+                                           float *cbuf, int *vband, int2 *sstr, int2 *sstt,
+                                           int x0, int y0, int d0, int tid)
+{
+    constexpr int WS = 2 * RW + 1;                    // block size w
+    constexpr int QH = kTileY + 2 * RB, QW = kTileX + 2 * RB;
+    constexpr int CW = kTileX + 2 * (RW + RB);        // product columns
+    constexpr int NQ = DC / 4;
+    constexpr int NSEG = (QW + kSeg - 1) / kSeg;
+    constexpr int NWV = (CW * DC + kThreads - 1) / kThreads;   // vertical walkers per thread
+    constexpr int TSW = QW + DC - 1;                  // target-statistics columns of a chunk
+    constexpr int NST = (kBand * (QW + TSW) + kThreads - 1) / kThreads;
+    const int RP = a.ref_box_w, TP = a.tgt_box_w;
+    const size_t crow = (size_t)QW * DC;
+
+    // walker start: the first w-1 product rows (row 0's window lacks only its last row)
+    int vacc[NWV];
+#pragma unroll
+    for (int k = 0; k < NWV; ++k) {
+        vacc[k] = 0;
+        const int w = tid + k * kThreads;
+        if (w < CW * DC) {
+            const int xp = w / DC, dd = w - xp * DC;
+            const uint8_t *rc = sref + a.ref_e + xp;
+            const uint8_t *tc = stgt + a.tgt_e + xp + (a.Dp - 1) - (d0 + dd);
+            int s0 = 0;
+#pragma unroll
+            for (int i = 0; i < WS - 1; ++i) s0 += (int)rc[i * RP] * (int)tc[i * TP];
+            vacc[k] = s0;
+        }
+    }
+    for (int yb0 = 0; yb0 < QH; yb0 += kBand) {
+        const int nrows = min(kBand, QH - yb0);
+        // window statistics of this band: loads issued now, stored after the vertical pass
+        int2 stv[NST];
+#pragma unroll
+        for (int k = 0; k < NST; ++k) {
+            const int e = tid + k * kThreads;
+            stv[k] = make_int2(0, 0);
+            if (e < kBand * (QW + TSW)) {
+                const int r = e / (QW + TSW), c = e - r * (QW + TSW);
+                if (r < nrows) {
+                    const size_t prow = (size_t)(y0 - RB + yb0 + r + a.pad_top) * a.pad_w;
+                    stv[k] = c < QW ? __ldg(a.ref_stats + prow + x0 - RB + a.pad_left + c)
+                                    : __ldg(a.tgt_stats + prow + x0 - RB + a.pad_left - d0 - (DC - 1) + (c - QW));
+                }
+            }
+        }
+        // vertical pass: all product loads of every walker first ...
+        int pn[NWV][kBand], po[NWV][kBand];
+#pragma unroll
+        for (int k = 0; k < NWV; ++k) {
+            const int w = tid + k * kThreads;
+            const int xp = w / DC, dd = w - xp * DC;
+            const bool on = w < CW * DC;
+            const uint8_t *rc = sref + a.ref_e + (on ? xp : 0);
+            const uint8_t *tc = stgt + a.tgt_e + (on ? xp + (a.Dp - 1) - (d0 + dd) : 0);
+#pragma unroll
+            for (int r = 0; r < kBand; ++r) {
+                const int yq = yb0 + r;
+                const bool live = on && r < nrows;
+                const int ya = live ? yq + WS - 1 : 0, yr = (live && yq > 0) ? yq - 1 : 0;
+                pn[k][r] = live ? (int)rc[ya * RP] * (int)tc[ya * TP] : 0;
+                po[k][r] = (live && yq > 0) ? (int)rc[yr * RP] * (int)tc[yr * TP] : 0;
+            }
+        }
+        // ... then the running sums and their stores
+#pragma unroll
+        for (int k = 0; k < NWV; ++k) {
+            const int w = tid + k * kThreads;
+            if (w < CW * DC) {
+                int *vo = vband + w;            // [r][xp][dd] with xp * DC + dd = w
+                int acc = vacc[k];
+#pragma unroll
+                for (int r = 0; r < kBand; ++r) {
+                    if (r < nrows) {
+                        acc += pn[k][r] - po[k][r];
+                        vo[r * CW * DC] = acc;
+                    }
+                }
+                vacc[k] = acc;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NST; ++k) {
+            const int e = tid + k * kThreads;
+            if (e < kBand * (QW + TSW)) {
+                const int r = e / (QW + TSW), c = e - r * (QW + TSW);
+                if (c < QW) sstr[r * QW + c] = stv[k];
+                else sstt[r * TSW + (c - QW)] = stv[k];
+            }
+        }
+        __syncthreads();
+        // horizontal pass: item = (band row, disparity quad, column segment), the segment
+        // index fastest so that neighbouring lanes hit distinct shared-memory banks
+        const int nitems = nrows * NSEG * NQ;
+        for (int it = tid; it < nitems; it += kThreads) {
+            const int seg = it % NSEG, rq = it / NSEG;
+            const int dq = rq % NQ, r = rq / NQ;
+            const int yq = yb0 + r;
+            const int xs = seg * kSeg;
+            const int nout = min(kSeg, QW - xs);
+            const int4 *vr = reinterpret_cast<const int4 *>(vband) + (size_t)r * CW * NQ + dq;
+            const int2 *rsr = sstr + r * QW;
+            const int2 *tsr = sstt + r * TSW + (DC - 1) - 4 * dq;   // column of x - d for d = d0 + 4dq
+            int4 v[kSeg + WS - 1];
+            int2 rs[kSeg], ts[kSeg + 3];
+#pragma unroll
+            for (int j = 0; j < kSeg + WS - 1; ++j)
+                v[j] = (j < nout + WS - 1) ? vr[(xs + j) * NQ] : make_int4(0, 0, 0, 0);
+#pragma unroll
+            for (int j = 0; j < kSeg; ++j) rs[j] = (j < nout) ? rsr[xs + j] : make_int2(0, 0);
+#pragma unroll
+            for (int j = 0; j < kSeg + 3; ++j) ts[j] = (j < nout + 3) ? tsr[xs + j - 3] : make_int2(0, 0);
+            float4 out[kSeg];
+            int4 S = make_int4(0, 0, 0, 0);
+#pragma unroll
+            for (int j = 0; j < WS; ++j) {
+                S.x += v[j].x;
+                S.y += v[j].y;
+                S.z += v[j].z;
+                S.w += v[j].w;
+            }
+#pragma unroll
+            for (int j = 0; j < kSeg; ++j) {
+                const float ir = __int_as_float(rs[j].y);
+                const int2 t0 = ts[j + 3], t1 = ts[j + 2], t2 = ts[j + 1], t3 = ts[j];
+                out[j].x = fmaf(-(float)(a.n * S.x - rs[j].x * t0.x), ir * __int_as_float(t0.y), 1.0f);
+                out[j].y = fmaf(-(float)(a.n * S.y - rs[j].x * t1.x), ir * __int_as_float(t1.y), 1.0f);
+                out[j].z = fmaf(-(float)(a.n * S.z - rs[j].x * t2.x), ir * __int_as_float(t2.y), 1.0f);
+                out[j].w = fmaf(-(float)(a.n * S.w - rs[j].x * t3.x), ir * __int_as_float(t3.y), 1.0f);
+                if (j + 1 < kSeg) {
+                    S.x += v[j + WS].x - v[j].x;
+                    S.y += v[j + WS].y - v[j].y;
+                    S.z += v[j + WS].z - v[j].z;
+                    S.w += v[j + WS].w - v[j].w;
+                }
+            }
+            float4 *co = reinterpret_cast<float4 *>(cbuf + (size_t)yq * crow) + dq;
+#pragma unroll
+            for (int j = 0; j < kSeg; ++j)
+                if (j < nout) co[(xs + j) * NQ] = out[j];
+        }
+        __syncthreads();
+    }
+}
+
 template <int RB, int DC>
 __global__ void __launch_bounds__(kThreads, 1)
 k_fused(const __grid_constant__ CUtensorMap tmap_ref, const __grid_constant__ CUtensorMap tmap_tgt,
@@ -126,6 +297,7 @@ k_fused(const __grid_constant__ CUtensorMap tmap_ref, const __grid_constant__ CU
     constexpr int KB = 2 * RB + 1;
     constexpr int QH = kTileY + 2 * RB, QW = kTileX + 2 * RB;
     constexpr int NR = kPY + 2 * RB;   // neighbour rows seen by one thread's pixel column
+    constexpr int NQ = DC / 4;         // disparity quads per chunk
     extern __shared__ __align__(128) uint8_t smem[];
 
     const int CW = kTileX + 2 * a.m;
@@ -134,6 +306,9 @@ k_fused(const __grid_constant__ CUtensorMap tmap_ref, const __grid_constant__ CU
     uint8_t *sref = smem + L.sref;
     uint8_t *stgt = smem + L.stgt;
     float *cbuf = reinterpret_cast<float *>(smem + L.cbuf);
+    int *vband = reinterpret_cast<int *>(smem + L.vband);
+    int2 *sstr = reinterpret_cast<int2 *>(smem + L.sstr);
+    int2 *sstt = reinterpret_cast<int2 *>(smem + L.sstt);
     float *sI = reinterpret_cast<float *>(smem + L.sI);
     float *sK = reinterpret_cast<float *>(smem + L.sK);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);
@@ -161,7 +336,7 @@ k_fused(const __grid_constant__ CUtensorMap tmap_ref, const __grid_constant__ CU
     __syncthreads();
     if (*flag == 0) return;
 
-    const int rw = a.rw, wsz = 2 * rw + 1;
+    const int rw = a.rw;
     // scaled reference intensities of the cost positions (tile + bilateral halo); a
     // position outside the image gets a huge value so its weight underflows to 0
     for (int i = tid; i < QH * QW; i += kThreads) {
@@ -189,46 +364,17 @@ k_fused(const __grid_constant__ CUtensorMap tmap_ref, const __grid_constant__ CU
         bd[i] = -1;
     }
 
-    const size_t rowstride = (size_t)CW * DC;
+    const size_t crow = (size_t)QW * DC;   // floats per cost row
     for (int d0 = 0; d0 < a.D; d0 += DC) {
-        // ---- 2a. vertical sums of products, one walker per (product column, d)
-        for (int w = tid; w < CW * DC; w += kThreads) {
-            const int xp = w / DC, dd = w - xp * DC;
-            const uint8_t *rc = sref + a.ref_e + xp;
-            const uint8_t *tc = stgt + a.tgt_e + xp + (a.Dp - 1) - (d0 + dd);
-            int acc = 0;
-            for (int i = 0; i < wsz; ++i) acc += (int)rc[i * RP] * (int)tc[i * TP];
-            int *o = reinterpret_cast<int *>(cbuf) + xp * DC + dd;
-            o[0] = acc;
-            for (int yq = 1; yq < QH; ++yq) {
-                const int ya = yq + wsz - 1, yr = yq - 1;
-                acc += (int)rc[ya * RP] * (int)tc[ya * TP] - (int)rc[yr * RP] * (int)tc[yr * TP];
-                o[yq * rowstride] = acc;
-            }
+        // ---- 2a/2b. costs of the chunk (block radius dispatched to a compile-time value)
+        switch (rw) {
+        case 1: cost_chunk<RB, DC, 1>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
+        case 2: cost_chunk<RB, DC, 2>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
+        case 3: cost_chunk<RB, DC, 3>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
+        case 4: cost_chunk<RB, DC, 4>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
+        default: cost_chunk<RB, DC, 5>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
         }
-        __syncthreads();
-        // ---- 2b. horizontal sums and the cost of eq. (c), in place
-        for (int w = tid; w < QH * DC; w += kThreads) {
-            const int yq = w / DC, dd = w - yq * DC;
-            const int d = d0 + dd;
-            int *row = reinterpret_cast<int *>(cbuf) + yq * rowstride + dd;
-            int S = 0;
-            for (int j = 0; j < wsz; ++j) S += row[j * DC];
-            const size_t prow = (size_t)(y0 - RB + yq + a.pad_top) * a.pad_w;
-            const int pcol = x0 - RB + a.pad_left;
-            const int2 *rs = a.ref_stats + prow + pcol;
-            const int2 *ts = a.tgt_stats + prow + pcol - d;
-            for (int xq = 0; xq < QW; ++xq) {
-                const int vold = row[xq * DC];
-                const int2 r = __ldg(rs + xq), t = __ldg(ts + xq);
-                const int num = a.n * S - r.x * t.x;
-                const float c = fmaf(-(float)num, __int_as_float(r.y) * __int_as_float(t.y), 1.0f);
-                reinterpret_cast<float *>(row)[xq * DC] = c;
-                if (xq + 1 < QW) S += row[(xq + wsz) * DC] - vold;
-            }
-        }
-        __syncthreads();
-        // ---- 2c. bilateral aggregation of the chunk
+        // ---- 2c. bilateral aggregation of the chunk: each thread kPY pixels x DC d
         float2 acc[kPY][DC / 2];
 #pragma unroll
         for (int i = 0; i < kPY; ++i)
@@ -238,27 +384,59 @@ k_fused(const __grid_constant__ CUtensorMap tmap_ref, const __grid_constant__ CU
             float Kr[KB];
 #pragma unroll
             for (int j = 0; j < KB; ++j) Kr[j] = sK[dx * KB + j];
-            const float *cb = cbuf + ((size_t)yt0 * CW + xt + dx) * DC;
+            const float *cb = cbuf + ((size_t)yt0 * QW + xt + dx) * DC;
             const float *ib = sI + yt0 * QW + xt + dx;
+            // software pipeline over neighbour rows: while row r is accumulated, the
+            // costs of row r+1 are in flight and its weights are being computed
+            float4 q[NQ];
 #pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                const float4 *c4 = reinterpret_cast<const float4 *>(cb + r * rowstride);
-                float4 q[DC / 4];
-#pragma unroll
-                for (int k = 0; k < DC / 4; ++k) q[k] = c4[k];
-                const float Iq = ib[r * QW];
+            for (int k = 0; k < NQ; ++k) q[k] = reinterpret_cast<const float4 *>(cb)[k];
+            float wgt[kPY];
+            {
+                const float Iq = ib[0];
 #pragma unroll
                 for (int i = 0; i < kPY; ++i) {
-                    const int dy = r - i;          // neighbour row - pixel row + RB
-                    if (dy < 0 || dy > 2 * RB) continue;
-                    const float t = Iq - Ip[i];
-                    const float wgt = ex2_approx(fmaf(-t, t, Kr[dy]));
-                    const float2 w2 = make_float2(wgt, wgt);
-#pragma unroll
-                    for (int k = 0; k < DC / 4; ++k) {
-                        acc[i][2 * k] = __ffma2_rn(w2, make_float2(q[k].x, q[k].y), acc[i][2 * k]);
-                        acc[i][2 * k + 1] = __ffma2_rn(w2, make_float2(q[k].z, q[k].w), acc[i][2 * k + 1]);
+                    const int dy = 0 - i;
+                    if (dy >= 0 && dy <= 2 * RB) {
+                        const float t = Iq - Ip[i];
+                        wgt[i] = ex2_approx(fmaf(-t, t, Kr[dy]));
                     }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                float4 qn[NQ];
+                float wn[kPY];
+                if (r + 1 < NR) {
+#pragma unroll
+                    for (int k = 0; k < NQ; ++k) qn[k] = reinterpret_cast<const float4 *>(cb + (r + 1) * crow)[k];
+                    const float Iq = ib[(r + 1) * QW];
+#pragma unroll
+                    for (int i = 0; i < kPY; ++i) {
+                        const int dy = r + 1 - i;      // neighbour row - pixel row + RB
+                        if (dy >= 0 && dy <= 2 * RB) {
+                            const float t = Iq - Ip[i];
+                            wn[i] = ex2_approx(fmaf(-t, t, Kr[dy]));
+                        }
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < kPY; ++i) {
+                    const int dy = r - i;
+                    if (dy >= 0 && dy <= 2 * RB) {
+                        const float2 w2 = make_float2(wgt[i], wgt[i]);
+#pragma unroll
+                        for (int k = 0; k < NQ; ++k) {
+                            acc[i][2 * k] = __ffma2_rn(w2, make_float2(q[k].x, q[k].y), acc[i][2 * k]);
+                            acc[i][2 * k + 1] = __ffma2_rn(w2, make_float2(q[k].z, q[k].w), acc[i][2 * k + 1]);
+                        }
+                    }
+                }
+                if (r + 1 < NR) {
+#pragma unroll
+                    for (int k = 0; k < NQ; ++k) q[k] = qn[k];
+#pragma unroll
+                    for (int i = 0; i < kPY; ++i) wgt[i] = wn[i];
                 }
             }
         }
@@ -282,29 +460,23 @@ k_fused(const __grid_constant__ CUtensorMap tmap_ref, const __grid_constant__ CU
         __syncthreads();
     }
 
-    // ---- 3. epilogue: eq. (subpixel), add back s_i(v)
+    // ---- 3. epilogue: eq. (subpixel), add back s_i(v), validity from the row table
 #pragma unroll
     for (int i = 0; i < kPY; ++i) {
         const int u = x0 + xt, v = y0 + yt0 + i;
         if (u >= a.W || v >= a.H) continue;
-        const int si = (int)floor((double)__ldg(a.shift + v) + 0.5);
+        const int4 rt = __ldg(a.row_tab + v);   // {s_i(v), max s_i, min s_i over v +- m}
         float delta = 0.f;
         if (bd[i] > 0 && bd[i] < a.D - 1) {
             const float den = 2.f * bm1[i] + 2.f * bp1[i] - 4.f * best[i];
             if (den > 0.f) delta = (bm1[i] - bp1[i]) / den;
         }
         const size_t o = (size_t)v * a.W + u;
-        a.disp[o] = (float)bd[i] + delta + (float)si;
+        a.disp[o] = (float)bd[i] + delta + (float)rt.x;
         if (a.wta) a.wta[o] = bd[i];
         if (a.valid) {
-            int s_hi = -(1 << 30), s_lo = 1 << 30;
-            for (int y = max(v - a.m, 0); y <= min(v + a.m, a.H - 1); ++y) {
-                const int s = (int)floor((double)__ldg(a.shift + y) + 0.5);
-                s_hi = max(s_hi, s);
-                s_lo = min(s_lo, s);
-            }
-            const int ulo = a.m + a.D - 1 + max(0, s_hi);
-            const int uhi = a.W - 1 - a.m + min(0, s_lo);
+            const int ulo = a.m + a.D - 1 + max(0, rt.y);
+            const int uhi = a.W - 1 - a.m + min(0, rt.z);
             a.valid[o] = (uint8_t)(v >= a.m && v <= a.H - 1 - a.m && u >= ulo && u <= uhi);
         }
     }
@@ -353,7 +525,8 @@ int launch_fused(stereo_ctx *ctx, const float *shift, float *disp, int32_t *wta,
     FusedArgs a;
     a.ref_stats = ctx->ref_stats;
     a.tgt_stats = ctx->tgt_stats;
-    a.shift = shift;
+    a.row_tab = ctx->row_tab;
+    (void)shift;
     a.disp = disp;
     a.wta = wta;
     a.valid = valid;

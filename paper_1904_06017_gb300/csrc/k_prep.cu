@@ -124,6 +124,29 @@ int launch_prep(stereo_ctx *ctx, const uint8_t *ref, const uint8_t *tgtw, cudaSt
     return cuda_error(cudaGetLastError(), "k_prep launch");
 }
 
+// Per image row v: the integer shift s_i(v) = floor(s(v) + 0.5) of §3.1, and the largest and
+// smallest s_i over rows v-m..v+m (the validity test of the fused epilogue).  FP64 here keeps
+// the rounding exact for any float s, once per row instead of once per pixel.
+__global__ void k_row_tables(const float *__restrict__ shift, int H, int m, int4 *__restrict__ tab)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= H) return;
+    int hi = -(1 << 30), lo = 1 << 30;
+    for (int y = max(v - m, 0); y <= min(v + m, H - 1); ++y) {
+        const int s = (int)floor((double)shift[y] + 0.5);
+        hi = max(hi, s);
+        lo = min(lo, s);
+    }
+    tab[v] = make_int4((int)floor((double)shift[v] + 0.5), hi, lo, 0);
+}
+
+int launch_row_tables(stereo_ctx *ctx, const float *shift, cudaStream_t s)
+{
+    const Geometry &g = ctx->g;
+    k_row_tables<<<(g.H + 127) / 128, 128, 0, s>>>(shift, g.H, g.m, ctx->row_tab);
+    return cuda_error(cudaGetLastError(), "k_row_tables launch");
+}
+
 // ------------------------------------------------------------------ FP32 probe
 constexpr int kProbeChains = 8;
 

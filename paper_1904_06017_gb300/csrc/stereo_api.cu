@@ -100,6 +100,7 @@ static void free_ctx(stereo_ctx *c)
     cudaFree(c->tgt_pad);
     cudaFree(c->ref_stats);
     cudaFree(c->tgt_stats);
+    cudaFree(c->row_tab);
     cudaFree(c->mom_part);
     cudaFree(c->dt_coef);
     cudaFree(c->res_dev);
@@ -183,6 +184,7 @@ int stereo_create(const stereo_params *p, stereo_ctx **out)
         (rc = cuda_error(cudaMalloc(&c->tgt_pad, img), "cudaMalloc tgt_pad")) ||
         (rc = cuda_error(cudaMalloc(&c->ref_stats, st), "cudaMalloc ref_stats")) ||
         (rc = cuda_error(cudaMalloc(&c->tgt_stats, st), "cudaMalloc tgt_stats")) ||
+        (rc = cuda_error(cudaMalloc(&c->row_tab, sizeof(int4) * g.H), "cudaMalloc row table")) ||
         (rc = cuda_error(cudaMalloc(&c->mom_part, sizeof(double) * 10 * kDtMaxBlocks), "cudaMalloc moments")) ||
         (rc = cuda_error(cudaMalloc(&c->res_dev, sizeof(stereo_dt_result)), "cudaMalloc result")) ||
         (rc = cuda_error(cudaMalloc(&c->dt_coef, 4 * sizeof(float)), "cudaMalloc coefficients")) ||
@@ -250,6 +252,7 @@ int stereo_cost_aggregate_wta(stereo_ctx *ctx, const uint8_t *ref, const uint8_t
         return set_error(STEREO_EINVAL, "stereo_cost_aggregate_wta: null pointer");
     cudaStream_t s = (cudaStream_t)stream;
     int rc = launch_prep(ctx, ref, tgtw, s);
+    if (!rc) rc = launch_row_tables(ctx, shift, s);
     if (rc) return rc;
     int slot = -1;
     if (ctx->prof_on && ctx->prof_n < kProfSlots) {
