@@ -168,6 +168,30 @@ int stereo_wta_volume(stereo_ctx *ctx, const float *agg_dev, const float *shift_
                       float *disp_dev, int32_t *wta_dev, float *best2_dev,
                       stereo_stream_t stream);
 
+/* ---------------------------------------------------- disparity transformation, no allocation
+ * The paper has no counterpart to this call: it exists for callers that cannot allocate
+ * device memory (a host framework that owns the whole device heap, a real-time loop that
+ * must never block in cudaMalloc, a plug-in forbidden to allocate after start-up).
+ * It computes exactly what stereo_disparity_transform computes, for a width x height map,
+ * with the search parameters passed directly instead of through a context, and calls no
+ * cudaMalloc, cudaFree or other allocating routine.  Its scratch (partial moments of up
+ * to 1024 blocks and the final coefficients, 80 KiB + 64 B) is a fixed array inside the
+ * library's device image, present on every device that loads the library until exit.
+ *   - The first call on each device looks up that array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call shares the one array and leaves its last contents there; nothing in it
+ *     needs to start at zero.  Calls whose kernels overlap on the GPU (other streams, other
+ *     host threads) race on it: serialise them.
+ *   - width, height must be 1..16384 (the same limit as stereo_create); larger maps are
+ *     rejected with STEREO_EINVAL.
+ * disp_dev, disp_out_dev: float [height][width]; mask_dev: uint8 or NULL; res_dev: a
+ * stereo_dt_result in device memory, or NULL.  Asynchronous on the stream. */
+int stereo_disparity_transform_noalloc(int32_t width, int32_t height, const float *disp_dev,
+                                       const uint8_t *mask_dev, double psi_init, float delta_t,
+                                       double lambda0, double delta_psi, int32_t max_iters,
+                                       float *disp_out_dev, stereo_dt_result *res_dev,
+                                       stereo_stream_t stream);
+
 /* ---------------------------------------------------------------- diagnostics */
 
 /* Synchronise the stream, read and clear the context's device status word.

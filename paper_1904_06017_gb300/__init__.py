@@ -22,6 +22,7 @@ __all__ = [
     "stereo_cost_volume", "stereo_aggregate_volume", "stereo_wta_volume",
     "stereo_check_device_status", "stereo_profile_enable", "stereo_profile_read",
     "stereo_fp32_peak_probe", "stereo_last_error", "stereo_version", "Stereo",
+    "stereo_disparity_transform_noalloc",
     "STEREO_OK", "STEREO_EINVAL", "STEREO_ENOMEM", "STEREO_ECUDA", "STEREO_ETIMEOUT",
     "STEREO_ENOCONV", "STEREO_ENOTSUP", "STEREO_F32", "STEREO_F16", "STEREO_BF16",
 ]
@@ -92,6 +93,7 @@ def load_library():
         "stereo_profile_enable": [P, I32],
         "stereo_profile_read": [P, P, P],
         "stereo_fp32_peak_probe": [I32, P, P],
+        "stereo_disparity_transform_noalloc": [I32, I32, P, P, D, F, D, D, I32, P, P, P],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -193,6 +195,20 @@ def stereo_disparity_transform(ctx, disp, mask, psi_init, delta_t, disp_out, res
     _check(lib.stereo_disparity_transform(ctx, _ptr(disp), _ptr(mask), float(psi_init), float(delta_t),
                                           _ptr(disp_out), _ptr(res), _stream(stream)))
     return None
+
+
+def stereo_disparity_transform_noalloc(width, height, disp, mask, psi_init, delta_t, disp_out,
+                                       res=None, lambda0=10.0, delta_psi=None, max_iters=100,
+                                       stream=None):
+    """The disparity transformation for callers that cannot allocate device memory:
+    no context, scratch in a fixed device array of the library (see include/stereo.h).
+    res: None, or a CUDA uint8 tensor of >= 48 bytes that receives the stereo_dt_result."""
+    import math
+    if delta_psi is None:
+        delta_psi = math.pi / 1.8e6
+    _check(load_library().stereo_disparity_transform_noalloc(
+        int(width), int(height), _ptr(disp), _ptr(mask), float(psi_init), float(delta_t),
+        float(lambda0), float(delta_psi), int(max_iters), _ptr(disp_out), _ptr(res), _stream(stream)))
 
 
 def stereo_cost_volume(ctx, ref, tgt_warped, cost, stream=None):

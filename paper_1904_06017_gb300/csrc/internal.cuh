@@ -83,4 +83,13 @@ int launch_dt(stereo_ctx *ctx, const float *disp, const uint8_t *mask, double ps
               float delta_t, float *out, stereo_dt_result *res_dev, cudaStream_t s);
 int run_fp32_probe(int blocks_per_sm, double *gflops_scalar, double *gflops_packed);
 
+// Kernels of the disparity transformation (k_dt.cu), shared with its no-allocation entry point.
+__global__ void k_dt_moments(const float *__restrict__ disp, const uint8_t *__restrict__ mask, int W, int H,
+                             double *__restrict__ part);
+__global__ void k_dt_solve(const double *__restrict__ part, int nblocks, int W, int H, double psi_init,
+                           double lambda0, double delta_psi, int max_iters, float delta_t,
+                           stereo_dt_result *__restrict__ res, float *__restrict__ coef);
+__global__ void k_dt_apply(const float *__restrict__ disp, int W, int H, const float *__restrict__ coef,
+                           float *__restrict__ out);
+
 }  // namespace sgb
