@@ -56,8 +56,10 @@ def dist_env():
 
 
 def kernel_sha():
-    p = os.path.join(ROOT, "paper_1904_06017_gb300", "csrc", "k_fused.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in ("k_fused.cuh", "k_fused_f32.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1904_06017_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 class ClockSampler:
@@ -213,7 +215,7 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     st = sg.Stereo(W, H, D, win=win, bil=bil, sigma0=p["sigma0"], sigma1=p["sigma1"], pitch=pitch)
     stream = torch.cuda.current_stream()
-    launches_per_step = 6   # k_warp, k_prep, k_fused, k_dt_moments, k_dt_solve, k_dt_apply
+    launches_per_step = 7   # k_warp, k_prep, k_row_tables, k_fused, k_dt_moments, k_dt_solve, k_dt_apply
 
     def step():
         st.warp_target(tgt, shift, tw)
@@ -282,6 +284,37 @@ def run_ours(args):
            "pairs_per_s": world * args.steps / (e_ms * 1e-3)}
     r = sg.stereo_dt_result.from_buffer_copy(res.cpu().numpy().tobytes()[:48])
 
+    # ---- cost-storage variants on the same pair: FP16 / BF16 storage vs the FP32 path
+    variants = {}
+    wta_ref = None
+    nvar = max(3, min(args.steps, 50))
+    for name, dtype in (("f32", sg.STEREO_F32), ("f16", sg.STEREO_F16), ("bf16", sg.STEREO_BF16)):
+        sv = sg.Stereo(W, H, D, win=win, bil=bil, sigma0=p["sigma0"], sigma1=p["sigma1"], pitch=pitch,
+                       cost_dtype=dtype)
+        wta_v = torch.empty((H, W), dtype=torch.int32, device=dev)
+        sv.warp_target(tgt, shift, tw)
+        sv.cost_aggregate_wta(ref, tw, shift, disp, wta_v, valid)
+        evv = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nvar)]
+        sg.stereo_profile_enable(sv.ctx, True)
+        for i in range(nvar):
+            flush.fill_(i & 0xFF)
+            evv[i][0].record(stream)
+            sv.warp_target(tgt, shift, tw)
+            sv.cost_aggregate_wta(ref, tw, shift, disp, None, valid)
+            sv.disparity_transform(disp, valid, 0.0, 0.0, out, res=res)
+            evv[i][1].record(stream)
+        torch.cuda.synchronize()
+        nf, fms = sg.stereo_profile_read(sv.ctx)
+        sv.check_device_status()
+        sv.close()
+        ms = sum(a.elapsed_time(b) for a, b in evv) / nvar
+        wv = wta_v.cpu().numpy()
+        if wta_ref is None:
+            wta_ref = wv
+        variants[name] = {"ms_per_step": ms, "pairs_per_s": 1e3 / ms, "gpix_disp_per_s": W * H * D / ms / 1e6,
+                          "fused_ms": fms / max(nf, 1), "steps": nvar,
+                          "wta_disagree_vs_f32": float(np.mean(wv != wta_ref))}
+
     if rank != 0:
         st.close()
         if world > 1:
@@ -309,7 +342,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "width": W, "height": H, "max_disp": D, "win": win, "bil": bil,
                        "pairs_per_step_per_gpu": 1, "l2": "flushed before each step (256 MiB write, untimed)"},
             "pairs_per_s": pairs_per_s, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-            "roofline": roof, "clocks": clk,
+            "roofline": roof, "clocks": clk, "cost_storage_variants": variants,
             "dt": {"psi": r.psi, "alpha0": r.alpha0, "alpha1": r.alpha1, "iters": r.iters, "status": r.status,
                    "true_roll": s.roll}}
     if not args.no_cpu_baseline and world == 1:

@@ -73,7 +73,7 @@ extern "C" int stereo_disparity_transform_noalloc(int32_t width, int32_t height,
     float *coef = reinterpret_cast<float *>(part + kNoAllocMoments);
     cudaStream_t s = (cudaStream_t)stream;
     const size_t N = (size_t)width * height;
-    int nb = (int)((N + (size_t)kDtThreads * 8 - 1) / ((size_t)kDtThreads * 8));
+    int nb = (int)((N + (size_t)kDtThreads * 32 - 1) / ((size_t)kDtThreads * 32));   // 32-pixel runs per thread
     if (nb > kDtMaxBlocks) nb = kDtMaxBlocks;
     // every partial block that the solve reads is written first by k_dt_moments, and the
     // coefficients are written by k_dt_solve before k_dt_apply reads them: nothing in the

@@ -30,6 +30,7 @@ constexpr int kDtMaxBlocks = 1024;   // partial-moment blocks of the disparity t
 struct Geometry {
     int W, H, pitch, D, rw, rb, m, n;
     int dc;            // disparities per chunk of the fused kernel
+    int esize;         // bytes per stored cost (4 for FP32, 2 for FP16 / BF16)
     int Dp;            // D rounded up to a multiple of dc
     int ntx, nty;      // tiles
     int pad_left, pad_top, pad_w, pad_h, pad_pitch;   // replicate-padded staging images

@@ -1,8 +1,10 @@
 // k_dt.cu -- disparity transformation (§3.3) on the device.
 //
-//  k_dt_moments: FP64 sums over the fitted pixels, with coordinates centred on the
-//      image middle (u~ = u - (W-1)/2, v~ = v - (H-1)/2) for conditioning:
-//      n, Su, Sv, Sd, Suu, Suv, Svv, Sud, Svd, Sdd; one partial per block.
+//  k_dt_moments: sums over the fitted pixels, with coordinates centred on the image
+//      middle (u~ = u - (W-1)/2, v~ = v - (H-1)/2) for conditioning:
+//      n, Su, Sv, Sd, Suu, Suv, Svv, Sud, Svd, Sdd -- FP32 within runs of 32 pixels
+//      (everything relative to the run's first fitted pixel), FP64 across runs, threads
+//      and blocks; one partial per block.
 //  k_dt_solve (one block): adds the partials in a fixed order, then one thread runs
 //      the roll search.  For a roll psi, with x = u cos + v sin (eq. x) and
 //      y = v cos - u sin (eq. y) and C.. the centred cross-products,
@@ -10,13 +12,23 @@
 //          E(psi) = C_dd - alpha1 C_yd                   (eq. E_min2)
 //          dE/dpsi = 2 alpha1 (C_xd - alpha1 C_xy)       (eq. d_e_min with eq. M)
 //      all from the ten moments.  The search (eq. e_min_gd, eq. adaptive_lambda) uses
-//      E / n with backtracking, psi wrapped into (-pi/2, pi/2] (eq. e_min_min).
+//      E / n with backtracking, psi wrapped into (-pi/2, pi/2] (eq. e_min_min); one warp
+//      evaluates 32 backtracking candidates at a time.
 //  k_dt_apply: eq. (disparity_transformation) for every pixel, FP32.
 #include "internal.cuh"
 
 namespace sgb {
 
 constexpr int kMom = 10;
+
+// A thread sums runs of kRun consecutive pixels.  Inside a run every quantity is taken
+// relative to the run's first fitted pixel (its column, row and disparity), so the FP32
+// sums are sums of small integers and small disparity offsets -- exact or all but exact;
+// each run is then shifted back to raw centred moments and added in FP64.  (The residual
+// energy of the fit is a small difference of large moments, so the moments must be far
+// more accurate than FP32 sums of raw values; GB300 runs FP64 at a small fraction of its
+// FP32 rate, so FP64 per pixel would make this kernel FP64-bound.)
+constexpr int kRun = 32;
 
 __global__ void __launch_bounds__(kDtThreads)
 k_dt_moments(const float *__restrict__ disp, const uint8_t *__restrict__ mask, int W, int H,
@@ -27,22 +39,58 @@ k_dt_moments(const float *__restrict__ disp, const uint8_t *__restrict__ mask, i
     for (int k = 0; k < kMom; ++k) m[k] = 0.0;
     const double uc = 0.5 * (W - 1), vc = 0.5 * (H - 1);
     const size_t N = (size_t)W * H;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
-        if (mask && !mask[i]) continue;
-        const float df = disp[i];
-        if (!isfinite(df)) continue;
-        const double d = df;
-        const double u = (double)(i % W) - uc, v = (double)(i / W) - vc;
-        m[0] += 1.0;
-        m[1] += u;
-        m[2] += v;
-        m[3] += d;
-        m[4] += u * u;
-        m[5] += u * v;
-        m[6] += v * v;
-        m[7] += u * d;
-        m[8] += v * d;
-        m[9] += d * d;
+    const size_t nrun = (N + kRun - 1) / kRun;
+    for (size_t run = (size_t)blockIdx.x * blockDim.x + threadIdx.x; run < nrun;
+         run += (size_t)gridDim.x * blockDim.x) {
+        const size_t i0 = run * kRun;
+        const int cnt = (int)min((size_t)kRun, N - i0);
+        float dref = 0.f;
+        int cref = 0, rref = 0;
+        bool have = false;
+        float n = 0.f, su = 0.f, sv = 0.f, se = 0.f, suu = 0.f, suv = 0.f, svv = 0.f, sue = 0.f, sve = 0.f,
+              see = 0.f;
+        int col = (int)(i0 % W), row = (int)(i0 / W);   // one division per run
+        for (int j = 0; j < cnt; ++j, ++col) {
+            if (col == W) {
+                col = 0;
+                ++row;
+            }
+            const size_t i = i0 + j;
+            if (mask && !mask[i]) continue;
+            const float d = disp[i];
+            if (!isfinite(d)) continue;
+            if (!have) {
+                dref = d;
+                cref = col;
+                rref = row;
+                have = true;
+            }
+            const float u = (float)(col - cref), v = (float)(row - rref), e = d - dref;
+            n += 1.f;
+            su += u;
+            sv += v;
+            se += e;
+            suu = fmaf(u, u, suu);
+            suv = fmaf(u, v, suv);
+            svv = fmaf(v, v, svv);
+            sue = fmaf(u, e, sue);
+            sve = fmaf(v, e, sve);
+            see = fmaf(e, e, see);
+        }
+        if (!have) continue;
+        // back to centred coordinates and raw disparities: x = x_local + x_ref
+        const double ur = cref - uc, vr = rref - vc, dr = dref;
+        const double N1 = n, Su = su, Sv = sv, Se = se;
+        m[0] += N1;
+        m[1] += Su + N1 * ur;
+        m[2] += Sv + N1 * vr;
+        m[3] += Se + N1 * dr;
+        m[4] += (double)suu + 2.0 * ur * Su + N1 * ur * ur;
+        m[5] += (double)suv + vr * Su + ur * Sv + N1 * ur * vr;
+        m[6] += (double)svv + 2.0 * vr * Sv + N1 * vr * vr;
+        m[7] += (double)sue + dr * Su + ur * Se + N1 * ur * dr;
+        m[8] += (double)sve + dr * Sv + vr * Se + N1 * vr * dr;
+        m[9] += (double)see + 2.0 * dr * Se + N1 * dr * dr;
     }
     __shared__ double red[kMom][kDtThreads];
 #pragma unroll
@@ -74,9 +122,10 @@ struct RollModel {
     }
 };
 
+// psi mapped into (-pi/2, pi/2] (E_t,min has period pi); one floor instead of an FP64 fmod
 __device__ double wrap_half_pi(double psi)
 {
-    psi = fmod(psi, M_PI);
+    if (psi > 0.5 * M_PI || psi <= -0.5 * M_PI) psi -= M_PI * floor(psi / M_PI + 0.5);
     if (psi > 0.5 * M_PI) psi -= M_PI;
     else if (psi <= -0.5 * M_PI) psi += M_PI;
     return psi;
@@ -103,12 +152,14 @@ k_dt_solve(const double *__restrict__ part, int nblocks, int W, int H, double ps
             for (int k = 0; k < kMom; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x >= 32) return;   // warp 0 runs the search, one candidate step per lane
+    const int lane = threadIdx.x;
     const double n = red[0][0], su = red[1][0], sv = red[2][0], sd = red[3][0];
     stereo_dt_result r;
     r.n = (int64_t)n;
     r.iters = 0;
     if (n < 2.0) {
+        if (lane != 0) return;
         r.psi = 0.0;
         r.alpha0 = n > 0 ? sd / n : 0.0;
         r.alpha1 = 0.0;
@@ -129,18 +180,34 @@ k_dt_solve(const double *__restrict__ part, int nblocks, int W, int H, double ps
     M.Cvd = red[8][0] - sv * sd / n;
     M.Cdd = red[9][0] - sd * sd / n;
 
+    // Every lane keeps the same search state.  A step is tried with rate lam; if the energy
+    // rises the rate is halved (backtracking, at most 60 times).  The 32 lanes evaluate the
+    // rates lam, lam/2, ..., lam/2^31 at once and the lowest lane whose energy does not rise
+    // wins -- the same choice as trying them one after another.
     double psi = wrap_half_pi(psi_init), lam = lambda0, E, g, a1;
     M.eval(psi, &E, &g, &a1);
     int status = STEREO_ENOCONV, it = 0;
     for (it = 1; it <= max_iters; ++it) {
-        double step = lam * g;
-        double psi_new = wrap_half_pi(psi - step), E_new, g_new, a1n;
-        M.eval(psi_new, &E_new, &g_new, &a1n);
-        for (int h = 0; h < 60 && E_new > E; ++h) {   // backtracking
-            lam *= 0.5;
-            step = lam * g;
-            psi_new = wrap_half_pi(psi - step);
-            M.eval(psi_new, &E_new, &g_new, &a1n);
+        double step = 0.0, psi_new = psi, E_new = E, g_new = g;
+        bool found = false;
+        for (int base = 0; base < 64 && !found; base += 32) {
+            const int h = base + lane;                    // halvings for this lane
+            const double lam_h = ldexp(lam, -h);
+            const double st = lam_h * g;
+            const double pn = wrap_half_pi(psi - st);
+            double En, gn, an;
+            M.eval(pn, &En, &gn, &an);
+            const bool ok = h == 60 || (h < 60 && !(En > E));   // after 60 halvings the step stands
+            const unsigned mask = __ballot_sync(0xffffffffu, ok && h <= 60);
+            if (mask) {
+                const int src = __ffs(mask) - 1;
+                step = __shfl_sync(0xffffffffu, st, src);
+                psi_new = __shfl_sync(0xffffffffu, pn, src);
+                E_new = __shfl_sync(0xffffffffu, En, src);
+                g_new = __shfl_sync(0xffffffffu, gn, src);
+                lam = ldexp(lam, -(base + src));
+                found = true;
+            }
         }
         const bool done = fabs(step) < delta_psi || g_new == 0.0 || g_new == g;
         const double lam_next = (g != g_new) ? lam * g / (g - g_new) : lam;   // eq. (adaptive_lambda)
@@ -153,6 +220,7 @@ k_dt_solve(const double *__restrict__ part, int nblocks, int W, int H, double ps
         }
         if (isfinite(lam_next) && lam_next > 0.0) lam = lam_next;
     }
+    if (lane != 0) return;
     if (it > max_iters) it = max_iters;
     M.eval(psi, &E, &g, &a1);
     double s, c;
@@ -189,7 +257,7 @@ int launch_dt(stereo_ctx *ctx, const float *disp, const uint8_t *mask, double ps
 {
     const Geometry &g = ctx->g;
     const size_t N = (size_t)g.W * g.H;
-    int nb = (int)((N + (size_t)kDtThreads * 8 - 1) / ((size_t)kDtThreads * 8));
+    int nb = (int)((N + (size_t)kDtThreads * kRun - 1) / ((size_t)kDtThreads * kRun));
     if (nb > kDtMaxBlocks) nb = kDtMaxBlocks;
     if (nb < 1) nb = 1;
     k_dt_moments<<<nb, kDtThreads, 0, s>>>(disp, mask, g.W, g.H, ctx->mom_part);

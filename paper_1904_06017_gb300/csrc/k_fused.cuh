@@ -1,4 +1,4 @@
-// k_fused.cu -- fused matching cost (eq. c) + bilateral aggregation (eq. omega_s,
+// k_fused.cuh -- fused matching cost (eq. c) + bilateral aggregation (eq. omega_s,
 // eq. fbs) + winner-take-all + parabola sub-pixel step (eq. subpixel), §3.2.
 //
 // One CTA (8 warps) owns a 64 x 32 block of output pixels and all D disparities:
@@ -21,6 +21,10 @@
 //  3. Epilogue: eq. (subpixel) on the winner's neighbours, add back s_i(v), write.
 // Normalising by sum_q w(p,q) is skipped: it is a positive per-pixel constant, so the
 // argmin and the (scale-free) parabola step do not change.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "internal.cuh"
 
 namespace sgb {
@@ -95,6 +99,53 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
+// Cost storage in shared memory: FP32, or FP16 / BF16 (rounded to nearest, widened back to
+// FP32 when loaded; aggregation always accumulates in FP32).  store4 writes the costs of
+// four consecutive disparities; load4 reads them back as two float2 pairs.
+template <typename T> struct CostStore;
+template <> struct CostStore<float> {
+    static __device__ __forceinline__ void store4(float *p, float4 c) { *reinterpret_cast<float4 *>(p) = c; }
+    static __device__ __forceinline__ void load4(const float *p, float2 &a, float2 &b)
+    {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        a = make_float2(v.x, v.y);
+        b = make_float2(v.z, v.w);
+    }
+};
+template <> struct CostStore<__half> {
+    static __device__ __forceinline__ void store4(__half *p, float4 c)
+    {
+        uint32_t lo, hi;
+        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(c.y), "f"(c.x));
+        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(c.w), "f"(c.z));
+        *reinterpret_cast<uint2 *>(p) = make_uint2(lo, hi);
+    }
+    static __device__ __forceinline__ void load4(const __half *p, float2 &a, float2 &b)
+    {
+        const uint2 v = *reinterpret_cast<const uint2 *>(p);
+        a = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
+        b = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
+    }
+};
+template <> struct CostStore<__nv_bfloat16> {
+    static __device__ __forceinline__ void store4(__nv_bfloat16 *p, float4 c)
+    {
+        uint32_t lo, hi;
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(c.y), "f"(c.x));
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(c.w), "f"(c.z));
+        *reinterpret_cast<uint2 *>(p) = make_uint2(lo, hi);
+    }
+    // a BF16 value is the top half of its FP32: byte moves only (no arithmetic pipe)
+    static __device__ __forceinline__ float lo_f(uint32_t w) { return __int_as_float(__byte_perm(w, 0, 0x1044)); }
+    static __device__ __forceinline__ float hi_f(uint32_t w) { return __int_as_float(w & 0xffff0000u); }
+    static __device__ __forceinline__ void load4(const __nv_bfloat16 *p, float2 &a, float2 &b)
+    {
+        const uint2 v = *reinterpret_cast<const uint2 *>(p);
+        a = make_float2(lo_f(v.x), hi_f(v.x));
+        b = make_float2(lo_f(v.y), hi_f(v.y));
+    }
+};
+
 // Shared-memory layout (offsets from the dynamic base, which is 128-byte aligned):
 //   sref  [box_h][ref_box_w] u8     reference tile (TMA)
 //   stgt  [box_h][tgt_box_w] u8     warped-target strip (TMA)
@@ -109,14 +160,14 @@ struct SmemLayout {
 };
 
 __host__ __device__ inline SmemLayout smem_layout(int rb, int m, int dc, int ref_box_w,
-                                                  int tgt_box_w, int box_h)
+                                                  int tgt_box_w, int box_h, int esize)
 {
     SmemLayout L;
     const int QH = kTileY + 2 * rb, QW = kTileX + 2 * rb, CW = kTileX + 2 * m, KB = 2 * rb + 1;
     L.sref = 0;
     L.stgt = align_up(L.sref + (size_t)box_h * ref_box_w, 128);
     L.cbuf = align_up(L.stgt + (size_t)box_h * tgt_box_w, 128);
-    L.vband = align_up(L.cbuf + (size_t)QH * QW * dc * 4, 128);
+    L.vband = align_up(L.cbuf + (size_t)QH * QW * dc * esize, 128);
     L.sstr = align_up(L.vband + (size_t)kBand * CW * dc * 4, 16);
     L.sstt = align_up(L.sstr + (size_t)kBand * QW * 8, 16);
     L.sI = align_up(L.sstt + (size_t)kBand * (QW + dc - 1) * 8, 16);
@@ -127,10 +178,6 @@ __host__ __device__ inline SmemLayout smem_layout(int rb, int m, int dc, int ref
     return L;
 }
 
-size_t fused_smem_bytes(const Geometry &g)
-{
-    return smem_layout(g.rb, g.m, g.dc, g.ref_box_w, g.tgt_box_w, g.box_h).total;
-}
 
 // The costs of one chunk of DC disparities at the tile plus its bilateral halo (QH x QW
 // positions), eq. (c), into cbuf[QH][QW][DC], band by band of kBand cost rows:
@@ -140,9 +187,9 @@ size_t fused_smem_bytes(const Geometry &g)
 //      c = 1 - (n S - S_ref S_tar) r_ref r_tar with the staged window statistics.
 // Every pass issues all of its shared-memory loads before its stores, so the loads of a
 // band are in flight together instead of waiting behind stores they might alias.
-template <int RB, int DC, int RW>
+template <int RB, int DC, int RW, typename T>
 __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sref, const uint8_t *stgt,
-                                           float *cbuf, int *vband, int2 *sstr, int2 *sstt,
+                                           T *cbuf, int *vband, int2 *sstr, int2 *sstt,
                                            int x0, int y0, int d0, int tid)
 {
     constexpr int WS = 2 * RW + 1;                    // block size w
@@ -279,16 +326,16 @@ __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sr
                     S.w += v[j + WS].w - v[j].w;
                 }
             }
-            float4 *co = reinterpret_cast<float4 *>(cbuf + (size_t)yq * crow) + dq;
+            T *co = cbuf + (size_t)yq * crow + 4 * dq;
 #pragma unroll
             for (int j = 0; j < kSeg; ++j)
-                if (j < nout) co[(xs + j) * NQ] = out[j];
+                if (j < nout) CostStore<T>::store4(co + (size_t)(xs + j) * DC, out[j]);
         }
         __syncthreads();
     }
 }
 
-template <int RB, int DC>
+template <int RB, int DC, typename T>
 __global__ void __launch_bounds__(kThreads, 1)
 k_fused(const __grid_constant__ CUtensorMap tmap_ref, const __grid_constant__ CUtensorMap tmap_tgt,
         const __grid_constant__ FusedArgs a)
@@ -302,10 +349,10 @@ k_fused(const __grid_constant__ CUtensorMap tmap_ref, const __grid_constant__ CU
 
     const int CW = kTileX + 2 * a.m;
     const int RP = a.ref_box_w, TP = a.tgt_box_w;
-    const SmemLayout L = smem_layout(RB, a.m, DC, RP, TP, a.box_h);
+    const SmemLayout L = smem_layout(RB, a.m, DC, RP, TP, a.box_h, (int)sizeof(T));
     uint8_t *sref = smem + L.sref;
     uint8_t *stgt = smem + L.stgt;
-    float *cbuf = reinterpret_cast<float *>(smem + L.cbuf);
+    T *cbuf = reinterpret_cast<T *>(smem + L.cbuf);
     int *vband = reinterpret_cast<int *>(smem + L.vband);
     int2 *sstr = reinterpret_cast<int2 *>(smem + L.sstr);
     int2 *sstt = reinterpret_cast<int2 *>(smem + L.sstt);
@@ -368,11 +415,11 @@ k_fused(const __grid_constant__ CUtensorMap tmap_ref, const __grid_constant__ CU
     for (int d0 = 0; d0 < a.D; d0 += DC) {
         // ---- 2a/2b. costs of the chunk (block radius dispatched to a compile-time value)
         switch (rw) {
-        case 1: cost_chunk<RB, DC, 1>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
-        case 2: cost_chunk<RB, DC, 2>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
-        case 3: cost_chunk<RB, DC, 3>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
-        case 4: cost_chunk<RB, DC, 4>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
-        default: cost_chunk<RB, DC, 5>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
+        case 1: cost_chunk<RB, DC, 1, T>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
+        case 2: cost_chunk<RB, DC, 2, T>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
+        case 3: cost_chunk<RB, DC, 3, T>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
+        case 4: cost_chunk<RB, DC, 4, T>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
+        default: cost_chunk<RB, DC, 5, T>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
         }
         // ---- 2c. bilateral aggregation of the chunk: each thread kPY pixels x DC d
         float2 acc[kPY][DC / 2];
@@ -384,13 +431,13 @@ k_fused(const __grid_constant__ CUtensorMap tmap_ref, const __grid_constant__ CU
             float Kr[KB];
 #pragma unroll
             for (int j = 0; j < KB; ++j) Kr[j] = sK[dx * KB + j];
-            const float *cb = cbuf + ((size_t)yt0 * QW + xt + dx) * DC;
+            const T *cb = cbuf + ((size_t)yt0 * QW + xt + dx) * DC;
             const float *ib = sI + yt0 * QW + xt + dx;
             // software pipeline over neighbour rows: while row r is accumulated, the
             // costs of row r+1 are in flight and its weights are being computed
-            float4 q[NQ];
+            float2 q[2 * NQ];
 #pragma unroll
-            for (int k = 0; k < NQ; ++k) q[k] = reinterpret_cast<const float4 *>(cb)[k];
+            for (int k = 0; k < NQ; ++k) CostStore<T>::load4(cb + 4 * k, q[2 * k], q[2 * k + 1]);
             float wgt[kPY];
             {
                 const float Iq = ib[0];
@@ -405,11 +452,12 @@ k_fused(const __grid_constant__ CUtensorMap tmap_ref, const __grid_constant__ CU
             }
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
-                float4 qn[NQ];
+                float2 qn[2 * NQ];
                 float wn[kPY];
                 if (r + 1 < NR) {
 #pragma unroll
-                    for (int k = 0; k < NQ; ++k) qn[k] = reinterpret_cast<const float4 *>(cb + (r + 1) * crow)[k];
+                    for (int k = 0; k < NQ; ++k)
+                        CostStore<T>::load4(cb + (r + 1) * crow + 4 * k, qn[2 * k], qn[2 * k + 1]);
                     const float Iq = ib[(r + 1) * QW];
 #pragma unroll
                     for (int i = 0; i < kPY; ++i) {
@@ -426,15 +474,12 @@ k_fused(const __grid_constant__ CUtensorMap tmap_ref, const __grid_constant__ CU
                     if (dy >= 0 && dy <= 2 * RB) {
                         const float2 w2 = make_float2(wgt[i], wgt[i]);
 #pragma unroll
-                        for (int k = 0; k < NQ; ++k) {
-                            acc[i][2 * k] = __ffma2_rn(w2, make_float2(q[k].x, q[k].y), acc[i][2 * k]);
-                            acc[i][2 * k + 1] = __ffma2_rn(w2, make_float2(q[k].z, q[k].w), acc[i][2 * k + 1]);
-                        }
+                        for (int k = 0; k < 2 * NQ; ++k) acc[i][k] = __ffma2_rn(w2, q[k], acc[i][k]);
                     }
                 }
                 if (r + 1 < NR) {
 #pragma unroll
-                    for (int k = 0; k < NQ; ++k) q[k] = qn[k];
+                    for (int k = 0; k < 2 * NQ; ++k) q[k] = qn[k];
 #pragma unroll
                     for (int i = 0; i < kPY; ++i) wgt[i] = wn[i];
                 }
@@ -484,75 +529,25 @@ k_fused(const __grid_constant__ CUtensorMap tmap_ref, const __grid_constant__ CU
 
 typedef void (*FusedKernel)(const CUtensorMap, const CUtensorMap, const FusedArgs);
 
-template <int DC>
-static FusedKernel pick_rb(int rb)
+template <int DC, typename T>
+FusedKernel pick_rb(int rb)
 {
     switch (rb) {
-    case 0: return k_fused<0, DC>;
-    case 1: return k_fused<1, DC>;
-    case 2: return k_fused<2, DC>;
-    case 3: return k_fused<3, DC>;
-    case 4: return k_fused<4, DC>;
-    case 5: return k_fused<5, DC>;
-    case 6: return k_fused<6, DC>;
-    case 7: return k_fused<7, DC>;
+    case 0: return k_fused<0, DC, T>;
+    case 1: return k_fused<1, DC, T>;
+    case 2: return k_fused<2, DC, T>;
+    case 3: return k_fused<3, DC, T>;
+    case 4: return k_fused<4, DC, T>;
+    case 5: return k_fused<5, DC, T>;
+    case 6: return k_fused<6, DC, T>;
+    case 7: return k_fused<7, DC, T>;
     }
     return nullptr;
 }
 
-static FusedKernel pick(const Geometry &g)
-{
-    if (g.dc == 12) return pick_rb<12>(g.rb);
-    if (g.dc == 4) return pick_rb<4>(g.rb);
-    return nullptr;
-}
-
-int fused_configure(stereo_ctx *ctx)
-{
-    FusedKernel k = pick(ctx->g);
-    if (!k) return set_error(STEREO_ENOTSUP, "no fused kernel for bil=%d dc=%d", ctx->p.bil, ctx->g.dc);
-    return cuda_error(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)ctx->g.smem_bytes),
-                      "cudaFuncSetAttribute(fused)");
-}
-
-int launch_fused(stereo_ctx *ctx, const float *shift, float *disp, int32_t *wta, uint8_t *valid,
-                 cudaStream_t s)
-{
-    const Geometry &g = ctx->g;
-    FusedKernel k = pick(g);
-    if (!k) return set_error(STEREO_ENOTSUP, "no fused kernel for bil=%d", ctx->p.bil);
-    FusedArgs a;
-    a.ref_stats = ctx->ref_stats;
-    a.tgt_stats = ctx->tgt_stats;
-    a.row_tab = ctx->row_tab;
-    (void)shift;
-    a.disp = disp;
-    a.wta = wta;
-    a.valid = valid;
-    a.status = ctx->status_dev;
-    a.W = g.W;
-    a.H = g.H;
-    a.D = g.D;
-    a.Dp = g.Dp;
-    a.rw = g.rw;
-    a.m = g.m;
-    a.n = g.n;
-    a.pad_left = g.pad_left;
-    a.pad_top = g.pad_top;
-    a.pad_w = g.pad_w;
-    a.ref_e = g.ref_e;
-    a.tgt_e = g.tgt_e;
-    a.ref_box_w = g.ref_box_w;
-    a.tgt_box_w = g.tgt_box_w;
-    a.box_h = g.box_h;
-    a.ref_box_x = g.pad_left - (int)align_up(g.m, 16);
-    a.iscale = ctx->iscale;
-    const int kb = 2 * g.rb + 1;
-    for (int i = 0; i < kb * kb; ++i) a.K[i] = ctx->kspatial[i];
-    dim3 grid(g.ntx, g.nty);
-    k<<<grid, kThreads, g.smem_bytes, s>>>(ctx->tmap_ref, ctx->tmap_tgt, a);
-    return cuda_error(cudaGetLastError(), "k_fused launch");
-}
+// One translation unit per cost-storage type (k_fused_f32.cu, k_fused_f16.cu, k_fused_bf16.cu).
+FusedKernel pick_fused_f32(int rb, int dc);
+FusedKernel pick_fused_f16(int rb, int dc);
+FusedKernel pick_fused_bf16(int rb, int dc);
 
 }  // namespace sgb

@@ -1,0 +1,79 @@
+// k_fused_f32.cu -- FP32 cost storage instantiations of the fused kernel, and the host
+// side shared by all storage types (shared-memory sizing, kernel choice, launch).
+#include "k_fused.cuh"
+
+namespace sgb {
+
+FusedKernel pick_fused_f32(int rb, int dc)
+{
+    if (dc == 12) return pick_rb<12, float>(rb);
+    if (dc == 4) return pick_rb<4, float>(rb);
+    return nullptr;
+}
+
+size_t fused_smem_bytes(const Geometry &g)
+{
+    return smem_layout(g.rb, g.m, g.dc, g.ref_box_w, g.tgt_box_w, g.box_h, g.esize).total;
+}
+
+static FusedKernel pick(const stereo_ctx *ctx)
+{
+    switch (ctx->p.cost_dtype) {
+    case STEREO_F32: return pick_fused_f32(ctx->g.rb, ctx->g.dc);
+    case STEREO_F16: return pick_fused_f16(ctx->g.rb, ctx->g.dc);
+    case STEREO_BF16: return pick_fused_bf16(ctx->g.rb, ctx->g.dc);
+    }
+    return nullptr;
+}
+
+int fused_configure(stereo_ctx *ctx)
+{
+    FusedKernel k = pick(ctx);
+    if (!k)
+        return set_error(STEREO_ENOTSUP, "no fused kernel for bil=%d dc=%d cost_dtype=%d", ctx->p.bil, ctx->g.dc,
+                         ctx->p.cost_dtype);
+    return cuda_error(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)ctx->g.smem_bytes),
+                      "cudaFuncSetAttribute(fused)");
+}
+
+int launch_fused(stereo_ctx *ctx, const float *shift, float *disp, int32_t *wta, uint8_t *valid,
+                 cudaStream_t s)
+{
+    (void)shift;   // the integer shifts come from the row table built by k_row_tables
+    const Geometry &g = ctx->g;
+    FusedKernel k = pick(ctx);
+    if (!k) return set_error(STEREO_ENOTSUP, "no fused kernel for bil=%d", ctx->p.bil);
+    FusedArgs a;
+    a.ref_stats = ctx->ref_stats;
+    a.tgt_stats = ctx->tgt_stats;
+    a.row_tab = ctx->row_tab;
+    a.disp = disp;
+    a.wta = wta;
+    a.valid = valid;
+    a.status = ctx->status_dev;
+    a.W = g.W;
+    a.H = g.H;
+    a.D = g.D;
+    a.Dp = g.Dp;
+    a.rw = g.rw;
+    a.m = g.m;
+    a.n = g.n;
+    a.pad_left = g.pad_left;
+    a.pad_top = g.pad_top;
+    a.pad_w = g.pad_w;
+    a.ref_e = g.ref_e;
+    a.tgt_e = g.tgt_e;
+    a.ref_box_w = g.ref_box_w;
+    a.tgt_box_w = g.tgt_box_w;
+    a.box_h = g.box_h;
+    a.ref_box_x = g.pad_left - (int)align_up(g.m, 16);
+    a.iscale = ctx->iscale;
+    const int kb = 2 * g.rb + 1;
+    for (int i = 0; i < kb * kb; ++i) a.K[i] = ctx->kspatial[i];
+    dim3 grid(g.ntx, g.nty);
+    k<<<grid, kThreads, g.smem_bytes, s>>>(ctx->tmap_ref, ctx->tmap_tgt, a);
+    return cuda_error(cudaGetLastError(), "k_fused launch");
+}
+
+}  // namespace sgb

@@ -43,6 +43,7 @@ static int geometry(const stereo_params &p, int dc, Geometry &g)
     g.m = g.rw + g.rb;
     g.n = p.win * p.win;
     g.dc = dc;
+    g.esize = p.cost_dtype == STEREO_F32 ? 4 : 2;
     g.Dp = round_up(g.D, dc);
     g.ntx = (g.W + kTileX - 1) / kTileX;
     g.nty = (g.H + kTileY - 1) / kTileY;
