@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     return ap.parse_args()
 
@@ -174,6 +175,64 @@ def run_reference(args):
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def bench_batch(args, dev, stream, flush):
+    """The batched workload: 64 pairs of uneven sizes and search ranges in one persistent
+    launch inside a captured CUDA graph (autotuned tiles), FP32 costs, and the same batch
+    with FP16 cost storage.  Its inputs (about 3 GB of images and staging) exceed L2."""
+    import numpy as np
+    import torch
+    import paper_1904_06017_gb300 as sg
+    import synth
+    scenes = synth.make_batch_scenes()
+    cfg = synth.CONFIGS["batch"]
+    pairs = []
+    for s in scenes:
+        H, W, D = s.height, s.width, s.params["D"]
+        pitch = (W + 15) // 16 * 16
+        def img(a):
+            t = torch.zeros((H, pitch), dtype=torch.uint8)
+            t[:, :W] = torch.from_numpy(a)
+            return t.to(dev)
+        pairs.append(dict(ref=img(s.ref), tgt=img(s.tgt), shift=torch.from_numpy(s.shift).to(dev),
+                          tgt_warped=torch.empty((H, pitch), dtype=torch.uint8, device=dev),
+                          disp=torch.empty((H, W), dtype=torch.float32, device=dev),
+                          valid=torch.empty((H, W), dtype=torch.uint8, device=dev),
+                          disp_out=torch.empty((H, W), dtype=torch.float32, device=dev),
+                          res=torch.zeros(64, dtype=torch.uint8, device=dev), max_disp=D))
+    units = sum(s.height * s.width * s.params["D"] for s in scenes)
+    out = {"pairs": len(scenes), "sizes": sorted({"%dx%d" % (s.width, s.height) for s in scenes}),
+           "search_ranges": sorted({s.params["D"] for s in scenes}), "win": cfg["win"], "bil": cfg["bil"]}
+    steps = max(3, min(args.steps, 20))
+    disp32 = None
+    for name, dtype in (("f32", sg.STEREO_F32), ("f16", sg.STEREO_F16)):
+        b = sg.StereoBatch(pairs, win=cfg["win"], bil=cfg["bil"], sigma0=cfg["sigma0"], sigma1=cfg["sigma1"],
+                           cost_dtype=dtype)
+        for _ in range(2):
+            b.run(stream)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            ev[i][0].record(stream)
+            b.run(stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        b.check_device_status()
+        ms = sum(a.elapsed_time(c) for a, c in ev) / steps
+        disp = [q["disp"].cpu().numpy() for q in pairs]
+        rec = {"ms_per_batch": ms, "pairs_per_s": len(scenes) * 1e3 / ms,
+               "gpix_disp_per_s": units / ms / 1e6, "graph_runs": steps, "tiles": b.config()}
+        if disp32 is None:
+            disp32 = disp
+        else:
+            moved = sum(int(np.count_nonzero(np.abs(a - c) > 0.5)) for a, c in zip(disp32, disp))
+            rec["disp_diff_gt_half_px_vs_f32"] = moved / sum(a.size for a in disp32)
+        out[name] = rec
+        b.close()
+    del pairs
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_ours(args):
@@ -345,6 +404,11 @@ def run_ours(args):
             "roofline": roof, "clocks": clk, "cost_storage_variants": variants,
             "dt": {"psi": r.psi, "alpha0": r.alpha0, "alpha1": r.alpha1, "iters": r.iters, "status": r.status,
                    "true_roll": s.roll}}
+    if not args.no_batch:
+        try:
+            line["batch"] = bench_batch(args, dev, stream, flush)
+        except Exception as exc:   # the headline line above stands on its own
+            line["batch"] = {"error": str(exc)[:300]}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline_sample(s, args.cpu_seconds)
     st.close()

@@ -168,6 +168,67 @@ int stereo_wta_volume(stereo_ctx *ctx, const float *agg_dev, const float *shift_
                       float *disp_dev, int32_t *wta_dev, float *best2_dev,
                       stereo_stream_t stream);
 
+/* ---------------------------------------------------------------- batches of pairs
+ * Many stereo pairs of uneven sizes and search ranges, processed as one unit (not in the
+ * paper; a throughput form of the same per-pair path).  A batch runs, for every pair, the
+ * warp (§3.1), the fused cost/aggregation/WTA/sub-pixel step (§3.2) and the disparity
+ * transformation (§3.3), with the fused step of all pairs in ONE persistent launch that
+ * takes (pair, tile) work items heaviest first from a device counter.  The whole batch is
+ * captured once into a CUDA graph at creation and replayed by stereo_batch_run.
+ * The pairs' buffers are fixed at creation (the graph reads and writes them): change the
+ * image contents between runs, not the pointers. */
+typedef struct {
+    int32_t width, height, pitch, max_disp;   /* as in stereo_params, per pair */
+    const uint8_t *ref_dev;                   /* [H][pitch] reference */
+    const uint8_t *tgt_dev;                   /* [H][pitch] target (warped inside the batch) */
+    const float *shift_dev;                   /* [H] row shift s(v) */
+    uint8_t *tgt_warped_dev;                  /* [H][pitch] scratch for the warped target */
+    float *disp_dev;                          /* [H][W] disparity (output) */
+    uint8_t *valid_dev;                       /* [H][W] validity mask (output; also the fit mask) */
+    float *disp_out_dev;                      /* [H][W] transformed disparity (output) */
+    stereo_dt_result *res_dev;                /* device result of the transformation (output) */
+    double psi_init;                          /* roll search start */
+    float delta_t;                            /* eq. (disparity_transformation) offset */
+} stereo_pair_desc;
+
+typedef struct {
+    int32_t win, bil;          /* shared by all pairs */
+    float sigma0, sigma1;
+    int32_t cost_dtype;        /* STEREO_F32 | STEREO_F16 | STEREO_BF16 */
+    double lambda0, delta_psi;
+    int32_t max_iters;
+    int32_t tile_wc;           /* warp columns of a tile (1: 32x64, 2: 64x32, 4: 128x16); 0 = autotune */
+    int32_t tile_dc;           /* disparities per chunk (12 or 4); 0 = autotune */
+} stereo_batch_params;
+
+typedef struct stereo_batch stereo_batch;
+
+/* Defaults: the stereo_params_default values, autotuned tiles (tile_wc = tile_dc = 0). */
+int stereo_batch_params_default(stereo_batch_params *p);
+
+/* Create a batch of n pairs (pairs_host: n descriptors in host memory, copied).  With
+ * tile_wc or tile_dc 0 the tile shape and chunk size are chosen by timing every candidate
+ * on this batch (the candidates write into the pairs' output buffers); the choice is
+ * cached in the JSON file named by the environment variable STEREO_AUTOTUNE_CACHE, keyed
+ * by the pair sizes, search ranges, windows, storage type and SM count.  Allocates the
+ * per-pair staging buffers and captures the CUDA graph.  Synchronous. */
+int stereo_batch_create(const stereo_batch_params *p, int32_t n, const stereo_pair_desc *pairs_host,
+                        stereo_batch **out);
+
+/* Launch the batch's graph on the stream (asynchronous). */
+int stereo_batch_run(stereo_batch *b, stereo_stream_t stream);
+
+/* The tile configuration in use, the number of work items, and whether it came from the
+ * autotuner cache (1), from timing (2) or from the parameters (0). */
+int stereo_batch_config(const stereo_batch *b, int32_t *tile_wc, int32_t *tile_dc, int32_t *n_items,
+                        int32_t *source);
+
+/* Synchronise the device, read and clear every pair's device status word. */
+int stereo_batch_check_device_status(stereo_batch *b);
+
+/* Free the batch (synchronises the device).  NULL is a no-op. */
+int stereo_batch_destroy(stereo_batch *b);
+
 /* ---------------------------------------------------- disparity transformation, no allocation
  * The paper has no counterpart to this call: it exists for callers that cannot allocate
  * device memory (a host framework that owns the whole device heap, a real-time loop that

@@ -22,7 +22,9 @@ __all__ = [
     "stereo_cost_volume", "stereo_aggregate_volume", "stereo_wta_volume",
     "stereo_check_device_status", "stereo_profile_enable", "stereo_profile_read",
     "stereo_fp32_peak_probe", "stereo_last_error", "stereo_version", "Stereo",
-    "stereo_disparity_transform_noalloc",
+    "stereo_disparity_transform_noalloc", "stereo_pair_desc", "stereo_batch_params",
+    "stereo_batch_params_default", "stereo_batch_create", "stereo_batch_run", "stereo_batch_config",
+    "stereo_batch_check_device_status", "stereo_batch_destroy", "StereoBatch",
     "STEREO_OK", "STEREO_EINVAL", "STEREO_ENOMEM", "STEREO_ECUDA", "STEREO_ETIMEOUT",
     "STEREO_ENOCONV", "STEREO_ENOTSUP", "STEREO_F32", "STEREO_F16", "STEREO_BF16",
 ]
@@ -64,6 +66,22 @@ class stereo_dt_result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class stereo_pair_desc(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("pitch", ctypes.c_int32),
+                ("max_disp", ctypes.c_int32), ("ref_dev", ctypes.c_void_p), ("tgt_dev", ctypes.c_void_p),
+                ("shift_dev", ctypes.c_void_p), ("tgt_warped_dev", ctypes.c_void_p),
+                ("disp_dev", ctypes.c_void_p), ("valid_dev", ctypes.c_void_p),
+                ("disp_out_dev", ctypes.c_void_p), ("res_dev", ctypes.c_void_p),
+                ("psi_init", ctypes.c_double), ("delta_t", ctypes.c_float)]
+
+
+class stereo_batch_params(ctypes.Structure):
+    _fields_ = [("win", ctypes.c_int32), ("bil", ctypes.c_int32), ("sigma0", ctypes.c_float),
+                ("sigma1", ctypes.c_float), ("cost_dtype", ctypes.c_int32), ("lambda0", ctypes.c_double),
+                ("delta_psi", ctypes.c_double), ("max_iters", ctypes.c_int32), ("tile_wc", ctypes.c_int32),
+                ("tile_dc", ctypes.c_int32)]
+
+
 def library_path() -> str:
     return _LIB_PATH
 
@@ -94,6 +112,12 @@ def load_library():
         "stereo_profile_read": [P, P, P],
         "stereo_fp32_peak_probe": [I32, P, P],
         "stereo_disparity_transform_noalloc": [I32, I32, P, P, D, F, D, D, I32, P, P, P],
+        "stereo_batch_params_default": [P],
+        "stereo_batch_create": [P, I32, P, P],
+        "stereo_batch_run": [P, P],
+        "stereo_batch_config": [P, P, P, P, P],
+        "stereo_batch_check_device_status": [P],
+        "stereo_batch_destroy": [P],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -296,3 +320,89 @@ class Stereo:
 
     def check_device_status(self, stream=None):
         stereo_check_device_status(self.ctx, stream)
+
+
+# ---------------------------------------------------------------------------- batches
+
+def stereo_batch_params_default(**overrides) -> stereo_batch_params:
+    p = stereo_batch_params()
+    _check(load_library().stereo_batch_params_default(ctypes.byref(p)))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def stereo_batch_create(params: stereo_batch_params, pairs):
+    """pairs: a sequence of stereo_pair_desc (device pointers filled in)."""
+    arr = (stereo_pair_desc * len(pairs))(*pairs)
+    b = ctypes.c_void_p()
+    _check(load_library().stereo_batch_create(ctypes.byref(params), len(pairs), arr, ctypes.byref(b)))
+    return b
+
+
+def stereo_batch_run(batch, stream=None):
+    _check(load_library().stereo_batch_run(batch, _stream(stream)))
+
+
+def stereo_batch_config(batch):
+    wc, dc, n, src = (ctypes.c_int32() for _ in range(4))
+    _check(load_library().stereo_batch_config(batch, ctypes.byref(wc), ctypes.byref(dc), ctypes.byref(n),
+                                              ctypes.byref(src)))
+    return {"tile_wc": wc.value, "tile_dc": dc.value, "items": n.value,
+            "source": {0: "parameters", 1: "autotune cache", 2: "autotune timing"}[src.value]}
+
+
+def stereo_batch_check_device_status(batch):
+    _check(load_library().stereo_batch_check_device_status(batch))
+
+
+def stereo_batch_destroy(batch):
+    _check(load_library().stereo_batch_destroy(batch))
+
+
+class StereoBatch:
+    """Owns one batch.  ``pairs`` is a list of dicts of CUDA tensors with keys ref, tgt,
+    shift, tgt_warped, disp, valid, disp_out, res (uint8 tensor of >= 48 bytes) and ints
+    max_disp (and optionally psi_init, delta_t); images are [H][pitch] uint8 tensors."""
+
+    def __init__(self, pairs, win=9, bil=11, sigma0=1.5, sigma1=5.5, cost_dtype=STEREO_F32,
+                 tile_wc=0, tile_dc=0, **extra):
+        self.params = stereo_batch_params_default(win=win, bil=bil, sigma0=sigma0, sigma1=sigma1,
+                                                  cost_dtype=cost_dtype, tile_wc=tile_wc,
+                                                  tile_dc=tile_dc, **extra)
+        descs = []
+        for q in pairs:
+            H, pitch = q["ref"].shape
+            W = q["disp"].shape[1]
+            descs.append(stereo_pair_desc(W, H, pitch, int(q["max_disp"]), _ptr(q["ref"]), _ptr(q["tgt"]),
+                                          _ptr(q["shift"]), _ptr(q["tgt_warped"]), _ptr(q["disp"]),
+                                          _ptr(q["valid"]), _ptr(q["disp_out"]), _ptr(q["res"]),
+                                          float(q.get("psi_init", 0.0)), float(q.get("delta_t", 0.0))))
+        self.pairs = pairs      # keep the tensors alive
+        self.batch = stereo_batch_create(self.params, descs)
+
+    def run(self, stream=None):
+        stereo_batch_run(self.batch, stream)
+
+    def config(self):
+        return stereo_batch_config(self.batch)
+
+    def check_device_status(self):
+        stereo_batch_check_device_status(self.batch)
+
+    def close(self):
+        if getattr(self, "batch", None) is not None:
+            stereo_batch_destroy(self.batch)
+            self.batch = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -12,12 +12,15 @@
 
 namespace sgb {
 
-// Tiling of the fused kernel: a CTA of 8 warps owns a kTileX x kTileY block of output
-// pixels; lane = column, each warp covers 32 columns x kPY rows.
-constexpr int kTileX = 64;
+// Tiling of the fused kernel: a CTA of 8 warps owns a tile of output pixels; lane =
+// column, each warp covers 32 columns x kPY rows, and WC warp columns x (8 / WC) warp rows
+// give tiles of 32 x 64 (WC = 1), 64 x 32 (WC = 2, the default) or 128 x 16 (WC = 4).
 constexpr int kPY = 8;
-constexpr int kTileY = 4 * kPY;
-constexpr int kThreads = 256;
+constexpr int kWarps = 8;
+constexpr int kThreads = 32 * kWarps;
+constexpr int kDefaultWC = 2;
+__host__ __device__ constexpr int tile_x(int wc) { return 32 * wc; }
+__host__ __device__ constexpr int tile_y(int wc) { return kPY * (kWarps / wc); }
 constexpr int kMaxRB = 7;          // bil <= 15
 constexpr int kMaxRW = 5;          // win <= 11
 constexpr int kMaxD = 256;
@@ -30,6 +33,8 @@ constexpr int kDtMaxBlocks = 1024;   // partial-moment blocks of the disparity t
 struct Geometry {
     int W, H, pitch, D, rw, rb, m, n;
     int dc;            // disparities per chunk of the fused kernel
+    int wc;            // warp columns of a fused-kernel tile (tile_x(wc) x tile_y(wc) pixels)
+    int tx, ty;        // tile size
     int esize;         // bytes per stored cost (4 for FP32, 2 for FP16 / BF16)
     int Dp;            // D rounded up to a multiple of dc
     int ntx, nty;      // tiles
@@ -75,6 +80,10 @@ int launch_fused(stereo_ctx *ctx, const float *shift, float *disp, int32_t *wta,
                  cudaStream_t s);
 size_t fused_smem_bytes(const Geometry &g);
 int fused_configure(stereo_ctx *ctx);
+int compute_geometry(const stereo_params &p, int dc, int wc, Geometry &g);
+// Context creation with a given (disparities per chunk, warp columns); 0 = default choice.
+int create_context(const stereo_params *p, int dc, int wc, stereo_ctx **out);
+int max_smem_optin();
 int launch_cost_volume(stereo_ctx *ctx, float *cost, cudaStream_t s);
 int launch_aggregate_volume(stereo_ctx *ctx, const uint8_t *ref, const float *cost, float *agg,
                             cudaStream_t s);

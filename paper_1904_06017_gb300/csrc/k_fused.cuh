@@ -44,6 +44,16 @@ struct FusedArgs {
     float K[(2 * kMaxRB + 1) * (2 * kMaxRB + 1)];
 };
 
+// Everything one pair needs: its two tensor maps (replicate-padded reference and warped
+// target) and its arguments.  A single-pair launch passes one as a __grid_constant__
+// parameter; a batch passes a device array of them.
+struct PairDesc {
+    CUtensorMap tmap_ref;
+    CUtensorMap tmap_tgt;
+    FusedArgs a;
+    int ntx, nty;   // tiles in x and y
+};
+
 constexpr int kBand = 6;   // cost rows per band of the two-pass window sums
 constexpr int kSeg = 7;    // cost columns per horizontal-pass work item
 
@@ -160,10 +170,10 @@ struct SmemLayout {
 };
 
 __host__ __device__ inline SmemLayout smem_layout(int rb, int m, int dc, int ref_box_w,
-                                                  int tgt_box_w, int box_h, int esize)
+                                                  int tgt_box_w, int box_h, int esize, int tx, int ty)
 {
     SmemLayout L;
-    const int QH = kTileY + 2 * rb, QW = kTileX + 2 * rb, CW = kTileX + 2 * m, KB = 2 * rb + 1;
+    const int QH = ty + 2 * rb, QW = tx + 2 * rb, CW = tx + 2 * m, KB = 2 * rb + 1;
     L.sref = 0;
     L.stgt = align_up(L.sref + (size_t)box_h * ref_box_w, 128);
     L.cbuf = align_up(L.stgt + (size_t)box_h * tgt_box_w, 128);
@@ -187,14 +197,14 @@ __host__ __device__ inline SmemLayout smem_layout(int rb, int m, int dc, int ref
 //      c = 1 - (n S - S_ref S_tar) r_ref r_tar with the staged window statistics.
 // Every pass issues all of its shared-memory loads before its stores, so the loads of a
 // band are in flight together instead of waiting behind stores they might alias.
-template <int RB, int DC, int RW, typename T>
+template <int RB, int DC, int RW, typename T, int TX, int TY>
 __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sref, const uint8_t *stgt,
                                            T *cbuf, int *vband, int2 *sstr, int2 *sstt,
                                            int x0, int y0, int d0, int tid)
 {
     constexpr int WS = 2 * RW + 1;                    // block size w
-    constexpr int QH = kTileY + 2 * RB, QW = kTileX + 2 * RB;
-    constexpr int CW = kTileX + 2 * (RW + RB);        // product columns
+    constexpr int QH = TY + 2 * RB, QW = TX + 2 * RB;
+    constexpr int CW = TX + 2 * (RW + RB);            // product columns
     constexpr int NQ = DC / 4;
     constexpr int NSEG = (QW + kSeg - 1) / kSeg;
     constexpr int NWV = (CW * DC + kThreads - 1) / kThreads;   // vertical walkers per thread
@@ -335,53 +345,90 @@ __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sr
     }
 }
 
-template <int RB, int DC, typename T>
+template <int RB, int DC, typename T, int WC>
 __global__ void __launch_bounds__(kThreads, 1)
-k_fused(const __grid_constant__ CUtensorMap tmap_ref, const __grid_constant__ CUtensorMap tmap_tgt,
-        const __grid_constant__ FusedArgs a)
+k_fused(const __grid_constant__ PairDesc single, const PairDesc *__restrict__ pairs,
+        const int2 *__restrict__ items, int nitems, int *__restrict__ counter)
 {
     static_assert(DC % 4 == 0, "DC must be a multiple of 4");
+    constexpr int TX = tile_x(WC), TY = tile_y(WC);
     constexpr int KB = 2 * RB + 1;
-    constexpr int QH = kTileY + 2 * RB, QW = kTileX + 2 * RB;
+    constexpr int QH = TY + 2 * RB, QW = TX + 2 * RB;
     constexpr int NR = kPY + 2 * RB;   // neighbour rows seen by one thread's pixel column
     constexpr int NQ = DC / 4;         // disparity quads per chunk
     extern __shared__ __align__(128) uint8_t smem[];
-
-    const int CW = kTileX + 2 * a.m;
-    const int RP = a.ref_box_w, TP = a.tgt_box_w;
-    const SmemLayout L = smem_layout(RB, a.m, DC, RP, TP, a.box_h, (int)sizeof(T));
-    uint8_t *sref = smem + L.sref;
-    uint8_t *stgt = smem + L.stgt;
-    T *cbuf = reinterpret_cast<T *>(smem + L.cbuf);
-    int *vband = reinterpret_cast<int *>(smem + L.vband);
-    int2 *sstr = reinterpret_cast<int2 *>(smem + L.sstr);
-    int2 *sstt = reinterpret_cast<int2 *>(smem + L.sstt);
-    float *sI = reinterpret_cast<float *>(smem + L.sI);
-    float *sK = reinterpret_cast<float *>(smem + L.sK);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);
-    int *flag = reinterpret_cast<int *>(smem + L.flag);
+    __shared__ __align__(16) FusedArgs s_args;
+    __shared__ int s_item;
+    // the mbarrier and the wait flag live at fixed addresses: the dynamic layout moves with
+    // each tile's pair (its search range sets the width of the target strip)
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ int s_flag;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
-
-    // ---- 1. stage the image tiles with TMA
+    const FusedArgs &a = s_args;
+    uint64_t *bar = &s_bar;
+    int *flag = &s_flag;
     if (tid == 0) mbar_init(bar, 1);
-    for (int i = tid; i < KB * KB; i += kThreads) sK[i] = a.K[i];
-    __syncthreads();
-    if (tid == 0) {
-        mbar_expect_tx(bar, (uint32_t)(a.box_h * (RP + TP)));
-        tma_load_3d(sref, &tmap_ref, 0, (x0 + a.ref_box_x) / 16, y0, bar);
-        tma_load_3d(stgt, &tmap_tgt, 0, x0 / 16, y0, bar);
-        // bounded wait (about a second of clock cycles), then give up with a status flag
-        const long long t0 = clock64();
-        bool ok = false;
-        while (!(ok = mbar_try_wait(bar, 0)) && clock64() - t0 < (1ll << 31)) {
+
+    // Tiles: a single pair walks its tiles in a fixed order (blockIdx.x, + gridDim.x, ...);
+    // a batch claims work-list items (pair, tile) with an atomic counter, heaviest first.
+    for (int iter = 0;; ++iter) {
+        if (tid == 0) s_item = pairs ? atomicAdd(counter, 1) : (int)blockIdx.x + iter * (int)gridDim.x;
+        __syncthreads();
+        const int item = s_item;
+        if (item >= nitems) return;
+        int p = 0, tx, ty;
+        if (pairs) {
+            const int2 it = items[item];
+            p = it.x;
+            tx = it.y & 0xffff;
+            ty = it.y >> 16;
+        } else {
+            tx = item % single.ntx;
+            ty = item / single.ntx;
         }
-        *flag = ok ? 1 : 0;
-        if (!ok) atomicOr(a.status, 1);
-    }
-    __syncthreads();
-    if (*flag == 0) return;
+        const PairDesc *pd = pairs ? pairs + p : &single;
+        {
+            const int *src = reinterpret_cast<const int *>(&pd->a);
+            int *dst = reinterpret_cast<int *>(&s_args);
+            for (int i = tid; i < (int)(sizeof(FusedArgs) / 4); i += kThreads) dst[i] = src[i];
+        }
+        __syncthreads();
+
+        const int CW = TX + 2 * a.m;
+        const int RP = a.ref_box_w, TP = a.tgt_box_w;
+        const SmemLayout L = smem_layout(RB, a.m, DC, RP, TP, a.box_h, (int)sizeof(T), TX, TY);
+        uint8_t *sref = smem + L.sref;
+        uint8_t *stgt = smem + L.stgt;
+        T *cbuf = reinterpret_cast<T *>(smem + L.cbuf);
+        int *vband = reinterpret_cast<int *>(smem + L.vband);
+        int2 *sstr = reinterpret_cast<int2 *>(smem + L.sstr);
+        int2 *sstt = reinterpret_cast<int2 *>(smem + L.sstt);
+        float *sI = reinterpret_cast<float *>(smem + L.sI);
+        float *sK = reinterpret_cast<float *>(smem + L.sK);
+        (void)CW;
+        const int x0 = tx * TX, y0 = ty * TY;
+
+        // ---- 1. stage the image tiles with TMA (the mbarrier completes once per tile)
+        for (int i = tid; i < KB * KB; i += kThreads) sK[i] = a.K[i];
+        __syncthreads();
+        if (tid == 0) {
+            // the previous tile's ordinary shared-memory accesses (ordered by the barrier
+            // above) come before the tensor copies that overwrite the same bytes
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(bar, (uint32_t)(a.box_h * (RP + TP)));
+            tma_load_3d(sref, &pd->tmap_ref, 0, (x0 + a.ref_box_x) / 16, y0, bar);
+            tma_load_3d(stgt, &pd->tmap_tgt, 0, x0 / 16, y0, bar);
+            // bounded wait (about a second of clock cycles), then give up with a status flag
+            const long long t0 = clock64();
+            bool ok = false;
+            while (!(ok = mbar_try_wait(bar, (uint32_t)(iter & 1))) && clock64() - t0 < (1ll << 31)) {
+            }
+            *flag = ok ? 1 : 0;
+            if (!ok) atomicOr(a.status, 1);
+        }
+        __syncthreads();
+        if (*flag == 0) return;
 
     const int rw = a.rw;
     // scaled reference intensities of the cost positions (tile + bilateral halo); a
@@ -396,8 +443,8 @@ k_fused(const __grid_constant__ CUtensorMap tmap_ref, const __grid_constant__ CU
     }
     __syncthreads();
 
-    const int xt = (warp & 1) * 32 + lane;
-    const int yt0 = (warp >> 1) * kPY;
+    const int xt = (warp % WC) * 32 + lane;
+    const int yt0 = (warp / WC) * kPY;
     float Ip[kPY];
 #pragma unroll
     for (int i = 0; i < kPY; ++i) Ip[i] = sI[(yt0 + i + RB) * QW + xt + RB];
@@ -415,11 +462,11 @@ k_fused(const __grid_constant__ CUtensorMap tmap_ref, const __grid_constant__ CU
     for (int d0 = 0; d0 < a.D; d0 += DC) {
         // ---- 2a/2b. costs of the chunk (block radius dispatched to a compile-time value)
         switch (rw) {
-        case 1: cost_chunk<RB, DC, 1, T>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
-        case 2: cost_chunk<RB, DC, 2, T>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
-        case 3: cost_chunk<RB, DC, 3, T>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
-        case 4: cost_chunk<RB, DC, 4, T>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
-        default: cost_chunk<RB, DC, 5, T>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
+        case 1: cost_chunk<RB, DC, 1, T, TX, TY>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
+        case 2: cost_chunk<RB, DC, 2, T, TX, TY>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
+        case 3: cost_chunk<RB, DC, 3, T, TX, TY>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
+        case 4: cost_chunk<RB, DC, 4, T, TX, TY>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
+        default: cost_chunk<RB, DC, 5, T, TX, TY>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
         }
         // ---- 2c. bilateral aggregation of the chunk: each thread kPY pixels x DC d
         float2 acc[kPY][DC / 2];
@@ -525,29 +572,35 @@ k_fused(const __grid_constant__ CUtensorMap tmap_ref, const __grid_constant__ CU
             a.valid[o] = (uint8_t)(v >= a.m && v <= a.H - 1 - a.m && u >= ulo && u <= uhi);
         }
     }
+    }  // tile loop
 }
 
-typedef void (*FusedKernel)(const CUtensorMap, const CUtensorMap, const FusedArgs);
+typedef void (*FusedKernel)(const PairDesc, const PairDesc *, const int2 *, int, int *);
 
-template <int DC, typename T>
+template <int DC, typename T, int WC>
 FusedKernel pick_rb(int rb)
 {
     switch (rb) {
-    case 0: return k_fused<0, DC, T>;
-    case 1: return k_fused<1, DC, T>;
-    case 2: return k_fused<2, DC, T>;
-    case 3: return k_fused<3, DC, T>;
-    case 4: return k_fused<4, DC, T>;
-    case 5: return k_fused<5, DC, T>;
-    case 6: return k_fused<6, DC, T>;
-    case 7: return k_fused<7, DC, T>;
+    case 0: return k_fused<0, DC, T, WC>;
+    case 1: return k_fused<1, DC, T, WC>;
+    case 2: return k_fused<2, DC, T, WC>;
+    case 3: return k_fused<3, DC, T, WC>;
+    case 4: return k_fused<4, DC, T, WC>;
+    case 5: return k_fused<5, DC, T, WC>;
+    case 6: return k_fused<6, DC, T, WC>;
+    case 7: return k_fused<7, DC, T, WC>;
     }
     return nullptr;
 }
 
-// One translation unit per cost-storage type (k_fused_f32.cu, k_fused_f16.cu, k_fused_bf16.cu).
-FusedKernel pick_fused_f32(int rb, int dc);
-FusedKernel pick_fused_f16(int rb, int dc);
-FusedKernel pick_fused_bf16(int rb, int dc);
+// Kernel choice by (bilateral radius, disparities per chunk, warp columns); one translation
+// unit per storage type and tile family keeps the instantiations compiling in parallel.
+FusedKernel pick_fused_f32(int rb, int dc, int wc);    // k_fused_f32.cu: WC = 2, DC in {12, 4}
+FusedKernel pick_fused_f32_tiles(int rb, int dc, int wc);  // k_fused_f32_tiles.cu: WC in {1, 4}, DC = 12
+FusedKernel pick_fused_f16(int rb, int dc, int wc);    // k_fused_f16.cu: WC = 2, DC = 12
+FusedKernel pick_fused_bf16(int rb, int dc, int wc);   // k_fused_bf16.cu: WC = 2, DC = 12
+FusedKernel pick_fused(int cost_dtype, int rb, int dc, int wc);
+// The descriptor of one context for one call (k_fused_f32.cu).
+void fill_pair_desc(const stereo_ctx *ctx, float *disp, int32_t *wta, uint8_t *valid, PairDesc &d);
 
 }  // namespace sgb

@@ -3,9 +3,9 @@
 
 namespace sgb {
 
-FusedKernel pick_fused_bf16(int rb, int dc)
+FusedKernel pick_fused_bf16(int rb, int dc, int wc)
 {
-    if (dc == 12) return pick_rb<12, __nv_bfloat16>(rb);
+    if (dc == 12 && wc == 2) return pick_rb<12, __nv_bfloat16, 2>(rb);
     return nullptr;
 }
 

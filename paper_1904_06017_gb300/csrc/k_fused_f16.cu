@@ -3,9 +3,9 @@
 
 namespace sgb {
 
-FusedKernel pick_fused_f16(int rb, int dc)
+FusedKernel pick_fused_f16(int rb, int dc, int wc)
 {
-    if (dc == 12) return pick_rb<12, __half>(rb);
+    if (dc == 12 && wc == 2) return pick_rb<12, __half, 2>(rb);
     return nullptr;
 }
 

@@ -1,29 +1,37 @@
 // k_fused_f32.cu -- FP32 cost storage instantiations of the fused kernel, and the host
 // side shared by all storage types (shared-memory sizing, kernel choice, launch).
+#include <string.h>
+
 #include "k_fused.cuh"
 
 namespace sgb {
 
-FusedKernel pick_fused_f32(int rb, int dc)
+FusedKernel pick_fused_f32(int rb, int dc, int wc)
 {
-    if (dc == 12) return pick_rb<12, float>(rb);
-    if (dc == 4) return pick_rb<4, float>(rb);
+    if (wc != 2) return pick_fused_f32_tiles(rb, dc, wc);
+    if (dc == 12) return pick_rb<12, float, 2>(rb);
+    if (dc == 4) return pick_rb<4, float, 2>(rb);
+    return nullptr;
+}
+
+FusedKernel pick_fused(int cost_dtype, int rb, int dc, int wc)
+{
+    switch (cost_dtype) {
+    case STEREO_F32: return pick_fused_f32(rb, dc, wc);
+    case STEREO_F16: return pick_fused_f16(rb, dc, wc);
+    case STEREO_BF16: return pick_fused_bf16(rb, dc, wc);
+    }
     return nullptr;
 }
 
 size_t fused_smem_bytes(const Geometry &g)
 {
-    return smem_layout(g.rb, g.m, g.dc, g.ref_box_w, g.tgt_box_w, g.box_h, g.esize).total;
+    return smem_layout(g.rb, g.m, g.dc, g.ref_box_w, g.tgt_box_w, g.box_h, g.esize, g.tx, g.ty).total;
 }
 
 static FusedKernel pick(const stereo_ctx *ctx)
 {
-    switch (ctx->p.cost_dtype) {
-    case STEREO_F32: return pick_fused_f32(ctx->g.rb, ctx->g.dc);
-    case STEREO_F16: return pick_fused_f16(ctx->g.rb, ctx->g.dc);
-    case STEREO_BF16: return pick_fused_bf16(ctx->g.rb, ctx->g.dc);
-    }
-    return nullptr;
+    return pick_fused(ctx->p.cost_dtype, ctx->g.rb, ctx->g.dc, ctx->g.wc);
 }
 
 int fused_configure(stereo_ctx *ctx)
@@ -37,14 +45,16 @@ int fused_configure(stereo_ctx *ctx)
                       "cudaFuncSetAttribute(fused)");
 }
 
-int launch_fused(stereo_ctx *ctx, const float *shift, float *disp, int32_t *wta, uint8_t *valid,
-                 cudaStream_t s)
+// The pair descriptor of a context for one call (outputs are per call).
+void fill_pair_desc(const stereo_ctx *ctx, float *disp, int32_t *wta, uint8_t *valid, PairDesc &d)
 {
-    (void)shift;   // the integer shifts come from the row table built by k_row_tables
     const Geometry &g = ctx->g;
-    FusedKernel k = pick(ctx);
-    if (!k) return set_error(STEREO_ENOTSUP, "no fused kernel for bil=%d", ctx->p.bil);
-    FusedArgs a;
+    FusedArgs &a = d.a;
+    memset(&d, 0, sizeof(d));
+    d.tmap_ref = ctx->tmap_ref;
+    d.tmap_tgt = ctx->tmap_tgt;
+    d.ntx = g.ntx;
+    d.nty = g.nty;
     a.ref_stats = ctx->ref_stats;
     a.tgt_stats = ctx->tgt_stats;
     a.row_tab = ctx->row_tab;
@@ -71,8 +81,19 @@ int launch_fused(stereo_ctx *ctx, const float *shift, float *disp, int32_t *wta,
     a.iscale = ctx->iscale;
     const int kb = 2 * g.rb + 1;
     for (int i = 0; i < kb * kb; ++i) a.K[i] = ctx->kspatial[i];
-    dim3 grid(g.ntx, g.nty);
-    k<<<grid, kThreads, g.smem_bytes, s>>>(ctx->tmap_ref, ctx->tmap_tgt, a);
+}
+
+int launch_fused(stereo_ctx *ctx, const float *shift, float *disp, int32_t *wta, uint8_t *valid,
+                 cudaStream_t s)
+{
+    (void)shift;   // the integer shifts come from the row table built by k_row_tables
+    const Geometry &g = ctx->g;
+    FusedKernel k = pick(ctx);
+    if (!k) return set_error(STEREO_ENOTSUP, "no fused kernel for bil=%d", ctx->p.bil);
+    PairDesc d;
+    fill_pair_desc(ctx, disp, wta, valid, d);
+    const int ntiles = g.ntx * g.nty;
+    k<<<ntiles, kThreads, g.smem_bytes, s>>>(d, nullptr, nullptr, ntiles, nullptr);
     return cuda_error(cudaGetLastError(), "k_fused launch");
 }
 

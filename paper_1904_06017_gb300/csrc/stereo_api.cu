@@ -32,7 +32,7 @@ int cuda_error(cudaError_t e, const char *what)
 
 static int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
-static int geometry(const stereo_params &p, int dc, Geometry &g)
+int compute_geometry(const stereo_params &p, int dc, int wc, Geometry &g)
 {
     g.W = p.width;
     g.H = p.height;
@@ -43,22 +43,25 @@ static int geometry(const stereo_params &p, int dc, Geometry &g)
     g.m = g.rw + g.rb;
     g.n = p.win * p.win;
     g.dc = dc;
+    g.wc = wc;
+    g.tx = tile_x(wc);
+    g.ty = tile_y(wc);
     g.esize = p.cost_dtype == STEREO_F32 ? 4 : 2;
     g.Dp = round_up(g.D, dc);
-    g.ntx = (g.W + kTileX - 1) / kTileX;
-    g.nty = (g.H + kTileY - 1) / kTileY;
+    g.ntx = (g.W + g.tx - 1) / g.tx;
+    g.nty = (g.H + g.ty - 1) / g.ty;
     g.pad_left = round_up(g.m + g.Dp - 1, 16);
     g.pad_top = g.m;
     g.ref_e = round_up(g.m, 16) - g.m;
-    g.ref_box_w = round_up(g.ref_e + kTileX + 2 * g.m, 16);
+    g.ref_box_w = round_up(g.ref_e + g.tx + 2 * g.m, 16);
     g.tgt_e = g.pad_left - (g.m + g.Dp - 1);
-    g.tgt_box_w = round_up(g.tgt_e + kTileX + 2 * g.m + g.Dp - 1, 16);
-    g.box_h = kTileY + 2 * g.m;
-    const int x_last = (g.ntx - 1) * kTileX;
+    g.tgt_box_w = round_up(g.tgt_e + g.tx + 2 * g.m + g.Dp - 1, 16);
+    g.box_h = g.ty + 2 * g.m;
+    const int x_last = (g.ntx - 1) * g.tx;
     int end_ref = x_last + g.pad_left - round_up(g.m, 16) + g.ref_box_w;
     int end_tgt = x_last + g.tgt_box_w;
     g.pad_w = round_up((end_ref > end_tgt ? end_ref : end_tgt), 16);
-    g.pad_h = g.nty * kTileY + 2 * g.m;
+    g.pad_h = g.nty * g.ty + 2 * g.m;
     g.pad_pitch = round_up(g.pad_w, 128);
     g.smem_bytes = fused_smem_bytes(g);
     return STEREO_OK;
@@ -137,6 +140,26 @@ int stereo_params_default(stereo_params *p)
 
 int stereo_create(const stereo_params *p, stereo_ctx **out)
 {
+    return create_context(p, 0, 0, out);
+}
+
+}  // extern "C"
+
+namespace sgb {
+
+int max_smem_optin()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+}
+
+// Static shared memory of the fused kernel (pair arguments, work item) on top of the dynamic part.
+constexpr int kFusedStaticSmem = 2048;
+
+int create_context(const stereo_params *p, int force_dc, int force_wc, stereo_ctx **out)
+{
     if (!p || !out) return set_error(STEREO_EINVAL, "stereo_create: null pointer");
     *out = nullptr;
     if (p->width < 1 || p->height < 1 || p->width > kMaxDim || p->height > kMaxDim)
@@ -169,10 +192,10 @@ int stereo_create(const stereo_params *p, stereo_ctx **out)
         return cuda_error(cudaErrorNoDevice, "stereo_create: no CUDA device");
     }
     // disparities per chunk: 12 when the fused kernel's shared memory allows it, else 4
-    int smem_max = 0;
-    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-    geometry(*p, 12, c->g);
-    if ((int)c->g.smem_bytes > smem_max) geometry(*p, 4, c->g);
+    const int smem_max = max_smem_optin() - kFusedStaticSmem;
+    const int wc = force_wc ? force_wc : kDefaultWC;
+    compute_geometry(*p, force_dc ? force_dc : 12, wc, c->g);
+    if (!force_dc && (int)c->g.smem_bytes > smem_max) compute_geometry(*p, 4, wc, c->g);
     if ((int)c->g.smem_bytes > smem_max) {
         free_ctx(c);
         return set_error(STEREO_ENOTSUP, "stereo_create: fused kernel needs %zu B of shared memory (max %d)",
@@ -218,6 +241,10 @@ int stereo_create(const stereo_params *p, stereo_ctx **out)
     *out = c;
     return STEREO_OK;
 }
+
+}  // namespace sgb
+
+extern "C" {
 
 int stereo_destroy(stereo_ctx *ctx)
 {

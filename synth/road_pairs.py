@@ -96,10 +96,20 @@ def _road(u, v, width, roll, coeffs):
 
 
 def _pothole_depth(u, v, potholes):
-    out = np.zeros(np.broadcast(u, v).shape)
+    """Depth of the pothole depressions at (u, v); v is constant along each row, so each
+    pothole only touches the band of rows with |v - pv| < rb (elsewhere rho^2 >= 1)."""
+    shape = np.broadcast(u, v).shape
+    ub = np.broadcast_to(u, shape)
+    vb = np.broadcast_to(v, shape)
+    out = np.zeros(shape)
+    vrow = vb[:, 0]
     for (pu, pv, ra, rb, depth) in potholes:
-        rho2 = ((u - pu) / ra) ** 2 + ((v - pv) / rb) ** 2
-        out += np.where(rho2 < 1.0, depth * (1.0 - rho2), 0.0)
+        rows = np.nonzero(np.abs(vrow - pv) < rb)[0]
+        if rows.size == 0:
+            continue
+        r0, r1 = int(rows[0]), int(rows[-1]) + 1
+        rho2 = ((ub[r0:r1] - pu) / ra) ** 2 + ((vb[r0:r1] - pv) / rb) ** 2
+        out[r0:r1] += np.where(rho2 < 1.0, depth * (1.0 - rho2), 0.0)
     return out
 
 
@@ -172,7 +182,7 @@ def make_batch_scenes(n: int | None = None, first: int = 0) -> list:
     """Pairs of uneven sizes and search ranges (the batched workload)."""
     cfg = CONFIGS["batch"]
     n = cfg["n_pairs"] if n is None else n
-    out = []
+    jobs = []
     for i in range(first, first + n):
         rng = np.random.Generator(np.random.PCG64(SEED_BASE + cfg["index"] + 7919 * (i + 1)))
         w, h = cfg["sizes"][int(rng.integers(len(cfg["sizes"])))]
@@ -180,5 +190,8 @@ def make_batch_scenes(n: int | None = None, first: int = 0) -> list:
         seed = SEED_BASE + cfg["index"] + 1000 * i
         kw = {k: cfg[k] for k in ("win", "bil", "sigma0", "sigma1", "roll_deg", "n_potholes",
                                   "depth", "sigma_n", "warp")}
-        out.append(make_scene(w, h, D, seed, **kw))
-    return out
+        jobs.append((w, h, D, seed, kw))
+    # every scene draws from its own generator, so threads change nothing but the wall time
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=8) as ex:
+        return list(ex.map(lambda j: make_scene(j[0], j[1], j[2], j[3], **j[4]), jobs))
