@@ -7,4 +7,6 @@ from .road_pairs import (  # noqa: F401
     make_config_scene,
     make_batch_scenes,
     texture,
+    crop_pair,
+    jitter,
 )

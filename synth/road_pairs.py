@@ -195,3 +195,26 @@ def make_batch_scenes(n: int | None = None, first: int = 0) -> list:
     from concurrent.futures import ThreadPoolExecutor
     with ThreadPoolExecutor(max_workers=8) as ex:
         return list(ex.map(lambda j: make_scene(j[0], j[1], j[2], j[3], **j[4]), jobs))
+
+
+def crop_pair(scene: RoadScene, u0: int, v0: int, width: int, height: int, offset: int | None = None):
+    """A width x height window of a pair, for checks that must stay small.
+
+    The reference is cut at column u0, the target at column u0 - offset, and the row-shift
+    table of those rows is lowered by the same whole number of pixels, so that the target
+    content a reference pixel matches stays inside the window.  ``offset`` defaults to the
+    whole part of the mean shift over the rows.  Returns (ref, tgt, shift) as uint8, uint8,
+    float32 arrays."""
+    s = scene.shift[v0:v0 + height]
+    off = int(math.floor(float(np.mean(s)))) if offset is None else int(offset)
+    if not (0 <= u0 - off and u0 + width <= scene.width and 0 <= v0 and v0 + height <= scene.height):
+        raise ValueError("window outside the pair")
+    ref = np.ascontiguousarray(scene.ref[v0:v0 + height, u0:u0 + width])
+    tgt = np.ascontiguousarray(scene.tgt[v0:v0 + height, u0 - off:u0 - off + width])
+    return ref, tgt, (s - np.float32(off)).astype(np.float32)
+
+
+def jitter(img: np.ndarray, seed: int, amp: float = 0.5) -> np.ndarray:
+    """img as float64 plus uniform noise in [-amp, amp): grey levels off the integer grid."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return img.astype(np.float64) + rng.uniform(-amp, amp, size=img.shape)
