@@ -42,30 +42,32 @@ def warp(tgt, shift):
     return torch.gather(tgt, 1, cols)
 
 
-def _safe_sd(var):
-    """Population standard deviation; a flat window (variance 0) gets 1 so that its
-    (unused) branch has a finite derivative."""
-    flat = var <= 0
-    return torch.sqrt(torch.where(flat, torch.ones_like(var), var)), flat
+def _window_sd(blocks):
+    """Population standard deviation of each w x w block and whether the block is flat
+    (all its values equal, i.e. sigma = 0 exactly).  A flat block gets sigma = 1 so that its
+    unused branch has a finite derivative."""
+    flat = blocks.amax(dim=(2, 3)) == blocks.amin(dim=(2, 3))
+    c = blocks - blocks.mean(dim=(2, 3), keepdim=True)
+    var = (c * c).mean(dim=(2, 3))
+    return torch.sqrt(torch.where(flat, torch.ones_like(var), var)), flat, c
 
 
 def cost_volume(ref, tgtw, D, win):
     """eq. (c) on float images: c[d, v, u], population statistics, clamped reads; a window
-    pair with sigma_ref * sigma_tgt = 0 gets c = 1 (NCC := 0)."""
+    pair with sigma_ref * sigma_tgt = 0 (a block whose values are all equal) gets c = 1
+    (NCC := 0)."""
     H, W = ref.shape
     rw = win // 2
     offs = torch.arange(-rw, rw + 1)
     ys = torch.clamp(torch.arange(H)[:, None] + offs[None, :], 0, H - 1)     # [H, w]
     xs = torch.clamp(torch.arange(W)[:, None] + offs[None, :], 0, W - 1)     # [W, w]
     a = ref[ys[:, None, :, None], xs[None, :, None, :]]                      # [H, W, w, w]
-    ca = a - a.mean(dim=(2, 3), keepdim=True)
-    sa, fa = _safe_sd((ca * ca).mean(dim=(2, 3)))
+    sa, fa, ca = _window_sd(a)
     out = []
     for d in range(D):
         xt = torch.clamp(torch.arange(W)[:, None] - d + offs[None, :], 0, W - 1)
         b = tgtw[ys[:, None, :, None], xt[None, :, None, :]]
-        cb = b - b.mean(dim=(2, 3), keepdim=True)
-        sb, fb = _safe_sd((cb * cb).mean(dim=(2, 3)))
+        sb, fb, cb = _window_sd(b)
         ncc = (ca * cb).mean(dim=(2, 3)) / (sa * sb)
         out.append(1.0 - torch.where(fa | fb, torch.zeros_like(ncc), ncc))
     return torch.stack(out, 0)

@@ -1,4 +1,5 @@
-"""GB300 (sm_103a) road-stereo library: Python binding of the C ABI in include/stereo.h.
+"""GB300 (sm_103a) road-stereo library: Python binding of the C ABI in include/stereo.h
+(and, in ``paper_1904_06017_gb300.diff``, of include/stereo_diff.h).
 
 Thin marshalling only: every function has the name of the C entry point it calls,
 turns tensors into device pointers and streams into cudaStream_t handles, and raises
@@ -118,6 +119,14 @@ def load_library():
         "stereo_batch_config": [P, P, P, P, P],
         "stereo_batch_check_device_status": [P],
         "stereo_batch_destroy": [P],
+        "stereo_diff_params_default": [P],
+        "stereo_softargmin_workspace_bytes": [P, P],
+        "stereo_softargmin_fwd": [P, P, P, P, P, P, ctypes.c_size_t, P],
+        "stereo_softargmin_bwd": [P, P, P, P, P, P, P, P, ctypes.c_size_t, P],
+        "stereo_dt_energy_workspace_bytes": [I32, P],
+        "stereo_dt_energy_fwd": [I32, I32, I32, P, P, P, P, P, ctypes.c_size_t, P],
+        "stereo_dt_energy_bwd": [I32, I32, I32, P, P, P, P, P, P, P, ctypes.c_size_t, P],
+        "stereo_dt_refine_roll": [I32, I32, I32, P, P, D, I32, P, P, ctypes.c_size_t, P],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)

@@ -36,8 +36,12 @@ def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+def _headers():
+    return sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(glob.glob(os.path.join(INCLUDE, "*.h")))
+
+
 def _deps():
-    return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "stereo.h")]
+    return _sources() + _headers()
 
 
 def _stale(target, deps):
@@ -49,8 +53,7 @@ def _stale(target, deps):
 
 def _compile(src, extra, verbose):
     obj = os.path.join(OBJ_DIR, os.path.basename(src) + ".o")
-    hdrs = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "stereo.h")]
-    if not _stale(obj, [src] + hdrs):
+    if not _stale(obj, [src] + _headers()):
         return obj
     cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -1,0 +1,880 @@
+// k_diff.cu -- soft-argmin disparity over the bilateral-aggregated cost and its adjoint
+// (include/stereo_diff.h).  FP32 throughout; the aggregated volume E(p,d) of eq. (fbs) is
+// never stored: the backward pass recomputes it tile by tile from the stored cost volume.
+//
+// Forward (per pair of a batch, float images):
+//   k_dwarp     tw(u,v) = tgt(clamp(u - s_i(v)), v)                                   §3.1
+//   k_dstats    window mean / population std of ref (image grid) and of tw (columns
+//               shifted by -(D-1), so that the target window of (p, d) is the entry at u-d)
+//   k_dcost     c(p,d) = 1 - sum_i (a_i - mu_a)(b_i - mu_b) / (n s_a s_b)           eq. (c)
+//   k_dagg<FWD> E(p,d) = sum_q w c / sum_q w (eq. omega_s, eq. fbs), online soft-max over d:
+//               l = sum_d d P(p,d) + s_i(v), P = softmax_d(-E/T); keeps log2-sum-exp, lbar
+// Backward, given gl = dS/dl:
+//   k_dagg<H>   recompute E; gE = -gl P (d - lbar) / T; h = gE / Z(p);  beta(p) = sum_d h E;
+//               t1(p) = sum_d h(p,d) sum_q w (I_q - I_p) c(q,d) - beta(p) sum_q w (I_q - I_p)
+//   k_dagg<GC>  gc(q,d) = sum_p w(p,q) h(p,d)                  (adjoint of eq. fbs in c)
+//               gw(x) = 2/sigma1^2 (t1(x) + sum_d c(x,d) sum_q w (I_q - I_x) h(q,d)
+//                                        - sum_q w (I_q - I_x) beta(q))  (through the weights)
+//   k_dcost_bwd adjoint of eq. (c): with A = -gc/(n s_a s_b), B = gc ncc/(n s_a^2),
+//               C = gc ncc/(n s_b^2) per window pair, every extended reference position X
+//               collects  sum_d sum_q A (t - mu_b) + B (r - mu_a)            -> gref_ext(X)
+//               and for the target position X - d:  sum_q A (r - mu_a) + C (t - mu_b) -> Gamma(X,d)
+//   k_dtgt_diag gtw_ext(Xt) = sum_d Gamma(Xt + d, d)
+//   k_dfold     fold the clamp-to-edge positions back onto the image and undo the warp
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "internal.cuh"
+#include "stereo_diff.h"
+
+namespace sgb {
+namespace {
+
+constexpr int kAggRows = 4;          // pixels per thread in k_dagg (a column segment)
+constexpr int kAggTile = 32;         // k_dagg tile: 32 x 32 pixels, 256 threads
+constexpr int kAggDC = 8;            // disparities per chunk in k_dagg
+constexpr int kCostDC = 16;          // disparities per block in k_dcost
+constexpr float kFar = 1e18f;        // scaled intensity of an out-of-image neighbour: weight 0
+constexpr float kLog2e = 1.4426950408889634f;
+
+enum { AGG_FWD = 0, AGG_H = 1, AGG_GC = 2 };
+
+__device__ __forceinline__ int clampi(int x, int lo, int hi) { return min(max(x, lo), hi); }
+
+// §3.1 integer row shift floor(s + 0.5) (exact in FP32 for |s| < 2^22), as the value added
+// back to the disparity.
+__device__ __forceinline__ float row_shift_value(float s) { return floorf(s + 0.5f); }
+
+// The same shift as a column offset, limited to +-2W: every column then clamps to the same
+// edge as it would with the exact value.
+__device__ __forceinline__ int row_shift(float s, int W)
+{
+    const float lim = 2.0f * (float)W;
+    return (int)fminf(fmaxf(row_shift_value(s), -lim), lim);
+}
+
+// ------------------------------------------------------------------ layout of the workspace
+struct Dims {
+    int W, H, B, D, rw, rb, n;
+    int We;            // W + D - 1: target statistics columns (u - d + D - 1)
+    int Wr, Hr;        // W + 2rw, H + 2rw: extended reference grid of the cost adjoint
+    int Wt;            // W + 2rw + D - 1: extended target columns
+};
+
+struct Ws {
+    float *tw, *mur, *sdr, *mut, *sdt, *cost, *lse, *lbar;      // forward
+    float *h, *gc, *beta, *t1, *gw, *gamma, *grefx, *gtwx;      // backward
+};
+
+size_t layout(const Dims &d, char *base, Ws *w)
+{
+    size_t off = 0;
+    auto take = [&](float **p, size_t elems) {
+        if (p) *p = base ? (float *)(base + off) : nullptr;
+        off += (elems * sizeof(float) + 255) / 256 * 256;
+    };
+    const size_t B = d.B, img = (size_t)d.H * d.W, vol = (size_t)d.D * img;
+    Ws tmp;
+    Ws *o = w ? w : &tmp;
+    take(&o->tw, B * img);
+    take(&o->mur, B * img);
+    take(&o->sdr, B * img);
+    take(&o->mut, B * (size_t)d.H * d.We);
+    take(&o->sdt, B * (size_t)d.H * d.We);
+    take(&o->cost, B * vol);
+    take(&o->lse, B * img);
+    take(&o->lbar, B * img);
+    take(&o->h, B * vol);
+    take(&o->gc, B * vol);
+    take(&o->beta, B * img);
+    take(&o->t1, B * img);
+    take(&o->gw, B * img);
+    take(&o->gamma, B * (size_t)d.D * d.Hr * d.Wr);
+    take(&o->grefx, B * (size_t)d.Hr * d.Wr);
+    take(&o->gtwx, B * (size_t)d.Hr * d.Wt);
+    return off;
+}
+
+int check_params(const stereo_diff_params *p, Dims *d, const char *who)
+{
+    if (!p) return set_error(STEREO_EINVAL, "%s: null parameters", who);
+    if (p->width < 1 || p->height < 1 || p->width > 8192 || p->height > 8192)
+        return set_error(STEREO_EINVAL, "%s: width/height %d x %d outside 1..8192", who, p->width,
+                         p->height);
+    if (p->batch < 1 || p->batch > 64)
+        return set_error(STEREO_EINVAL, "%s: batch %d outside 1..64", who, p->batch);
+    if (p->max_disp < 1 || p->max_disp > 256)
+        return set_error(STEREO_EINVAL, "%s: max_disp %d outside 1..256", who, p->max_disp);
+    if (p->win < 1 || p->win > 15 || !(p->win & 1))
+        return set_error(STEREO_EINVAL, "%s: win %d must be odd, 1..15", who, p->win);
+    if (p->bil < 1 || p->bil > 15 || !(p->bil & 1))
+        return set_error(STEREO_EINVAL, "%s: bil %d must be odd, 1..15", who, p->bil);
+    if (!(p->sigma0 > 0.f) || !(p->sigma1 > 0.f) || !isfinite(p->sigma0) || !isfinite(p->sigma1))
+        return set_error(STEREO_EINVAL, "%s: sigma0, sigma1 must be positive and finite", who);
+    if (!(p->temperature > 0.f) || !isfinite(p->temperature))
+        return set_error(STEREO_EINVAL, "%s: temperature must be positive and finite", who);
+    d->W = p->width;
+    d->H = p->height;
+    d->B = p->batch;
+    d->D = p->max_disp;
+    d->rw = p->win / 2;
+    d->rb = p->bil / 2;
+    d->n = p->win * p->win;
+    d->We = d->W + d->D - 1;
+    d->Wr = d->W + 2 * d->rw;
+    d->Hr = d->H + 2 * d->rw;
+    d->Wt = d->W + 2 * d->rw + d->D - 1;
+    return STEREO_OK;
+}
+
+int check_ws(const Dims &d, void *ws, size_t bytes, Ws *w, const char *who)
+{
+    const size_t need = layout(d, nullptr, nullptr);
+    if (!ws) return set_error(STEREO_EINVAL, "%s: null workspace", who);
+    if ((uintptr_t)ws % 256) return set_error(STEREO_EINVAL, "%s: workspace not 256-byte aligned", who);
+    if (bytes < need)
+        return set_error(STEREO_EINVAL, "%s: workspace of %zu bytes, %zu needed", who, bytes, need);
+    layout(d, (char *)ws, w);
+    return STEREO_OK;
+}
+
+// ------------------------------------------------------------------ forward kernels
+__global__ void __launch_bounds__(256) k_dwarp(const float *__restrict__ tgt, const float *__restrict__ shift,
+                                               float *__restrict__ tw, int W, int H)
+{
+    const int u = blockIdx.x * blockDim.x + threadIdx.x, v = blockIdx.y, b = blockIdx.z;
+    if (u >= W) return;
+    const int si = row_shift(shift[(size_t)b * H + v], W);
+    const size_t row = ((size_t)b * H + v) * W;
+    tw[row + u] = tgt[row + clampi(u - si, 0, W - 1)];
+}
+
+// Window mean and population standard deviation over (2rw+1)^2 clamp-to-edge reads, on an
+// output grid of Wout columns whose column xo is centred on image column xo + off.
+__global__ void __launch_bounds__(256) k_dstats(const float *__restrict__ img, int W, int H, int Wout, int off,
+                                                int rw, float *__restrict__ mu, float *__restrict__ sd)
+{
+    extern __shared__ float s[];
+    const int sw = 32 + 2 * rw, sh = 8 + 2 * rw;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8, b = blockIdx.z;
+    const float *im = img + (size_t)b * H * W;
+    for (int i = threadIdx.x; i < sw * sh; i += 256) {
+        const int r = i / sw, c = i - r * sw;
+        s[i] = im[(size_t)clampi(y0 - rw + r, 0, H - 1) * W + clampi(x0 + off - rw + c, 0, W - 1)];
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int xo = x0 + tx, v = y0 + ty;
+    if (xo >= Wout || v >= H) return;
+    const int w = 2 * rw + 1;
+    const float n = (float)(w * w);
+    // relative to the centre value: a block whose values are all equal gets sd = 0 exactly
+    const float c0 = s[(ty + rw) * sw + tx + rw];
+    float sum = 0.f;
+    for (int dy = 0; dy < w; ++dy)
+        for (int dx = 0; dx < w; ++dx) sum += s[(ty + dy) * sw + tx + dx] - c0;
+    const float m = sum / n;
+    float q = 0.f;
+    for (int dy = 0; dy < w; ++dy)
+        for (int dx = 0; dx < w; ++dx) {
+            const float a = (s[(ty + dy) * sw + tx + dx] - c0) - m;
+            q = fmaf(a, a, q);
+        }
+    const size_t o = ((size_t)b * H + v) * Wout + xo;
+    mu[o] = c0 + m;
+    sd[o] = sqrtf(q / n);
+}
+
+// eq. (c) for a 32 x 8 pixel tile and kCostDC disparities: the centred reference window
+// times the target window, corrected by the target mean through sum_i (a_i - mu_a).
+__global__ void __launch_bounds__(256) k_dcost(const float *__restrict__ ref, const float *__restrict__ tw,
+                                               const float *__restrict__ mur, const float *__restrict__ sdr,
+                                               const float *__restrict__ mut, const float *__restrict__ sdt,
+                                               float *__restrict__ cost, int W, int H, int D, int rw,
+                                               int nchunk)
+{
+    constexpr int DC = kCostDC;
+    extern __shared__ float s[];
+    const int sw = 32 + 2 * rw, sh = 8 + 2 * rw, st = 32 + 2 * rw + DC - 1;
+    float *rs = s, *ts = s + sw * sh;
+    const int b = blockIdx.z / nchunk, d0 = (blockIdx.z % nchunk) * DC;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8;
+    const size_t HW = (size_t)H * W;
+    const float *R = ref + b * HW, *T = tw + b * HW;
+    for (int i = threadIdx.x; i < sw * sh; i += 256) {
+        const int r = i / sw, c = i - r * sw;
+        rs[i] = R[(size_t)clampi(y0 - rw + r, 0, H - 1) * W + clampi(x0 - rw + c, 0, W - 1)];
+    }
+    const int tc0 = x0 - d0 - (DC - 1) - rw;     // image column of ts column 0
+    for (int i = threadIdx.x; i < st * sh; i += 256) {
+        const int r = i / st, c = i - r * st;
+        ts[i] = T[(size_t)clampi(y0 - rw + r, 0, H - 1) * W + clampi(tc0 + c, 0, W - 1)];
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int u = x0 + tx, v = y0 + ty;
+    if (u >= W || v >= H) return;
+    const size_t pix = b * HW + (size_t)v * W + u;
+    const float ma = mur[pix], sa = sdr[pix];
+    const int w = 2 * rw + 1;
+    float acc[DC];
+#pragma unroll
+    for (int k = 0; k < DC; ++k) acc[k] = 0.f;
+    float asum = 0.f;
+    for (int dy = 0; dy < w; ++dy) {
+        const float *rrow = rs + (ty + dy) * sw + tx;
+        const float *trow = ts + (ty + dy) * st + tx + (DC - 1);
+        for (int dx = 0; dx < w; ++dx) {
+            const float a = rrow[dx] - ma;
+            asum += a;
+#pragma unroll
+            for (int k = 0; k < DC; ++k) acc[k] = fmaf(a, trow[dx - k], acc[k]);
+        }
+    }
+    const int We = W + D - 1;
+    const float n = (float)(w * w);
+#pragma unroll
+    for (int k = 0; k < DC; ++k) {
+        const int d = d0 + k;
+        if (d >= D) break;
+        const size_t so = ((size_t)b * H + v) * We + (u - d + D - 1);
+        const float mb = mut[so], sb = sdt[so];
+        float c = 1.f;
+        if (sa > 0.f && sb > 0.f) c = 1.f - fmaf(-mb, asum, acc[k]) / (n * sa * sb);
+        cost[((size_t)b * D + d) * HW + (size_t)v * W + u] = c;
+    }
+}
+
+// ------------------------------------------------------------------ aggregation stencil
+struct AggArgs {
+    const float *img;      // reference image [B][H][W]
+    const float *vol;      // neighbour values [B][D][H][W]: the cost (FWD, H) or h (GC)
+    const float *shift;    // FWD: row shifts
+    float *disp;           // FWD: l
+    float *lse, *lbar;     // FWD out, H in
+    const float *gdisp;    // H: dS/dl
+    float *h;              // H out
+    float *beta, *t1;      // H out, GC in
+    float *gc;             // GC out
+    const float *cost;     // GC: c(x, d) of the centre pixel
+    float *gw;             // GC out: image gradient through the weights
+    int W, H, D;
+    float kappa;           // sqrt(log2 e) / sigma1: scaled intensities
+    float k0;              // -log2 e / sigma0^2
+    float kT;              // log2 e / T
+    float invT;            // 1 / T
+    float gw_scale;        // 2 / (sigma1^2 kappa)
+};
+
+// One 32 x 32 tile per block; thread (tx, ty) owns the pixels (x0 + tx, y0 + 4 ty + i),
+// i < 4, and kAggDC disparities at a time.  The weights of eq. (omega_s) are formed as
+// exp2(kx + ky - (sI_p - sI_q)^2) with sI = kappa I; an out-of-image neighbour has
+// sI = kFar and a zero value, so its weight and every product with it are exactly 0.
+template <int MODE, int RB>
+__global__ void __launch_bounds__(256) k_dagg(const AggArgs a)
+{
+    constexpr int DC = kAggDC, NQ = DC / 4, NR = kAggRows + 2 * RB;
+    constexpr int TW = kAggTile + 2 * RB, TH = kAggTile + 2 * RB;
+    constexpr bool TWO = MODE != AGG_FWD;
+    extern __shared__ float4 smem4[];
+    float4 *V = smem4;                              // [NQ][TH][TW]
+    float *sI = (float *)(V + NQ * TH * TW);        // [TH][TW]
+    const int b = blockIdx.z, x0 = blockIdx.x * kAggTile, y0 = blockIdx.y * kAggTile;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int W = a.W, H = a.H, D = a.D;
+    const size_t HW = (size_t)H * W;
+    const float *img = a.img + b * HW;
+    for (int i = threadIdx.x; i < TH * TW; i += 256) {
+        const int r = i / TW, c = i - r * TW, y = y0 - RB + r, x = x0 - RB + c;
+        sI[i] = (y >= 0 && y < H && x >= 0 && x < W) ? img[(size_t)y * W + x] * a.kappa : kFar;
+    }
+    float ky[2 * RB + 1];
+#pragma unroll
+    for (int j = 0; j <= 2 * RB; ++j) ky[j] = a.k0 * (float)((j - RB) * (j - RB));
+    __syncthreads();
+
+    const int px = x0 + tx;
+    float sIp[kAggRows];
+    int py[kAggRows];
+    bool pin[kAggRows];
+#pragma unroll
+    for (int i = 0; i < kAggRows; ++i) {
+        py[i] = y0 + kAggRows * ty + i;
+        pin[i] = px < W && py[i] < H;
+        sIp[i] = sI[(kAggRows * ty + i + RB) * TW + tx + RB];
+    }
+    // per-pixel state across chunks
+    float st0[kAggRows], st1[kAggRows], st2[kAggRows], st3[kAggRows];
+#pragma unroll
+    for (int i = 0; i < kAggRows; ++i) {
+        st0[i] = st1[i] = st2[i] = st3[i] = 0.f;
+        if constexpr (MODE == AGG_FWD) st0[i] = -INFINITY;   // running max of -E kT
+        if (MODE == AGG_H && pin[i]) {
+            const size_t o = b * HW + (size_t)py[i] * W + px;
+            st0[i] = a.gdisp[o];                             // gl
+            st1[i] = a.lse[o];                               // log2-sum-exp
+            st2[i] = a.lbar[o];                              // soft-argmin without the shift
+        }
+    }
+    float S[kAggRows];          // sum_q w (sI_q - sI_p), the same in every chunk
+    float beta[kAggRows], tacc[kAggRows];
+#pragma unroll
+    for (int i = 0; i < kAggRows; ++i) S[i] = beta[i] = tacc[i] = 0.f;
+
+    for (int d0 = 0; d0 < D; d0 += DC) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < TH * TW; i += 256) {
+            const int r = i / TW, c = i - r * TW, y = y0 - RB + r, x = x0 - RB + c;
+            const bool in = y >= 0 && y < H && x >= 0 && x < W;
+            const float *src = a.vol + ((size_t)b * D) * HW + (in ? (size_t)y * W + x : 0);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                float e[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int d = d0 + 4 * q + j;
+                    e[j] = (in && d < D) ? src[(size_t)d * HW] : 0.f;
+                }
+                V[(q * TH + r) * TW + c] = make_float4(e[0], e[1], e[2], e[3]);
+            }
+        }
+        __syncthreads();
+
+        float acc0[kAggRows][DC], acc1[kAggRows][TWO ? DC : 1], Z[kAggRows];
+#pragma unroll
+        for (int i = 0; i < kAggRows; ++i) {
+            Z[i] = 0.f;
+            if constexpr (TWO) S[i] = 0.f;
+#pragma unroll
+            for (int k = 0; k < DC; ++k) {
+                acc0[i][k] = 0.f;
+                if constexpr (TWO) acc1[i][k] = 0.f;
+            }
+        }
+#pragma unroll 1
+        for (int dx = -RB; dx <= RB; ++dx) {
+            const float kx = a.k0 * (float)(dx * dx);
+            const int col = tx + RB + dx;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int srow = kAggRows * ty + r;
+                const float sq = sI[srow * TW + col];
+                float4 v4[NQ];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) v4[q] = V[(q * TH + srow) * TW + col];
+#pragma unroll
+                for (int i = 0; i < kAggRows; ++i) {
+                    const int dy = r - RB - i;
+                    if (dy < -RB || dy > RB) continue;
+                    const float dd = sIp[i] - sq;
+                    const float w = exp2f(kx + ky[dy + RB] - dd * dd);
+                    Z[i] += w;
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) {
+                        acc0[i][4 * q + 0] = fmaf(w, v4[q].x, acc0[i][4 * q + 0]);
+                        acc0[i][4 * q + 1] = fmaf(w, v4[q].y, acc0[i][4 * q + 1]);
+                        acc0[i][4 * q + 2] = fmaf(w, v4[q].z, acc0[i][4 * q + 2]);
+                        acc0[i][4 * q + 3] = fmaf(w, v4[q].w, acc0[i][4 * q + 3]);
+                    }
+                    if constexpr (TWO) {
+                        const float wd = -w * dd;
+                        S[i] += wd;
+#pragma unroll
+                        for (int q = 0; q < NQ; ++q) {
+                            acc1[i][4 * q + 0] = fmaf(wd, v4[q].x, acc1[i][4 * q + 0]);
+                            acc1[i][4 * q + 1] = fmaf(wd, v4[q].y, acc1[i][4 * q + 1]);
+                            acc1[i][4 * q + 2] = fmaf(wd, v4[q].z, acc1[i][4 * q + 2]);
+                            acc1[i][4 * q + 3] = fmaf(wd, v4[q].w, acc1[i][4 * q + 3]);
+                        }
+                    }
+                }
+            }
+        }
+
+        // chunk epilogue
+#pragma unroll
+        for (int i = 0; i < kAggRows; ++i) {
+            if (!pin[i]) continue;
+            const float invZ = 1.f / Z[i];
+            const size_t pix = (size_t)py[i] * W + px;
+            if constexpr (MODE == AGG_FWD) {
+                float z[DC], mc = st0[i];
+#pragma unroll
+                for (int k = 0; k < DC; ++k) {
+                    z[k] = -(acc0[i][k] * invZ) * a.kT;
+                    if (d0 + k < D) mc = fmaxf(mc, z[k]);
+                }
+                const float sc = exp2f(st0[i] - mc);
+                float s0 = st1[i] * sc, s1 = st2[i] * sc;
+#pragma unroll
+                for (int k = 0; k < DC; ++k) {
+                    if (d0 + k >= D) break;
+                    const float e = exp2f(z[k] - mc);
+                    s0 += e;
+                    s1 = fmaf((float)(d0 + k), e, s1);
+                }
+                st0[i] = mc;
+                st1[i] = s0;
+                st2[i] = s1;
+            } else if constexpr (MODE == AGG_H) {
+#pragma unroll
+                for (int k = 0; k < DC; ++k) {
+                    const int d = d0 + k;
+                    if (d >= D) break;
+                    const float E = acc0[i][k] * invZ;
+                    const float P = exp2f(-E * a.kT - st1[i]);
+                    const float hv = -st0[i] * a.invT * P * ((float)d - st2[i]) * invZ;
+                    a.h[((size_t)b * D + d) * HW + pix] = hv;
+                    beta[i] = fmaf(hv, E, beta[i]);
+                    tacc[i] = fmaf(hv, acc1[i][k], tacc[i]);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < DC; ++k) {
+                    const int d = d0 + k;
+                    if (d >= D) break;
+                    const size_t o = ((size_t)b * D + d) * HW + pix;
+                    a.gc[o] = acc0[i][k];
+                    tacc[i] = fmaf(a.cost[o], acc1[i][k], tacc[i]);
+                }
+            }
+        }
+    }
+
+    if constexpr (MODE == AGG_FWD) {
+#pragma unroll
+        for (int i = 0; i < kAggRows; ++i) {
+            if (!pin[i]) continue;
+            const size_t o = b * HW + (size_t)py[i] * W + px;
+            const float lbar = st2[i] / st1[i];
+            a.lbar[o] = lbar;
+            a.lse[o] = st0[i] + log2f(st1[i]);
+            a.disp[o] = lbar + row_shift_value(a.shift[(size_t)b * H + py[i]]);
+        }
+        return;
+    }
+    if constexpr (MODE == AGG_H) {
+#pragma unroll
+        for (int i = 0; i < kAggRows; ++i) {
+            if (!pin[i]) continue;
+            const size_t o = b * HW + (size_t)py[i] * W + px;
+            a.beta[o] = beta[i];
+            a.t1[o] = fmaf(-beta[i], S[i], tacc[i]);
+        }
+        return;
+    }
+    // AGG_GC: the weights' term of beta, sum_q w (sI_q - sI_x) beta(q), over a staged tile
+    __syncthreads();
+    float *sb = (float *)V;
+    for (int i = threadIdx.x; i < TH * TW; i += 256) {
+        const int r = i / TW, c = i - r * TW, y = y0 - RB + r, x = x0 - RB + c;
+        sb[i] = (y >= 0 && y < H && x >= 0 && x < W) ? a.beta[b * HW + (size_t)y * W + x] : 0.f;
+    }
+    __syncthreads();
+    float sbeta[kAggRows];
+#pragma unroll
+    for (int i = 0; i < kAggRows; ++i) sbeta[i] = 0.f;
+#pragma unroll 1
+    for (int dx = -RB; dx <= RB; ++dx) {
+        const float kx = a.k0 * (float)(dx * dx);
+        const int col = tx + RB + dx;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int srow = kAggRows * ty + r;
+            const float sq = sI[srow * TW + col], bq = sb[srow * TW + col];
+#pragma unroll
+            for (int i = 0; i < kAggRows; ++i) {
+                const int dy = r - RB - i;
+                if (dy < -RB || dy > RB) continue;
+                const float dd = sIp[i] - sq;
+                const float w = exp2f(kx + ky[dy + RB] - dd * dd);
+                sbeta[i] = fmaf(-w * dd, bq, sbeta[i]);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kAggRows; ++i) {
+        if (!pin[i]) continue;
+        const size_t o = b * HW + (size_t)py[i] * W + px;
+        a.gw[o] = a.gw_scale * (a.t1[o] + tacc[i] - sbeta[i]);
+    }
+}
+
+// ------------------------------------------------------------------ cost adjoint
+struct CbArgs {
+    const float *ref, *tw, *mur, *sdr, *mut, *sdt, *cost, *gc;
+    float *gamma, *grefx;
+    int W, H, D, Wr, Hr, We;
+    float inv_n;
+};
+
+// Extended reference positions X in [-rw, W-1+rw] x [-rw, H-1+rw], a 32 x 8 tile per block.
+// Per disparity the four window-pair terms A, A mu_a, C, C mu_b of the pairs q in the tile's
+// halo are staged and box-summed (rows, then columns); the d-independent terms of the
+// reference gradient are summed over d per q and box-summed once at the end.
+template <int RW>
+__global__ void __launch_bounds__(256) k_dcost_bwd(const CbArgs a)
+{
+    constexpr int QW = 32 + 2 * RW, QH = 8 + 2 * RW, NQ = QW * QH, NS = (NQ + 255) / 256;
+    constexpr int WN = 2 * RW + 1;
+    __shared__ float st[4][NQ];
+    __shared__ float hb[4][QH][32];
+    const int b = blockIdx.z;
+    const int W = a.W, H = a.H, D = a.D;
+    const size_t HW = (size_t)H * W;
+    const int X0 = blockIdx.x * 32 - RW, Y0 = blockIdx.y * 8 - RW;   // image coords of the tile origin
+    float qmu[NS], qsa[NS], sAmb[NS], sB[NS], sBmu[NS];
+    size_t vbase[NS], sbase[NS];       // cost / gc entry of (q, d = 0); statistics entry of (q, 0)
+    bool qin[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const int j = threadIdx.x + 256 * s;
+        const int qy = Y0 - RW + j / QW, qx = X0 - RW + j % QW;
+        qin[s] = j < NQ && qy >= 0 && qy < H && qx >= 0 && qx < W;
+        const size_t qo = qin[s] ? (size_t)qy * W + qx : 0;
+        vbase[s] = (size_t)b * D * HW + qo;
+        sbase[s] = qin[s] ? ((size_t)b * H + qy) * a.We + qx + D - 1 : 0;
+        qmu[s] = qin[s] ? a.mur[b * HW + qo] : 0.f;
+        qsa[s] = qin[s] ? a.sdr[b * HW + qo] : 0.f;
+        sAmb[s] = sB[s] = sBmu[s] = 0.f;
+    }
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int X = X0 + tx, Y = Y0 + ty;
+    const bool xin = X <= W - 1 + RW && Y <= H - 1 + RW;
+    const int yc = clampi(Y, 0, H - 1);
+    const float rv = a.ref[b * HW + (size_t)yc * W + clampi(X, 0, W - 1)];
+    const float *twrow = a.tw + b * HW + (size_t)yc * W;
+    float gacc = 0.f;
+    for (int d = 0; d < D; ++d) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const int j = threadIdx.x + 256 * s;
+            if (j >= NQ) break;
+            float A = 0.f, Am = 0.f, C = 0.f, Cm = 0.f;
+            if (qin[s]) {
+                const size_t vo = vbase[s] + (size_t)d * HW, so = sbase[s] - d;
+                const float sb = a.sdt[so];
+                if (qsa[s] > 0.f && sb > 0.f) {
+                    const float g = a.gc[vo], ncc = 1.f - a.cost[vo], mub = a.mut[so];
+                    const float gn = g * a.inv_n;
+                    A = -gn / (qsa[s] * sb);
+                    const float Bq = gn * ncc / (qsa[s] * qsa[s]);
+                    C = gn * ncc / (sb * sb);
+                    Am = A * qmu[s];
+                    Cm = C * mub;
+                    sAmb[s] = fmaf(A, mub, sAmb[s]);
+                    sB[s] += Bq;
+                    sBmu[s] = fmaf(Bq, qmu[s], sBmu[s]);
+                }
+            }
+            st[0][j] = A;
+            st[1][j] = Am;
+            st[2][j] = C;
+            st[3][j] = Cm;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < 4 * QH * 32; e += 256) {
+            const int k = e / (QH * 32), rem = e - k * QH * 32, row = rem >> 5, xc = rem & 31;
+            const float *src = &st[k][row * QW + xc];
+            float sum = 0.f;
+#pragma unroll
+            for (int j = 0; j < WN; ++j) sum += src[j];
+            hb[k][row][xc] = sum;
+        }
+        __syncthreads();
+        float bx[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float sum = 0.f;
+#pragma unroll
+            for (int i = 0; i < WN; ++i) sum += hb[k][ty + i][tx];
+            bx[k] = sum;
+        }
+        if (xin) {
+            const float t = twrow[clampi(X - d, 0, W - 1)];
+            if (a.gamma)
+                a.gamma[(((size_t)b * D + d) * a.Hr + (Y + RW)) * a.Wr + (X + RW)] =
+                    fmaf(rv, bx[0], -bx[1]) + fmaf(t, bx[2], -bx[3]);
+            gacc = fmaf(t, bx[0], gacc);
+        }
+    }
+    // the d-independent terms: - box(sum_d A mu_b) + r box(sum_d B) - box(sum_d B mu_a)
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const int j = threadIdx.x + 256 * s;
+        if (j >= NQ) break;
+        st[0][j] = sAmb[s];
+        st[1][j] = sB[s];
+        st[2][j] = sBmu[s];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 3 * QH * 32; e += 256) {
+        const int k = e / (QH * 32), rem = e - k * QH * 32, row = rem >> 5, xc = rem & 31;
+        const float *src = &st[k][row * QW + xc];
+        float sum = 0.f;
+#pragma unroll
+        for (int j = 0; j < WN; ++j) sum += src[j];
+        hb[k][row][xc] = sum;
+    }
+    __syncthreads();
+    float bx[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float sum = 0.f;
+#pragma unroll
+        for (int i = 0; i < WN; ++i) sum += hb[k][ty + i][tx];
+        bx[k] = sum;
+    }
+    if (xin)
+        a.grefx[((size_t)b * a.Hr + (Y + RW)) * a.Wr + (X + RW)] = gacc - bx[0] + fmaf(rv, bx[1], -bx[2]);
+}
+
+// Target positions Xt in [-rw-(D-1), W-1+rw]: the sum over d of Gamma(Xt + d, d).
+__global__ void __launch_bounds__(256) k_dtgt_diag(const float *__restrict__ gamma, float *__restrict__ gtwx,
+                                                   int D, int rw, int Wr, int Hr, int Wt)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x, row = blockIdx.y, b = blockIdx.z;
+    if (c >= Wt) return;
+    const int xr = c - (D - 1);                  // Xt + rw
+    const int dlo = max(0, -xr), dhi = min(D - 1, Wr - 1 - xr);
+    float s = 0.f;
+    for (int d = dlo; d <= dhi; ++d) s += gamma[(((size_t)b * D + d) * Hr + row) * Wr + xr + d];
+    gtwx[((size_t)b * Hr + row) * Wt + c] = s;
+}
+
+// Fold the extended grids back onto the image (every clamp-to-edge position adds to the
+// edge pixel it read) and undo the warp (every warped column adds to the column it read).
+__global__ void __launch_bounds__(256) k_dfold(const float *__restrict__ grefx, const float *__restrict__ gw,
+                                               const float *__restrict__ gtwx, const float *__restrict__ shift,
+                                               float *__restrict__ gref, float *__restrict__ gtgt, int W, int H,
+                                               int D, int rw, int Wr, int Hr, int Wt)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, b = blockIdx.z;
+    if (x >= W) return;
+    const size_t pix = ((size_t)b * H + y) * W + x;
+    const int ylo = y == 0 ? -rw : y, yhi = y == H - 1 ? H - 1 + rw : y;
+    if (gref) {
+        const int xlo = x == 0 ? -rw : x, xhi = x == W - 1 ? W - 1 + rw : x;
+        float s = 0.f;
+        for (int Y = ylo; Y <= yhi; ++Y)
+            for (int X = xlo; X <= xhi; ++X) s += grefx[((size_t)b * Hr + Y + rw) * Wr + X + rw];
+        gref[pix] = s + gw[pix];
+    }
+    if (gtgt) {
+        const int si = row_shift(shift[(size_t)b * H + y], W);
+        int lo, hi;                              // warped columns reading source column x
+        if (W == 1) {
+            lo = 0;
+            hi = 0;
+        } else if (x == 0) {
+            lo = 0;
+            hi = min(W - 1, si);
+        } else if (x == W - 1) {
+            lo = max(0, W - 1 + si);
+            hi = W - 1;
+        } else {
+            lo = hi = x + si;
+            if (lo < 0 || lo > W - 1) {
+                lo = 1;
+                hi = 0;
+            }
+        }
+        float s = 0.f;
+        for (int xw = lo; xw <= hi; ++xw) {
+            const int tlo = xw == 0 ? -rw - (D - 1) : xw, thi = xw == W - 1 ? W - 1 + rw : xw;
+            for (int Y = ylo; Y <= yhi; ++Y) {
+                const float *row = gtwx + ((size_t)b * Hr + Y + rw) * Wt + rw + (D - 1);
+                for (int Xt = tlo; Xt <= thi; ++Xt) s += row[Xt];
+            }
+        }
+        gtgt[pix] = s;
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+template <int MODE, int RB>
+cudaError_t launch_agg_rb(const AggArgs &a, int B, cudaStream_t st)
+{
+    constexpr int T = kAggTile + 2 * RB;
+    const size_t smem = (size_t)T * T * (sizeof(float4) * (kAggDC / 4) + sizeof(float));
+    cudaError_t e = cudaFuncSetAttribute(k_dagg<MODE, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.W + kAggTile - 1) / kAggTile, (a.H + kAggTile - 1) / kAggTile, B);
+    k_dagg<MODE, RB><<<grid, 256, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_agg(const AggArgs &a, int rb, int B, cudaStream_t st)
+{
+    switch (rb) {
+    case 0: return launch_agg_rb<MODE, 0>(a, B, st);
+    case 1: return launch_agg_rb<MODE, 1>(a, B, st);
+    case 2: return launch_agg_rb<MODE, 2>(a, B, st);
+    case 3: return launch_agg_rb<MODE, 3>(a, B, st);
+    case 4: return launch_agg_rb<MODE, 4>(a, B, st);
+    case 5: return launch_agg_rb<MODE, 5>(a, B, st);
+    case 6: return launch_agg_rb<MODE, 6>(a, B, st);
+    default: return launch_agg_rb<MODE, 7>(a, B, st);
+    }
+}
+
+template <int RW>
+cudaError_t launch_cb_rw(const CbArgs &a, int B, cudaStream_t st)
+{
+    dim3 grid((a.Wr + 31) / 32, (a.Hr + 7) / 8, B);
+    k_dcost_bwd<RW><<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cb(const CbArgs &a, int rw, int B, cudaStream_t st)
+{
+    switch (rw) {
+    case 0: return launch_cb_rw<0>(a, B, st);
+    case 1: return launch_cb_rw<1>(a, B, st);
+    case 2: return launch_cb_rw<2>(a, B, st);
+    case 3: return launch_cb_rw<3>(a, B, st);
+    case 4: return launch_cb_rw<4>(a, B, st);
+    case 5: return launch_cb_rw<5>(a, B, st);
+    case 6: return launch_cb_rw<6>(a, B, st);
+    default: return launch_cb_rw<7>(a, B, st);
+    }
+}
+
+AggArgs agg_args(const stereo_diff_params *p, const Dims &d, const Ws &w, const float *ref)
+{
+    AggArgs a;
+    memset(&a, 0, sizeof(a));
+    a.img = ref;
+    a.W = d.W;
+    a.H = d.H;
+    a.D = d.D;
+    a.kappa = sqrtf(kLog2e) / p->sigma1;
+    a.k0 = -kLog2e / (p->sigma0 * p->sigma0);
+    a.kT = kLog2e / p->temperature;
+    a.invT = 1.0f / p->temperature;
+    a.gw_scale = 2.0f / (p->sigma1 * p->sigma1 * a.kappa);
+    a.lse = w.lse;
+    a.lbar = w.lbar;
+    return a;
+}
+
+}  // namespace
+}  // namespace sgb
+
+using namespace sgb;
+
+extern "C" int stereo_diff_params_default(stereo_diff_params *p)
+{
+    if (!p) return set_error(STEREO_EINVAL, "stereo_diff_params_default: null pointer");
+    memset(p, 0, sizeof(*p));
+    p->batch = 1;
+    p->win = 9;
+    p->bil = 11;
+    p->sigma0 = 1.5f;
+    p->sigma1 = 5.5f;
+    p->temperature = 0.1f;
+    return STEREO_OK;
+}
+
+extern "C" int stereo_softargmin_workspace_bytes(const stereo_diff_params *p, size_t *bytes)
+{
+    Dims d;
+    int rc = check_params(p, &d, "stereo_softargmin_workspace_bytes");
+    if (rc) return rc;
+    if (!bytes) return set_error(STEREO_EINVAL, "stereo_softargmin_workspace_bytes: null output");
+    *bytes = layout(d, nullptr, nullptr);
+    return STEREO_OK;
+}
+
+extern "C" int stereo_softargmin_fwd(const stereo_diff_params *p, const float *ref, const float *tgt,
+                                     const float *shift, float *disp, void *ws, size_t ws_bytes,
+                                     stereo_stream_t stream)
+{
+    static const char *who = "stereo_softargmin_fwd";
+    Dims d;
+    Ws w;
+    int rc = check_params(p, &d, who);
+    if (rc) return rc;
+    if (!ref || !tgt || !shift || !disp) return set_error(STEREO_EINVAL, "%s: null pointer", who);
+    if ((rc = check_ws(d, ws, ws_bytes, &w, who))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int B = d.B;
+    k_dwarp<<<dim3((d.W + 255) / 256, d.H, B), 256, 0, st>>>(tgt, shift, w.tw, d.W, d.H);
+    const size_t ssm = (size_t)(32 + 2 * d.rw) * (8 + 2 * d.rw) * sizeof(float);
+    k_dstats<<<dim3((d.W + 31) / 32, (d.H + 7) / 8, B), 256, ssm, st>>>(ref, d.W, d.H, d.W, 0, d.rw, w.mur,
+                                                                        w.sdr);
+    k_dstats<<<dim3((d.We + 31) / 32, (d.H + 7) / 8, B), 256, ssm, st>>>(w.tw, d.W, d.H, d.We, -(d.D - 1),
+                                                                         d.rw, w.mut, w.sdt);
+    const int nchunk = (d.D + kCostDC - 1) / kCostDC;
+    const size_t csm = ((size_t)(32 + 2 * d.rw) + (32 + 2 * d.rw + kCostDC - 1)) * (8 + 2 * d.rw) * sizeof(float);
+    k_dcost<<<dim3((d.W + 31) / 32, (d.H + 7) / 8, B * nchunk), 256, csm, st>>>(
+        ref, w.tw, w.mur, w.sdr, w.mut, w.sdt, w.cost, d.W, d.H, d.D, d.rw, nchunk);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, who);
+    AggArgs a = agg_args(p, d, w, ref);
+    a.vol = w.cost;
+    a.shift = shift;
+    a.disp = disp;
+    e = launch_agg<AGG_FWD>(a, d.rb, B, st);
+    return cuda_error(e, who);
+}
+
+extern "C" int stereo_softargmin_bwd(const stereo_diff_params *p, const float *ref, const float *tgt,
+                                     const float *shift, const float *gdisp, float *gref, float *gtgt,
+                                     void *ws, size_t ws_bytes, stereo_stream_t stream)
+{
+    static const char *who = "stereo_softargmin_bwd";
+    Dims d;
+    Ws w;
+    int rc = check_params(p, &d, who);
+    if (rc) return rc;
+    if (!ref || !tgt || !shift || !gdisp) return set_error(STEREO_EINVAL, "%s: null pointer", who);
+    if ((rc = check_ws(d, ws, ws_bytes, &w, who))) return rc;
+    if (!gref && !gtgt) return STEREO_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int B = d.B;
+    AggArgs a = agg_args(p, d, w, ref);
+    a.vol = w.cost;
+    a.gdisp = gdisp;
+    a.h = w.h;
+    a.beta = w.beta;
+    a.t1 = w.t1;
+    cudaError_t e = launch_agg<AGG_H>(a, d.rb, B, st);
+    if (e != cudaSuccess) return cuda_error(e, who);
+    a.vol = w.h;
+    a.gc = w.gc;
+    a.cost = w.cost;
+    a.gw = w.gw;
+    e = launch_agg<AGG_GC>(a, d.rb, B, st);
+    if (e != cudaSuccess) return cuda_error(e, who);
+    CbArgs c;
+    c.ref = ref;
+    c.tw = w.tw;
+    c.mur = w.mur;
+    c.sdr = w.sdr;
+    c.mut = w.mut;
+    c.sdt = w.sdt;
+    c.cost = w.cost;
+    c.gc = w.gc;
+    c.gamma = gtgt ? w.gamma : nullptr;
+    c.grefx = w.grefx;
+    c.W = d.W;
+    c.H = d.H;
+    c.D = d.D;
+    c.Wr = d.Wr;
+    c.Hr = d.Hr;
+    c.We = d.We;
+    c.inv_n = 1.0f / (float)d.n;
+    if ((e = launch_cb(c, d.rw, B, st)) != cudaSuccess) return cuda_error(e, who);
+    if (gtgt)
+        k_dtgt_diag<<<dim3((d.Wt + 255) / 256, d.Hr, B), 256, 0, st>>>(w.gamma, w.gtwx, d.D, d.rw, d.Wr,
+                                                                       d.Hr, d.Wt);
+    k_dfold<<<dim3((d.W + 255) / 256, d.H, B), 256, 0, st>>>(w.grefx, w.gw, w.gtwx, shift, gref, gtgt, d.W,
+                                                             d.H, d.D, d.rw, d.Wr, d.Hr, d.Wt);
+    return cuda_error(cudaGetLastError(), who);
+}

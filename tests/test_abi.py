@@ -1,7 +1,8 @@
 """C-ABI checks that need no GPU: the library builds, loads and exports every entry
-point include/stereo.h declares; the ctypes structures match the C layout; host-only
-helpers and argument validation behave as documented."""
+point the headers under include/ declare; the ctypes structures match the C layout;
+host-only helpers and argument validation behave as documented."""
 import ctypes
+import glob
 import json
 import math
 import os
@@ -15,7 +16,7 @@ import paper_1904_06017_gb300 as sg
 from paper_1904_06017_gb300 import build as sgbuild
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "stereo.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 @pytest.fixture(scope="module")
@@ -25,14 +26,17 @@ def lib():
 
 
 def declared_functions():
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(stereo_[a-z0-9_]+)\s*\(", src)))
+    names = set()
+    for h in HEADERS:
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(stereo_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_every_declared_symbol_is_exported(lib):
     names = declared_functions()
-    assert len(names) >= 15
+    assert len(HEADERS) >= 2 and len(names) >= 25
+    assert "stereo_softargmin_bwd" in names and "stereo_dt_refine_roll" in names
     out = subprocess.run(["nm", "-D", "--defined-only", sg.library_path()], capture_output=True,
                          text=True, check=True).stdout
     exported = set(re.findall(r"\bT (stereo_[a-z0-9_]+)", out))
@@ -107,3 +111,75 @@ def test_null_pointers_rejected(lib):
 
 def test_version(lib):
     assert "sm_103a" in sg.stereo_version()
+
+
+def test_diff_struct_layout_matches_header(tmp_path):
+    from paper_1904_06017_gb300 import diff as sgd
+    prog = tmp_path / "layout_diff.c"
+    prog.write_text(r'''
+#include <stddef.h>
+#include <stdio.h>
+#include "stereo_diff.h"
+int main(void) {
+  printf("%zu %zu %zu\n", sizeof(stereo_diff_params), offsetof(stereo_diff_params, sigma0),
+         offsetof(stereo_diff_params, temperature));
+  return 0;
+}''')
+    exe = tmp_path / "layout_diff"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    vals = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                           check=True).stdout.split()]
+    assert vals == [ctypes.sizeof(sgd.stereo_diff_params), sgd.stereo_diff_params.sigma0.offset,
+                    sgd.stereo_diff_params.temperature.offset]
+
+
+def test_diff_defaults_and_workspace_size(lib):
+    from paper_1904_06017_gb300 import diff as sgd
+    p = sgd.stereo_diff_params_default()
+    assert (p.win, p.bil, p.batch) == (9, 11, 1)
+    assert p.sigma0 == pytest.approx(1.5) and p.sigma1 == pytest.approx(5.5)
+    assert p.temperature == pytest.approx(0.1)
+    p = sgd.stereo_diff_params_default(width=960, height=540, batch=8, max_disp=64)
+    n = sgd.stereo_softargmin_workspace_bytes(p)
+    W, H, B, D, rw = 960, 540, 8, 64, 4
+    vol = B * D * H * W * 4
+    assert n >= 3 * vol + B * D * (H + 2 * rw) * (W + 2 * rw) * 4
+    assert n % 256 == 0
+    # grows linearly in the batch
+    p1 = sgd.stereo_diff_params_default(width=960, height=540, batch=1, max_disp=64)
+    assert abs(n - 8 * sgd.stereo_softargmin_workspace_bytes(p1)) < 8 * 16 * 256
+    assert sgd.stereo_dt_energy_workspace_bytes(8) >= 8 * 64 * 10 * 8
+
+
+@pytest.mark.parametrize("field,value", [("width", 0), ("height", 9000), ("batch", 0), ("batch", 65),
+                                         ("max_disp", 0), ("max_disp", 257), ("win", 4), ("win", 17),
+                                         ("bil", 0), ("sigma0", -1.0), ("sigma1", float("inf")),
+                                         ("temperature", 0.0)])
+def test_diff_rejects_bad_parameters(lib, field, value):
+    from paper_1904_06017_gb300 import diff as sgd
+    p = sgd.stereo_diff_params_default(width=64, height=48, max_disp=16)
+    setattr(p, field, value)
+    with pytest.raises(sg.StereoError) as e:
+        sgd.stereo_softargmin_workspace_bytes(p)
+    assert e.value.code == sg.STEREO_EINVAL
+
+
+def test_diff_rejects_null_and_small_workspaces(lib):
+    from paper_1904_06017_gb300 import diff as sgd
+    p = sgd.stereo_diff_params_default(width=64, height=48, max_disp=16)
+    fake = 1 << 20          # never dereferenced: every check below fails before a launch
+    assert lib.stereo_softargmin_fwd(ctypes.byref(p), fake, fake, fake, fake, None, 0, None) == sg.STEREO_EINVAL
+    assert lib.stereo_softargmin_fwd(ctypes.byref(p), fake, fake, fake, fake, fake + 16, 1 << 30,
+                                     None) == sg.STEREO_EINVAL
+    assert "aligned" in sg.stereo_last_error()
+    assert lib.stereo_softargmin_fwd(ctypes.byref(p), fake, fake, fake, fake, fake, 256, None) == sg.STEREO_EINVAL
+    assert "needed" in sg.stereo_last_error()
+    assert lib.stereo_softargmin_bwd(ctypes.byref(p), fake, fake, fake, None, fake, fake, fake, 1 << 40,
+                                     None) == sg.STEREO_EINVAL
+    assert lib.stereo_dt_energy_fwd(64, 48, 1, fake, None, fake, fake, fake, 16, None) == sg.STEREO_EINVAL
+    assert lib.stereo_dt_energy_bwd(0, 48, 1, fake, None, fake, fake, fake, fake, fake, 1 << 20,
+                                    None) == sg.STEREO_EINVAL
+    assert lib.stereo_dt_refine_roll(64, 48, 1, fake, None, 0.0, 1001, fake, fake, 1 << 20,
+                                     None) == sg.STEREO_EINVAL
+    assert lib.stereo_dt_refine_roll(64, 48, 1, fake, None, float("nan"), 5, fake, fake, 1 << 20,
+                                     None) == sg.STEREO_EINVAL

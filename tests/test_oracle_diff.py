@@ -70,13 +70,19 @@ def test_warp_equals_the_c_oracle():
 def test_flat_window_costs_one_with_finite_gradients():
     rng = np.random.default_rng(1)
     ref = rng.uniform(0, 255, (16, 24))
-    ref[2:12, 3:14] = 77.0              # a flat patch: windows centred well inside it
+    ref[2:12, 3:14] = 77.123456789      # a flat patch whose rounded mean need not be exact
     tgt = rng.uniform(0, 255, (16, 24))
     c = diff.cost_volume(torch.tensor(ref), torch.tensor(tgt), 4, 5).numpy()
     assert np.all(c[:, 6:9, 7:11] == 1.0)
     _, g_r, g_t = diff.disparity_vjp(ref, tgt, np.zeros(16, np.float32), 4, 5, 5, S0, S1, T,
                                      np.ones((16, 24)))
     assert np.all(np.isfinite(g_r)) and np.all(np.isfinite(g_t))
+    # a 1 x 1 image: every clamped block is flat, every cost 1, every gradient 0
+    x = np.array([[123.456789]])
+    c1 = diff.cost_volume(torch.tensor(x), torch.tensor(x * 0.37), 3, 3).numpy()
+    assert np.all(c1 == 1.0)
+    _, g_r, g_t = diff.disparity_vjp(x, x * 0.37, np.zeros(1, np.float32), 3, 3, 3, S0, S1, T, np.ones((1, 1)))
+    assert np.all(g_r == 0) and np.all(g_t == 0)
 
 
 def test_soft_argmin_closed_forms():
