@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     return ap.parse_args()
 
@@ -235,6 +236,80 @@ def bench_batch(args, dev, stream, flush):
     return out
 
 
+def bench_diff(args, dev, stream, flush):
+    """The differentiation workload: 8 pairs of 960 x 540, D = 64, w = 9, k = 11, T = 0.1.
+    One step = soft-argmin forward, eq. (E2) forward, and the backward of both (gradients
+    in both images and theta), through torch.autograd; plus 50 steps of roll refinement.
+    Its workspace (about 4.3 GB) exceeds L2."""
+    import numpy as np
+    import torch
+    from paper_1904_06017_gb300 import diff as sgd
+    import synth
+    cfg = synth.CONFIGS["grad"]
+    B, W, H, D = cfg["n_pairs"], cfg["width"], cfg["height"], cfg["D"]
+    scenes = [synth.make_config_scene("grad", pair=i) for i in range(B)]
+    ref = torch.tensor(np.stack([s.ref for s in scenes]).astype(np.float32), device=dev, requires_grad=True)
+    tgt = torch.tensor(np.stack([s.tgt for s in scenes]).astype(np.float32), device=dev, requires_grad=True)
+    shift = torch.tensor(np.stack([s.shift for s in scenes]), device=dev)
+    theta = torch.zeros((B, 3), dtype=torch.float64, device=dev)
+    theta[:, 1], theta[:, 2] = 30.0, 0.1
+    theta.requires_grad_(True)
+    kw = dict(win=cfg["win"], bil=cfg["bil"], sigma0=cfg["sigma0"], sigma1=cfg["sigma1"],
+              temperature=cfg["temperature"])
+
+    def fwd():
+        return sgd.SoftArgmin.apply(ref, tgt, shift, D, kw["win"], kw["bil"], kw["sigma0"], kw["sigma1"],
+                                    kw["temperature"])
+
+    def step():
+        ref.grad = tgt.grad = theta.grad = None
+        l = fwd()
+        sgd.DTEnergy.apply(l, theta, None).sum().backward()
+        return l
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    n = max(3, min(args.steps, 10))
+    e_f = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    e_s = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for i in range(n):
+        flush.fill_(i & 0xFF)
+        e_f[i][0].record(stream)
+        with torch.no_grad():
+            l = fwd()
+        e_f[i][1].record(stream)
+        flush.fill_(i & 0xFF)
+        e_s[i][0].record(stream)
+        l = step()
+        e_s[i][1].record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = sum(a.elapsed_time(b) for a, b in e_f) / n
+    step_ms = sum(a.elapsed_time(b) for a, b in e_s) / n
+    mask = torch.ones((B, H, W), dtype=torch.uint8, device=dev)
+    sgd.refine_roll(l.detach(), mask, 0.0, 50)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    traj = sgd.refine_roll(l.detach(), mask, 0.0, 50)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    psi = traj[:, -1, 0].cpu().numpy()
+    units = B * W * H * D
+    k2 = cfg["bil"] ** 2
+    return {"pairs": B, "size": "%dx%d" % (W, H), "max_disp": D, "temperature": cfg["temperature"],
+            "forward_ms": fwd_ms, "forward_backward_ms": step_ms, "backward_ms": step_ms - fwd_ms,
+            "forward_gpix_disp_per_s": units / fwd_ms / 1e6,
+            "forward_backward_gpix_disp_per_s": units / step_ms / 1e6,
+            "aggregation_flops_per_step": 2.0 * k2 * units * (1 + 2 + 2),
+            "aggregation_tflops_effective": 2.0 * k2 * units * 5 / (step_ms * 1e-3) / 1e12,
+            "refine_roll_50_steps_ms": e0.elapsed_time(e1),
+            "refined_psi_deg": [float(np.degrees(x)) for x in psi],
+            "true_roll_deg": [float(np.degrees(s.roll)) for s in scenes],
+            "grad_finite": bool(torch.isfinite(ref.grad).all() and torch.isfinite(tgt.grad).all()),
+            "steps": n}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -409,6 +484,11 @@ def run_ours(args):
             line["batch"] = bench_batch(args, dev, stream, flush)
         except Exception as exc:   # the headline line above stands on its own
             line["batch"] = {"error": str(exc)[:300]}
+    if not args.no_diff:
+        try:
+            line["differentiation"] = bench_diff(args, dev, stream, flush)
+        except Exception as exc:   # the headline line above stands on its own
+            line["differentiation"] = {"error": str(exc)[:300]}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline_sample(s, args.cpu_seconds)
     st.close()

@@ -511,21 +511,24 @@ struct CbArgs {
 };
 
 // Extended reference positions X in [-rw, W-1+rw] x [-rw, H-1+rw], a 32 x 8 tile per block.
-// Per disparity the four window-pair terms A, A mu_a, C, C mu_b of the pairs q in the tile's
-// halo are staged and box-summed (rows, then columns); the d-independent terms of the
-// reference gradient are summed over d per q and box-summed once at the end.
+// kCbDC disparities at a time: the four window-pair terms A, A mu_a, C, C mu_b of the pairs q
+// in the tile's halo are staged and box-summed (rows, then columns); the d-independent
+// terms of the reference gradient are summed over d per q and box-summed once at the end.
+constexpr int kCbDC = 4;
+
 template <int RW>
 __global__ void __launch_bounds__(256) k_dcost_bwd(const CbArgs a)
 {
     constexpr int QW = 32 + 2 * RW, QH = 8 + 2 * RW, NQ = QW * QH, NS = (NQ + 255) / 256;
-    constexpr int WN = 2 * RW + 1;
-    __shared__ float st[4][NQ];
-    __shared__ float hb[4][QH][32];
+    constexpr int WN = 2 * RW + 1, DC = kCbDC;
+    extern __shared__ float cb_smem[];
+    float *st = cb_smem;                       // [4][DC][NQ]
+    float *hb = cb_smem + 4 * DC * NQ;         // [4][DC][QH][32]
     const int b = blockIdx.z;
     const int W = a.W, H = a.H, D = a.D;
     const size_t HW = (size_t)H * W;
     const int X0 = blockIdx.x * 32 - RW, Y0 = blockIdx.y * 8 - RW;   // image coords of the tile origin
-    float qmu[NS], qsa[NS], sAmb[NS], sB[NS], sBmu[NS];
+    float qmu[NS], qisa[NS], sAmb[NS], sB[NS], sBmu[NS];
     size_t vbase[NS], sbase[NS];       // cost / gc entry of (q, d = 0); statistics entry of (q, 0)
     bool qin[NS];
 #pragma unroll
@@ -537,7 +540,8 @@ __global__ void __launch_bounds__(256) k_dcost_bwd(const CbArgs a)
         vbase[s] = (size_t)b * D * HW + qo;
         sbase[s] = qin[s] ? ((size_t)b * H + qy) * a.We + qx + D - 1 : 0;
         qmu[s] = qin[s] ? a.mur[b * HW + qo] : 0.f;
-        qsa[s] = qin[s] ? a.sdr[b * HW + qo] : 0.f;
+        const float sa = qin[s] ? a.sdr[b * HW + qo] : 0.f;
+        qisa[s] = sa > 0.f ? __frcp_rn(sa) : 0.f;       // 0 marks a flat reference block
         sAmb[s] = sB[s] = sBmu[s] = 0.f;
     }
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -547,57 +551,69 @@ __global__ void __launch_bounds__(256) k_dcost_bwd(const CbArgs a)
     const float rv = a.ref[b * HW + (size_t)yc * W + clampi(X, 0, W - 1)];
     const float *twrow = a.tw + b * HW + (size_t)yc * W;
     float gacc = 0.f;
-    for (int d = 0; d < D; ++d) {
+    for (int d0 = 0; d0 < D; d0 += DC) {
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             const int j = threadIdx.x + 256 * s;
             if (j >= NQ) break;
-            float A = 0.f, Am = 0.f, C = 0.f, Cm = 0.f;
-            if (qin[s]) {
-                const size_t vo = vbase[s] + (size_t)d * HW, so = sbase[s] - d;
-                const float sb = a.sdt[so];
-                if (qsa[s] > 0.f && sb > 0.f) {
-                    const float g = a.gc[vo], ncc = 1.f - a.cost[vo], mub = a.mut[so];
-                    const float gn = g * a.inv_n;
-                    A = -gn / (qsa[s] * sb);
-                    const float Bq = gn * ncc / (qsa[s] * qsa[s]);
-                    C = gn * ncc / (sb * sb);
-                    Am = A * qmu[s];
-                    Cm = C * mub;
-                    sAmb[s] = fmaf(A, mub, sAmb[s]);
-                    sB[s] += Bq;
-                    sBmu[s] = fmaf(Bq, qmu[s], sBmu[s]);
-                }
+            float g[DC], cc[DC], sb[DC], mb[DC];
+#pragma unroll
+            for (int k = 0; k < DC; ++k) {      // all loads of the DC disparities first
+                const bool ok = qin[s] && d0 + k < D;
+                const size_t vo = vbase[s] + (size_t)(ok ? d0 + k : 0) * HW, so = sbase[s] - (ok ? d0 + k : 0);
+                g[k] = ok ? a.gc[vo] : 0.f;
+                cc[k] = ok ? a.cost[vo] : 1.f;
+                sb[k] = ok ? a.sdt[so] : 0.f;
+                mb[k] = ok ? a.mut[so] : 0.f;
             }
-            st[0][j] = A;
-            st[1][j] = Am;
-            st[2][j] = C;
-            st[3][j] = Cm;
+#pragma unroll
+            for (int k = 0; k < DC; ++k) {
+                float A = 0.f, C = 0.f, Bq = 0.f;
+                if (qisa[s] > 0.f && sb[k] > 0.f) {
+                    const float isb = __frcp_rn(sb[k]);
+                    const float gn = g[k] * a.inv_n, gnc = gn * (1.f - cc[k]);
+                    A = -gn * qisa[s] * isb;
+                    Bq = gnc * qisa[s] * qisa[s];
+                    C = gnc * isb * isb;
+                }
+                sAmb[s] = fmaf(A, mb[k], sAmb[s]);
+                sB[s] += Bq;
+                sBmu[s] = fmaf(Bq, qmu[s], sBmu[s]);
+                st[(0 * DC + k) * NQ + j] = A;
+                st[(1 * DC + k) * NQ + j] = A * qmu[s];
+                st[(2 * DC + k) * NQ + j] = C;
+                st[(3 * DC + k) * NQ + j] = C * mb[k];
+            }
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < 4 * QH * 32; e += 256) {
-            const int k = e / (QH * 32), rem = e - k * QH * 32, row = rem >> 5, xc = rem & 31;
-            const float *src = &st[k][row * QW + xc];
+        for (int e = threadIdx.x; e < 4 * DC * QH * 32; e += 256) {
+            const int kk = e / (QH * 32), rem = e - kk * QH * 32, row = rem >> 5, xc = rem & 31;
+            const float *src = st + kk * NQ + row * QW + xc;
             float sum = 0.f;
 #pragma unroll
             for (int j = 0; j < WN; ++j) sum += src[j];
-            hb[k][row][xc] = sum;
+            hb[e] = sum;
         }
         __syncthreads();
-        float bx[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float sum = 0.f;
+        for (int k = 0; k < DC; ++k) {
+            const int d = d0 + k;
+            float bx[4];
 #pragma unroll
-            for (int i = 0; i < WN; ++i) sum += hb[k][ty + i][tx];
-            bx[k] = sum;
-        }
-        if (xin) {
-            const float t = twrow[clampi(X - d, 0, W - 1)];
-            if (a.gamma)
-                a.gamma[(((size_t)b * D + d) * a.Hr + (Y + RW)) * a.Wr + (X + RW)] =
-                    fmaf(rv, bx[0], -bx[1]) + fmaf(t, bx[2], -bx[3]);
-            gacc = fmaf(t, bx[0], gacc);
+            for (int qn = 0; qn < 4; ++qn) {
+                const float *col = hb + ((qn * DC + k) * QH + ty) * 32 + tx;
+                float sum = 0.f;
+#pragma unroll
+                for (int i = 0; i < WN; ++i) sum += col[i * 32];
+                bx[qn] = sum;
+            }
+            if (xin && d < D) {
+                const float t = twrow[clampi(X - d, 0, W - 1)];
+                if (a.gamma)
+                    a.gamma[(((size_t)b * D + d) * a.Hr + (Y + RW)) * a.Wr + (X + RW)] =
+                        fmaf(rv, bx[0], -bx[1]) + fmaf(t, bx[2], -bx[3]);
+                gacc = fmaf(t, bx[0], gacc);
+            }
         }
     }
     // the d-independent terms: - box(sum_d A mu_b) + r box(sum_d B) - box(sum_d B mu_a)
@@ -606,27 +622,28 @@ __global__ void __launch_bounds__(256) k_dcost_bwd(const CbArgs a)
     for (int s = 0; s < NS; ++s) {
         const int j = threadIdx.x + 256 * s;
         if (j >= NQ) break;
-        st[0][j] = sAmb[s];
-        st[1][j] = sB[s];
-        st[2][j] = sBmu[s];
+        st[0 * NQ + j] = sAmb[s];
+        st[1 * NQ + j] = sB[s];
+        st[2 * NQ + j] = sBmu[s];
     }
     __syncthreads();
     for (int e = threadIdx.x; e < 3 * QH * 32; e += 256) {
-        const int k = e / (QH * 32), rem = e - k * QH * 32, row = rem >> 5, xc = rem & 31;
-        const float *src = &st[k][row * QW + xc];
+        const int kk = e / (QH * 32), rem = e - kk * QH * 32, row = rem >> 5, xc = rem & 31;
+        const float *src = st + kk * NQ + row * QW + xc;
         float sum = 0.f;
 #pragma unroll
         for (int j = 0; j < WN; ++j) sum += src[j];
-        hb[k][row][xc] = sum;
+        hb[e] = sum;
     }
     __syncthreads();
     float bx[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
+    for (int qn = 0; qn < 3; ++qn) {
+        const float *col = hb + (qn * QH + ty) * 32 + tx;
         float sum = 0.f;
 #pragma unroll
-        for (int i = 0; i < WN; ++i) sum += hb[k][ty + i][tx];
-        bx[k] = sum;
+        for (int i = 0; i < WN; ++i) sum += col[i * 32];
+        bx[qn] = sum;
     }
     if (xin)
         a.grefx[((size_t)b * a.Hr + (Y + RW)) * a.Wr + (X + RW)] = gacc - bx[0] + fmaf(rv, bx[1], -bx[2]);
@@ -726,8 +743,13 @@ cudaError_t launch_agg(const AggArgs &a, int rb, int B, cudaStream_t st)
 template <int RW>
 cudaError_t launch_cb_rw(const CbArgs &a, int B, cudaStream_t st)
 {
+    constexpr int QW = 32 + 2 * RW, QH = 8 + 2 * RW;
+    const size_t smem = (size_t)4 * kCbDC * (QW * QH + QH * 32) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_dcost_bwd<RW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
     dim3 grid((a.Wr + 31) / 32, (a.Hr + 7) / 8, B);
-    k_dcost_bwd<RW><<<grid, 256, 0, st>>>(a);
+    k_dcost_bwd<RW><<<grid, 256, smem, st>>>(a);
     return cudaGetLastError();
 }
 
