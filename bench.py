@@ -109,6 +109,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(x, world, device="cpu"):
+    """The largest of the ranks' values (the slowest rank's time); x itself at world = 1."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, steps, units_per_step, t_max_ms):
+    """Whole-job throughput in units/s (x1e-9): every rank processed `steps` steps of
+    `units_per_step` units; the job took the slowest rank's time."""
+    return world * steps * units_per_step / (t_max_ms * 1e-3) / 1e9
+
+
 def make_inputs():
     import synth
     s = synth.make_config_scene("hd")
@@ -139,6 +156,21 @@ def cpu_baseline_sample(s, seconds):
                       "FP64 C oracle (cost, aggregation, WTA, sub-pixel), %.1f s" % (v0, v0 + rows, rows, W, D, el)}
 
 
+REFERENCE_BUDGET_S = 150.0
+
+
+def reference_rows(s, n_steps, budget_s=REFERENCE_BUDGET_S):
+    """Rows per reference step (1..16) so that n_steps steps take about budget_s seconds."""
+    import oracle
+    p = s.params
+    tw = oracle.warp(s.tgt, s.shift)
+    v0 = s.height // 2
+    t = time.perf_counter()
+    oracle.stereo(s.ref, tw, s.shift, p["D"], p["win"], p["bil"], p["sigma0"], p["sigma1"], rows=(v0, v0 + 2))
+    per_row = (time.perf_counter() - t) / 2
+    return int(max(1, min(16, budget_s / max(n_steps, 1) / max(per_row, 1e-6))))
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -150,7 +182,7 @@ def run_reference(args):
     s = make_inputs()
     p = s.params
     H, W, D = s.height, s.width, p["D"]
-    rows = 16
+    rows = reference_rows(s, args.warmup + args.steps)
     times = []
     for it in range(args.warmup + args.steps):
         v0 = 16 + (it * 37) % (H - 32 - rows)
@@ -168,11 +200,11 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD + " (oracle on 16-row bands)",
+            "data": "synthetic", "config": {"workload": WORKLOAD + " (oracle on %d-row bands)" % rows,
                                             "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
                              "sample": "per step: warp of the full target, then cost/aggregation/WTA/"
-                                       "sub-pixel on a 16-row band and the roll fit of that band"},
+                                       "sub-pixel on a %d-row band and the roll fit of that band" % rows},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -383,16 +415,9 @@ def run_ours(args):
     sg.stereo_profile_enable(st.ctx, False)
     st.check_device_status()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_local = sum(step_ms)
-    t_max = t_local
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    units = world * args.steps * W * H * D
-    value = units / (t_max * 1e-3) / 1e9
-    pairs_per_s = world * args.steps / (t_max * 1e-3)
+    t_max = max_over_ranks(sum(step_ms), world, dev)
+    value = job_throughput(world, args.steps, W * H * D, t_max)
+    pairs_per_s = job_throughput(world, args.steps, 1, t_max) * 1e9
 
     # ---- end to end through the public API: pinned host inputs in, transformed map out
     e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -407,15 +432,10 @@ def run_ours(args):
         res_h.copy_(res, non_blocking=True)
         e_ev[i][1].record(stream)
     torch.cuda.synchronize()
-    e_ms = sum(a.elapsed_time(b) for a, b in e_ev)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e_ms = float(tt.item())
-    e2e = {"value": world * args.steps * W * H * D / (e_ms * 1e-3) / 1e9, "unit": UNIT,
+    e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in e_ev), world, dev)
+    e2e = {"value": job_throughput(world, args.steps, W * H * D, e_ms), "unit": UNIT,
            "h2d_bytes_per_step": 2 * H * pitch + 4 * H, "d2h_bytes_per_step": 4 * H * W + 64,
-           "pairs_per_s": world * args.steps / (e_ms * 1e-3)}
+           "pairs_per_s": job_throughput(world, args.steps, 1, e_ms) * 1e9}
     r = sg.stereo_dt_result.from_buffer_copy(res.cpu().numpy().tobytes()[:48])
 
     # ---- cost-storage variants on the same pair: FP16 / BF16 storage vs the FP32 path
