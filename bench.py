@@ -34,7 +34,7 @@ SM_MAX_MHZ = 2070.0
 # DRAM traffic of one fused-kernel launch on this workload, from the ncu capture summarised
 # in profiles/ (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the kernel
 # source with this SHA-256 prefix.
-FUSED_TRAFFIC = {"sha256": "ce15a31c41b591cb", "bytes": 40299776}
+FUSED_TRAFFIC = {"sha256": "b0dcb46782148724", "bytes": 40291584}
 
 
 def parse():
@@ -59,7 +59,7 @@ def dist_env():
 
 def kernel_sha():
     h = hashlib.sha256()
-    for f in ("k_fused.cuh", "k_fused_f32.cu"):
+    for f in ("internal.cuh", "k_fused.cuh", "k_fused_f32.cu"):
         h.update(open(os.path.join(ROOT, "paper_1904_06017_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -476,16 +476,19 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    # ---- roofline of the fused kernel: aggregation arithmetic, 2 k^2 flops per (pixel, d)
+    # ---- roofline of the fused kernel: algorithmic flops per (pixel, d) F = 2k^2 (aggregation)
+    # + 11 (cost from window sums) + 2k^2/D (weights and their sum, once per pixel) + 1 (WTA)
     fused_avg_ms = fused_ms / max(n_fused, 1)
-    agg_flops = 2.0 * bil * bil * W * H * D
+    flops_per_unit = 2.0 * bil * bil + 11.0 + 2.0 * bil * bil / D + 1.0
+    agg_flops = flops_per_unit * W * H * D
     achieved = agg_flops / (fused_avg_ms * 1e-3) / 1e12
     peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     traffic = FUSED_TRAFFIC["bytes"] if FUSED_TRAFFIC["sha256"] == kernel_sha() else None
     probe_s, probe_p = sg.stereo_fp32_peak_probe(2)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": "k_fused (cost + bilateral aggregation + WTA + sub-pixel)",
-            "flops_per_launch": agg_flops, "avg_launch_ms": fused_avg_ms, "launches": n_fused,
+            "flops_per_launch": agg_flops, "flops_per_pixel_disparity": flops_per_unit,
+            "avg_launch_ms": fused_avg_ms, "launches": n_fused,
             "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal, derived)",
             "fp32_probe_tflops": {"scalar_fma": probe_s / 1e3, "packed_f32x2_fma": probe_p / 1e3},
             "fused_gpix_disp_per_s": W * H * D / (fused_avg_ms * 1e-3) / 1e9}
