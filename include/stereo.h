@@ -197,7 +197,10 @@ typedef struct {
     int32_t cost_dtype;        /* STEREO_F32 | STEREO_F16 | STEREO_BF16 */
     double lambda0, delta_psi;
     int32_t max_iters;
-    int32_t tile_wc;           /* warp columns of a tile (1: 32x64, 2: 64x32, 4: 128x16); 0 = autotune */
+    int32_t tile_wc;           /* tile shape: warp columns 1 (32x64), 2 (64x32), 4 (128x16), or 8: 64x16
+                                  tiles with the costs of the next chunk computed by separate producer
+                                  warps while consumer warps aggregate (FP32 storage, tile_dc 12,
+                                  bil <= 11); 0 = autotune */
     int32_t tile_dc;           /* disparities per chunk (12 or 4); 0 = autotune */
 } stereo_batch_params;
 

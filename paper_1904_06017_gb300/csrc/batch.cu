@@ -134,7 +134,7 @@ static int enqueue_fused(stereo_batch *b, cudaStream_t s)
     PairDesc unused;
     memset(&unused, 0, sizeof(unused));
     const int grid = std::min(b->nsm, b->nitems);
-    b->kernel<<<grid, kThreads, b->smem, s>>>(unused, b->d_pairs, b->d_items, b->nitems, b->d_counter);
+    b->kernel<<<grid, fused_threads(b->wc), b->smem, s>>>(unused, b->d_pairs, b->d_items, b->nitems, b->d_counter);
     return cuda_error(cudaGetLastError(), "batch: fused launch");
 }
 
@@ -193,7 +193,7 @@ static std::string tune_key(const stereo_batch *b)
 {
     std::string k;
     char buf[96];
-    snprintf(buf, sizeof(buf), "w%d k%d t%d sm%d |", b->bp.win, b->bp.bil, b->bp.cost_dtype, b->nsm);
+    snprintf(buf, sizeof(buf), "c5 w%d k%d t%d sm%d |", b->bp.win, b->bp.bil, b->bp.cost_dtype, b->nsm);
     k += buf;
     for (const stereo_pair_desc &d : b->pairs) {
         snprintf(buf, sizeof(buf), " %dx%dx%d", d.width, d.height, d.max_disp);
@@ -262,7 +262,7 @@ static int autotune(stereo_batch *b, int *wc_out, int *dc_out, int *source)
         *source = 1;
         return STEREO_OK;
     }
-    const int cand[][2] = {{2, 12}, {1, 12}, {4, 12}, {2, 4}};
+    const int cand[][2] = {{kWsWC, 12}, {2, 12}, {1, 12}, {4, 12}, {2, 4}};
     double best_ms = 1e30;
     int best_wc = 0, best_dc = 0;
     cudaEvent_t e0, e1;
@@ -329,9 +329,9 @@ int stereo_batch_create(const stereo_batch_params *p, int32_t n, const stereo_pa
     if (!p || !pairs || !out) return set_error(STEREO_EINVAL, "stereo_batch_create: null pointer");
     *out = nullptr;
     if (n < 1 || n > 4096) return set_error(STEREO_EINVAL, "stereo_batch_create: n = %d outside 1..4096", n);
-    if ((p->tile_wc && p->tile_wc != 1 && p->tile_wc != 2 && p->tile_wc != 4) ||
+    if ((p->tile_wc && p->tile_wc != 1 && p->tile_wc != 2 && p->tile_wc != 4 && p->tile_wc != kWsWC) ||
         (p->tile_dc && p->tile_dc != 4 && p->tile_dc != 12))
-        return set_error(STEREO_EINVAL, "stereo_batch_create: tile_wc must be 0, 1, 2 or 4 and tile_dc 0, 4 or 12");
+        return set_error(STEREO_EINVAL, "stereo_batch_create: tile_wc must be 0, 1, 2, 4 or 8 and tile_dc 0, 4 or 12");
     for (int i = 0; i < n; ++i) {
         const stereo_pair_desc &d = pairs[i];
         if (!d.ref_dev || !d.tgt_dev || !d.shift_dev || !d.tgt_warped_dev || !d.disp_dev || !d.valid_dev ||

@@ -15,12 +15,26 @@ namespace sgb {
 // Tiling of the fused kernel: a CTA of 8 warps owns a tile of output pixels; lane =
 // column, each warp covers 32 columns x kPY rows, and WC warp columns x (8 / WC) warp rows
 // give tiles of 32 x 64 (WC = 1), 64 x 32 (WC = 2, the default) or 128 x 16 (WC = 4).
-constexpr int kPY = 8;
-constexpr int kWarps = 8;
+constexpr int kPY = 6;
+constexpr int kWarps = 12;
 constexpr int kThreads = 32 * kWarps;
 constexpr int kDefaultWC = 2;
-__host__ __device__ constexpr int tile_x(int wc) { return 32 * wc; }
-__host__ __device__ constexpr int tile_y(int wc) { return kPY * (kWarps / wc); }
+// The warp-specialised form (tile code kWsWC): 8 producer warps compute the costs of the next
+// chunk while 8 consumer warps aggregate the current one, on 64 x 16 tiles (2 consumer warp
+// columns x 4 consumer warp rows x kWsPY pixels per thread).
+constexpr int kWsWC = 8;
+constexpr int kWsProdWarps = 8;
+constexpr int kWsConsWarps = 8;
+constexpr int kWsThreads = 32 * (kWsProdWarps + kWsConsWarps);
+constexpr int kWsPY = 4;
+constexpr int kWsBand = 3;          // cost rows per band of the producers' two-pass window sums
+constexpr int kWsMaxRB = 5;         // the two cost buffers fit shared memory up to bil = 11
+__host__ __device__ constexpr int tile_x(int wc) { return wc == kWsWC ? 64 : 32 * wc; }
+__host__ __device__ constexpr int tile_y(int wc)
+{
+    return wc == kWsWC ? kWsPY * (kWsConsWarps / 2) : kPY * (kWarps / wc);
+}
+__host__ __device__ constexpr int fused_threads(int wc) { return wc == kWsWC ? kWsThreads : kThreads; }
 constexpr int kMaxRB = 7;          // bil <= 15
 constexpr int kMaxRW = 5;          // win <= 11
 constexpr int kMaxD = 256;

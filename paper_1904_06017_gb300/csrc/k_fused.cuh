@@ -55,7 +55,7 @@ struct PairDesc {
 };
 
 constexpr int kBand = 6;   // cost rows per band of the two-pass window sums
-constexpr int kSeg = 7;    // cost columns per horizontal-pass work item
+constexpr int kSeg = 5;    // cost columns per horizontal-pass work item (5: conflict-free LDS.128 strides)
 
 __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -166,21 +166,25 @@ template <> struct CostStore<__nv_bfloat16> {
 //   sI    [QH][QW] f32              scaled reference intensity at the cost positions
 //   sK    [KB][KB] f32              spatial part of the weight exponent
 struct SmemLayout {
-    size_t sref, stgt, cbuf, vband, sstr, sstt, sI, sK, bar, flag, total;
+    size_t sref, stgt, cbuf, cbuf1, vband, sstr, sstt, sI, sK, bar, flag, total;
 };
 
+// nbuf cost buffers (2 for the warp-specialised form), band cost rows per window-sum band.
 __host__ __device__ inline SmemLayout smem_layout(int rb, int m, int dc, int ref_box_w,
-                                                  int tgt_box_w, int box_h, int esize, int tx, int ty)
+                                                  int tgt_box_w, int box_h, int esize, int tx, int ty,
+                                                  int nbuf = 1, int band = kBand)
 {
     SmemLayout L;
     const int QH = ty + 2 * rb, QW = tx + 2 * rb, CW = tx + 2 * m, KB = 2 * rb + 1;
+    const size_t cbytes = align_up((size_t)QH * QW * dc * esize, 128);
     L.sref = 0;
     L.stgt = align_up(L.sref + (size_t)box_h * ref_box_w, 128);
     L.cbuf = align_up(L.stgt + (size_t)box_h * tgt_box_w, 128);
-    L.vband = align_up(L.cbuf + (size_t)QH * QW * dc * esize, 128);
-    L.sstr = align_up(L.vband + (size_t)kBand * CW * dc * 4, 16);
-    L.sstt = align_up(L.sstr + (size_t)kBand * QW * 8, 16);
-    L.sI = align_up(L.sstt + (size_t)kBand * (QW + dc - 1) * 8, 16);
+    L.cbuf1 = L.cbuf + (nbuf > 1 ? cbytes : 0);
+    L.vband = L.cbuf + (size_t)nbuf * cbytes;
+    L.sstr = align_up(L.vband + (size_t)band * CW * dc * 4, 16);
+    L.sstt = align_up(L.sstr + (size_t)band * QW * 8, 16);
+    L.sI = align_up(L.sstt + (size_t)band * (QW + dc - 1) * 8, 16);
     L.sK = align_up(L.sI + (size_t)QH * QW * 4, 16);
     L.bar = align_up(L.sK + (size_t)KB * KB * 4, 8);
     L.flag = L.bar + 8;
@@ -197,11 +201,22 @@ __host__ __device__ inline SmemLayout smem_layout(int rb, int m, int dc, int ref
 //      c = 1 - (n S - S_ref S_tar) r_ref r_tar with the staged window statistics.
 // Every pass issues all of its shared-memory loads before its stores, so the loads of a
 // band are in flight together instead of waiting behind stores they might alias.
-template <int RB, int DC, int RW, typename T, int TX, int TY>
+// Synchronisation of the NT threads that run cost_chunk: the whole CTA (BAR = 0) or a named
+// barrier BAR of NT threads (the producer warps of the warp-specialised form).
+template <int BAR, int NT>
+__device__ __forceinline__ void group_sync()
+{
+    if constexpr (BAR == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NT) : "memory");
+}
+
+template <int RB, int DC, int RW, typename T, int TX, int TY, int NT = kThreads, int BAR = 0,
+          int KBAND = kBand>
 __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sref, const uint8_t *stgt,
                                            T *cbuf, int *vband, int2 *sstr, int2 *sstt,
                                            int x0, int y0, int d0, int tid)
 {
+    constexpr int kThreads = NT, kBand = KBAND;      // the threads and band of this instantiation
     constexpr int WS = 2 * RW + 1;                    // block size w
     constexpr int QH = TY + 2 * RB, QW = TX + 2 * RB;
     constexpr int CW = TX + 2 * (RW + RB);            // product columns
@@ -229,23 +244,30 @@ __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sr
             vacc[k] = s0;
         }
     }
-    for (int yb0 = 0; yb0 < QH; yb0 += kBand) {
-        const int nrows = min(kBand, QH - yb0);
-        // window statistics of this band: loads issued now, stored after the vertical pass
-        int2 stv[NST];
+    // window statistics of a band (global loads, stored to shared memory after the band's
+    // vertical pass); each band's loads are issued one band ahead to hide their latency
+    auto load_stats = [&](int2 (&st)[NST], int yb) {
+        const int nr = min(kBand, QH - yb);
 #pragma unroll
         for (int k = 0; k < NST; ++k) {
             const int e = tid + k * kThreads;
-            stv[k] = make_int2(0, 0);
-            if (e < kBand * (QW + TSW)) {
+            st[k] = make_int2(0, 0);
+            if (yb < QH && e < kBand * (QW + TSW)) {
                 const int r = e / (QW + TSW), c = e - r * (QW + TSW);
-                if (r < nrows) {
-                    const size_t prow = (size_t)(y0 - RB + yb0 + r + a.pad_top) * a.pad_w;
-                    stv[k] = c < QW ? __ldg(a.ref_stats + prow + x0 - RB + a.pad_left + c)
-                                    : __ldg(a.tgt_stats + prow + x0 - RB + a.pad_left - d0 - (DC - 1) + (c - QW));
+                if (r < nr) {
+                    const size_t prow = (size_t)(y0 - RB + yb + r + a.pad_top) * a.pad_w;
+                    st[k] = c < QW ? __ldg(a.ref_stats + prow + x0 - RB + a.pad_left + c)
+                                   : __ldg(a.tgt_stats + prow + x0 - RB + a.pad_left - d0 - (DC - 1) + (c - QW));
                 }
             }
         }
+    };
+    int2 stv[NST];
+    load_stats(stv, 0);
+    for (int yb0 = 0; yb0 < QH; yb0 += kBand) {
+        const int nrows = min(kBand, QH - yb0);
+        int2 stn[NST];
+        load_stats(stn, yb0 + kBand);
         // vertical pass: all product loads of every walker first ...
         int pn[NWV][kBand], po[NWV][kBand];
 #pragma unroll
@@ -290,7 +312,7 @@ __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sr
                 else sstt[r * TSW + (c - QW)] = stv[k];
             }
         }
-        __syncthreads();
+        group_sync<BAR, NT>();
         // horizontal pass: item = (band row, disparity quad, column segment), the segment
         // index fastest so that neighbouring lanes hit distinct shared-memory banks
         const int nitems = nrows * NSEG * NQ;
@@ -341,7 +363,9 @@ __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sr
             for (int j = 0; j < kSeg; ++j)
                 if (j < nout) CostStore<T>::store4(co + (size_t)(xs + j) * DC, out[j]);
         }
-        __syncthreads();
+        group_sync<BAR, NT>();
+#pragma unroll
+        for (int k = 0; k < NST; ++k) stv[k] = stn[k];
     }
 }
 
@@ -575,6 +599,263 @@ k_fused(const __grid_constant__ PairDesc single, const PairDesc *__restrict__ pa
     }  // tile loop
 }
 
+// Named barriers of the warp-specialised kernel (0 is __syncthreads).
+enum { kBarFull0 = 1, kBarFull1 = 2, kBarEmpty0 = 3, kBarEmpty1 = 4, kBarProd = 5 };
+
+__device__ __forceinline__ void named_sync(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void named_arrive(int id, int n)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// The fused kernel with its two phases on separate warps.  Producer warps (kWsProdWarps)
+// compute the costs of chunk k+1 (eq. c, the same integer passes as cost_chunk) into one of
+// two cost buffers while the consumer warps (kWsConsWarps) aggregate chunk k from the other
+// (eq. fbs) and keep the running WTA; "full" and "empty" named barriers hand each buffer
+// over.  Tiles are 64 x 16; the persistent tile loop, the staging and the epilogue are those
+// of k_fused.
+template <int RB, int DC, typename T>
+__global__ void __launch_bounds__(kWsThreads, 1)
+k_fused_ws(const __grid_constant__ PairDesc single, const PairDesc *__restrict__ pairs,
+           const int2 *__restrict__ items, int nitems, int *__restrict__ counter)
+{
+    static_assert(DC % 4 == 0, "DC must be a multiple of 4");
+    constexpr int TX = tile_x(kWsWC), TY = tile_y(kWsWC);
+    constexpr int KB = 2 * RB + 1;
+    constexpr int QH = TY + 2 * RB, QW = TX + 2 * RB;
+    constexpr int NR = kWsPY + 2 * RB;
+    constexpr int NQ = DC / 4;
+    constexpr int NPT = 32 * kWsProdWarps;      // producer threads
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ __align__(16) FusedArgs s_args;
+    __shared__ int s_item;
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ int s_flag;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const FusedArgs &a = s_args;
+    uint64_t *bar = &s_bar;
+    int *flag = &s_flag;
+    if (tid == 0) mbar_init(bar, 1);
+
+    for (int iter = 0;; ++iter) {
+        if (tid == 0) s_item = pairs ? atomicAdd(counter, 1) : (int)blockIdx.x + iter * (int)gridDim.x;
+        __syncthreads();
+        const int item = s_item;
+        if (item >= nitems) return;
+        int p = 0, tx, ty;
+        if (pairs) {
+            const int2 it = items[item];
+            p = it.x;
+            tx = it.y & 0xffff;
+            ty = it.y >> 16;
+        } else {
+            tx = item % single.ntx;
+            ty = item / single.ntx;
+        }
+        const PairDesc *pd = pairs ? pairs + p : &single;
+        {
+            const int *src = reinterpret_cast<const int *>(&pd->a);
+            int *dst = reinterpret_cast<int *>(&s_args);
+            for (int i = tid; i < (int)(sizeof(FusedArgs) / 4); i += kWsThreads) dst[i] = src[i];
+        }
+        __syncthreads();
+
+        const int RP = a.ref_box_w, TP = a.tgt_box_w;
+        const SmemLayout L = smem_layout(RB, a.m, DC, RP, TP, a.box_h, (int)sizeof(T), TX, TY, 2, kWsBand);
+        uint8_t *sref = smem + L.sref;
+        uint8_t *stgt = smem + L.stgt;
+        T *cbuf0 = reinterpret_cast<T *>(smem + L.cbuf);
+        T *cbuf1 = reinterpret_cast<T *>(smem + L.cbuf1);
+        int *vband = reinterpret_cast<int *>(smem + L.vband);
+        int2 *sstr = reinterpret_cast<int2 *>(smem + L.sstr);
+        int2 *sstt = reinterpret_cast<int2 *>(smem + L.sstt);
+        float *sI = reinterpret_cast<float *>(smem + L.sI);
+        float *sK = reinterpret_cast<float *>(smem + L.sK);
+        const int x0 = tx * TX, y0 = ty * TY;
+
+        // ---- 1. stage the image tiles with TMA (bounded wait, as in k_fused)
+        for (int i = tid; i < KB * KB; i += kWsThreads) sK[i] = a.K[i];
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(bar, (uint32_t)(a.box_h * (RP + TP)));
+            tma_load_3d(sref, &pd->tmap_ref, 0, (x0 + a.ref_box_x) / 16, y0, bar);
+            tma_load_3d(stgt, &pd->tmap_tgt, 0, x0 / 16, y0, bar);
+            const long long t0 = clock64();
+            bool ok = false;
+            while (!(ok = mbar_try_wait(bar, (uint32_t)(iter & 1))) && clock64() - t0 < (1ll << 31)) {
+            }
+            *flag = ok ? 1 : 0;
+            if (!ok) atomicOr(a.status, 1);
+        }
+        __syncthreads();
+        if (*flag == 0) return;
+
+        const int rw = a.rw;
+        for (int i = tid; i < QH * QW; i += kWsThreads) {
+            const int yq = i / QW, xq = i - yq * QW;
+            const int ix = x0 - RB + xq, iy = y0 - RB + yq;
+            float v = 1e18f;
+            if (ix >= 0 && ix < a.W && iy >= 0 && iy < a.H)
+                v = (float)sref[(yq + rw) * RP + a.ref_e + xq + rw] * a.iscale;
+            sI[i] = v;
+        }
+        __syncthreads();
+
+        const int nchunk = (a.D + DC - 1) / DC;
+        if (warp < kWsProdWarps) {
+            // ---- producers: costs of chunk k into buffer k & 1, once the consumers are done
+            // with what that buffer held (chunk k - 2)
+            for (int k = 0; k < nchunk; ++k) {
+                const int b = k & 1;
+                if (k >= 2) named_sync(b ? kBarEmpty1 : kBarEmpty0, kWsThreads);
+                T *cb = b ? cbuf1 : cbuf0;
+                switch (rw) {
+                case 1: cost_chunk<RB, DC, 1, T, TX, TY, NPT, kBarProd, kWsBand>(a, sref, stgt, cb, vband, sstr, sstt, x0, y0, k * DC, tid); break;
+                case 2: cost_chunk<RB, DC, 2, T, TX, TY, NPT, kBarProd, kWsBand>(a, sref, stgt, cb, vband, sstr, sstt, x0, y0, k * DC, tid); break;
+                case 3: cost_chunk<RB, DC, 3, T, TX, TY, NPT, kBarProd, kWsBand>(a, sref, stgt, cb, vband, sstr, sstt, x0, y0, k * DC, tid); break;
+                case 4: cost_chunk<RB, DC, 4, T, TX, TY, NPT, kBarProd, kWsBand>(a, sref, stgt, cb, vband, sstr, sstt, x0, y0, k * DC, tid); break;
+                default: cost_chunk<RB, DC, 5, T, TX, TY, NPT, kBarProd, kWsBand>(a, sref, stgt, cb, vband, sstr, sstt, x0, y0, k * DC, tid); break;
+                }
+                __threadfence_block();
+                named_arrive(b ? kBarFull1 : kBarFull0, kWsThreads);
+            }
+            // match the consumers' "empty" arrivals of the last two chunks
+            for (int k = nchunk < 2 ? 0 : nchunk - 2; k < nchunk; ++k)
+                named_sync((k & 1) ? kBarEmpty1 : kBarEmpty0, kWsThreads);
+        } else {
+            // ---- consumers: aggregation of chunk k, running WTA, then release the buffer
+            const int cw = warp - kWsProdWarps;
+            const int xt = (cw & 1) * 32 + lane;
+            const int yt0 = (cw >> 1) * kWsPY;
+            float Ip[kWsPY];
+#pragma unroll
+            for (int i = 0; i < kWsPY; ++i) Ip[i] = sI[(yt0 + i + RB) * QW + xt + RB];
+            float best[kWsPY], bm1[kWsPY], bp1[kWsPY], prev[kWsPY];
+            int bd[kWsPY];
+#pragma unroll
+            for (int i = 0; i < kWsPY; ++i) {
+                best[i] = __int_as_float(0x7f800000);
+                bm1[i] = bp1[i] = prev[i] = best[i];
+                bd[i] = -1;
+            }
+            const size_t crow = (size_t)QW * DC;
+            for (int k = 0; k < nchunk; ++k) {
+                const int b = k & 1;
+                const int d0 = k * DC;
+                named_sync(b ? kBarFull1 : kBarFull0, kWsThreads);
+                const T *cbuf = b ? cbuf1 : cbuf0;
+                float2 acc[kWsPY][DC / 2];
+#pragma unroll
+                for (int i = 0; i < kWsPY; ++i)
+#pragma unroll
+                    for (int q = 0; q < DC / 2; ++q) acc[i][q] = make_float2(0.f, 0.f);
+                for (int dx = 0; dx < KB; ++dx) {
+                    float Kr[KB];
+#pragma unroll
+                    for (int j = 0; j < KB; ++j) Kr[j] = sK[dx * KB + j];
+                    const T *cb = cbuf + ((size_t)yt0 * QW + xt + dx) * DC;
+                    const float *ib = sI + yt0 * QW + xt + dx;
+                    float2 q[2 * NQ];
+#pragma unroll
+                    for (int j = 0; j < NQ; ++j) CostStore<T>::load4(cb + 4 * j, q[2 * j], q[2 * j + 1]);
+                    float wgt[kWsPY];
+                    {
+                        const float Iq = ib[0];
+#pragma unroll
+                        for (int i = 0; i < kWsPY; ++i) {
+                            const int dy = 0 - i;
+                            if (dy >= 0 && dy <= 2 * RB) {
+                                const float t = Iq - Ip[i];
+                                wgt[i] = ex2_approx(fmaf(-t, t, Kr[dy]));
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        float2 qn[2 * NQ];
+                        float wn[kWsPY];
+                        if (r + 1 < NR) {
+#pragma unroll
+                            for (int j = 0; j < NQ; ++j)
+                                CostStore<T>::load4(cb + (r + 1) * crow + 4 * j, qn[2 * j], qn[2 * j + 1]);
+                            const float Iq = ib[(r + 1) * QW];
+#pragma unroll
+                            for (int i = 0; i < kWsPY; ++i) {
+                                const int dy = r + 1 - i;
+                                if (dy >= 0 && dy <= 2 * RB) {
+                                    const float t = Iq - Ip[i];
+                                    wn[i] = ex2_approx(fmaf(-t, t, Kr[dy]));
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int i = 0; i < kWsPY; ++i) {
+                            const int dy = r - i;
+                            if (dy >= 0 && dy <= 2 * RB) {
+                                const float2 w2 = make_float2(wgt[i], wgt[i]);
+#pragma unroll
+                                for (int j = 0; j < 2 * NQ; ++j) acc[i][j] = __ffma2_rn(w2, q[j], acc[i][j]);
+                            }
+                        }
+                        if (r + 1 < NR) {
+#pragma unroll
+                            for (int j = 0; j < 2 * NQ; ++j) q[j] = qn[j];
+#pragma unroll
+                            for (int i = 0; i < kWsPY; ++i) wgt[i] = wn[i];
+                        }
+                    }
+                }
+                // the buffer is free once every consumer has read it
+                named_arrive(b ? kBarEmpty1 : kBarEmpty0, kWsThreads);
+#pragma unroll
+                for (int i = 0; i < kWsPY; ++i)
+#pragma unroll
+                    for (int dd = 0; dd < DC; ++dd) {
+                        const int d = d0 + dd;
+                        if (d >= a.D) break;
+                        const float v = (dd & 1) ? acc[i][dd >> 1].y : acc[i][dd >> 1].x;
+                        if (v < best[i]) {
+                            best[i] = v;
+                            bd[i] = d;
+                            bm1[i] = prev[i];
+                        } else if (d == bd[i] + 1) {
+                            bp1[i] = v;
+                        }
+                        prev[i] = v;
+                    }
+            }
+            // ---- epilogue: eq. (subpixel), add back s_i(v), validity from the row table
+#pragma unroll
+            for (int i = 0; i < kWsPY; ++i) {
+                const int u = x0 + xt, v = y0 + yt0 + i;
+                if (u >= a.W || v >= a.H) continue;
+                const int4 rt = __ldg(a.row_tab + v);
+                float delta = 0.f;
+                if (bd[i] > 0 && bd[i] < a.D - 1) {
+                    const float den = 2.f * bm1[i] + 2.f * bp1[i] - 4.f * best[i];
+                    if (den > 0.f) delta = (bm1[i] - bp1[i]) / den;
+                }
+                const size_t o = (size_t)v * a.W + u;
+                a.disp[o] = (float)bd[i] + delta + (float)rt.x;
+                if (a.wta) a.wta[o] = bd[i];
+                if (a.valid) {
+                    const int ulo = a.m + a.D - 1 + max(0, rt.y);
+                    const int uhi = a.W - 1 - a.m + min(0, rt.z);
+                    a.valid[o] = (uint8_t)(v >= a.m && v <= a.H - 1 - a.m && u >= ulo && u <= uhi);
+                }
+            }
+        }
+        // every warp leaves the tile together: the next tile's copies overwrite the buffers
+        __syncthreads();
+    }
+}
+
 typedef void (*FusedKernel)(const PairDesc, const PairDesc *, const int2 *, int, int *);
 
 template <int DC, typename T, int WC>
@@ -599,6 +880,7 @@ FusedKernel pick_fused_f32(int rb, int dc, int wc);    // k_fused_f32.cu: WC = 2
 FusedKernel pick_fused_f32_tiles(int rb, int dc, int wc);  // k_fused_f32_tiles.cu: WC in {1, 4}, DC = 12
 FusedKernel pick_fused_f16(int rb, int dc, int wc);    // k_fused_f16.cu: WC = 2, DC = 12
 FusedKernel pick_fused_bf16(int rb, int dc, int wc);   // k_fused_bf16.cu: WC = 2, DC = 12
+FusedKernel pick_fused_ws(int rb, int dc);             // k_fused_ws.cu: warp-specialised, FP32, DC = 12
 FusedKernel pick_fused(int cost_dtype, int rb, int dc, int wc);
 // The descriptor of one context for one call (k_fused_f32.cu).
 void fill_pair_desc(const stereo_ctx *ctx, float *disp, int32_t *wta, uint8_t *valid, PairDesc &d);

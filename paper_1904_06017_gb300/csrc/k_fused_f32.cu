@@ -16,6 +16,7 @@ FusedKernel pick_fused_f32(int rb, int dc, int wc)
 
 FusedKernel pick_fused(int cost_dtype, int rb, int dc, int wc)
 {
+    if (wc == kWsWC) return cost_dtype == STEREO_F32 && rb <= kWsMaxRB ? pick_fused_ws(rb, dc) : nullptr;
     switch (cost_dtype) {
     case STEREO_F32: return pick_fused_f32(rb, dc, wc);
     case STEREO_F16: return pick_fused_f16(rb, dc, wc);
@@ -26,7 +27,10 @@ FusedKernel pick_fused(int cost_dtype, int rb, int dc, int wc)
 
 size_t fused_smem_bytes(const Geometry &g)
 {
-    return smem_layout(g.rb, g.m, g.dc, g.ref_box_w, g.tgt_box_w, g.box_h, g.esize, g.tx, g.ty).total;
+    const bool ws = g.wc == kWsWC;
+    return smem_layout(g.rb, g.m, g.dc, g.ref_box_w, g.tgt_box_w, g.box_h, g.esize, g.tx, g.ty, ws ? 2 : 1,
+                       ws ? kWsBand : kBand)
+        .total;
 }
 
 static FusedKernel pick(const stereo_ctx *ctx)
@@ -93,7 +97,7 @@ int launch_fused(stereo_ctx *ctx, const float *shift, float *disp, int32_t *wta,
     PairDesc d;
     fill_pair_desc(ctx, disp, wta, valid, d);
     const int ntiles = g.ntx * g.nty;
-    k<<<ntiles, kThreads, g.smem_bytes, s>>>(d, nullptr, nullptr, ntiles, nullptr);
+    k<<<ntiles, fused_threads(g.wc), g.smem_bytes, s>>>(d, nullptr, nullptr, ntiles, nullptr);
     return cuda_error(cudaGetLastError(), "k_fused launch");
 }
 
