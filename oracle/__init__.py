@@ -56,6 +56,11 @@ def lib():
         _lib.oracle_stereo_rows.argtypes = [P, P, P, I, I, I, I, I, I, Dd, Dd, I, I, P, P, P, P]
         _lib.oracle_stereo_rows.restype = I
         _lib.oracle_valid_mask.argtypes = [I, I, I, I, I, P, P]
+        _lib.oracle_cost_tar.argtypes = [P, P, I, I, I, I, I, I, I]
+        _lib.oracle_cost_tar.restype = Dd
+        _lib.oracle_target_view_rows.argtypes = [P, P, I, I, I, I, I, I, Dd, Dd, I, I, P, P, P]
+        _lib.oracle_target_view_rows.restype = I
+        _lib.oracle_lr_check.argtypes = [I, I, P, P, Dd, P]
     return _lib
 
 
@@ -167,3 +172,40 @@ def valid_mask(W, H, D, win, bil, shift):
     m = np.empty((H, W), np.uint8)
     lib().oracle_valid_mask(int(W), int(H), int(D), win // 2, bil // 2, _ptr(shift), _ptr(m))
     return m
+
+
+def cost_tar(ref, tgtw, u, v, d, win):
+    """The target view's eq. (c) at target pixel (u, v) and disparity d: the target block
+    around (u, v) against the reference block around (u + d, v)."""
+    ref, tgtw = _u8(ref), _u8(tgtw)
+    H, W = ref.shape
+    return float(lib().oracle_cost_tar(_ptr(ref), _ptr(tgtw), W, H, W, int(u), int(v), int(d), win // 2))
+
+
+def target_view(ref, tgtw, D, win, bil, sigma0, sigma1, rows=None):
+    """Target-view WTA (the second cost volume of §3.2.1, the warped target as the
+    aggregation guide) for rows [v0, v1).  Returns (dstar, e_best, e_second), each
+    [v1 - v0][W], u a column of the warped target."""
+    ref, tgtw = _u8(ref), _u8(tgtw)
+    H, W = ref.shape
+    v0, v1 = (0, H) if rows is None else rows
+    n = v1 - v0
+    dstar = np.empty((n, W), np.int32)
+    eb = np.empty((n, W), np.float64)
+    es = np.empty((n, W), np.float64)
+    rc = lib().oracle_target_view_rows(_ptr(ref), _ptr(tgtw), W, H, W, int(D), win // 2, bil // 2,
+                                       float(sigma0), float(sigma1), int(v0), int(v1), _ptr(dstar),
+                                       _ptr(eb), _ptr(es))
+    if rc != 0:
+        raise MemoryError("oracle_target_view_rows: out of memory")
+    return dstar, eb, es
+
+
+def lr_check(dref, dtar, delta_r=1.0):
+    """eq. (lrc) on integer disparity maps of the warped pair: 1 where the pixel is kept."""
+    dref = np.ascontiguousarray(dref, dtype=np.int32)
+    dtar = np.ascontiguousarray(dtar, dtype=np.int32)
+    H, W = dref.shape
+    ok = np.empty((H, W), np.uint8)
+    lib().oracle_lr_check(W, H, _ptr(dref), _ptr(dtar), float(delta_r), _ptr(ok))
+    return ok

@@ -20,7 +20,13 @@
  *     factor 2), the guide image is the reference, and neighbours outside the image
  *     are left out of both sums;
  *   - WTA: the lowest d wins a tie; eq. (subpixel) is applied to the aggregated cost
- *     E; delta = 0 when d* is 0 or D-1 or when the denominator is not positive.
+ *     E; delta = 0 when d* is 0 or D-1 or when the denominator is not positive;
+ *   - the target view (the second cost volume of §3.2.1) matches the target block around
+ *     x against the reference block around x + [d, 0] with eq. (c), and its aggregation
+ *     takes the target image as the guide of eq. (omega_s);
+ *   - eq. (lrc) compares the integer WTA disparities of the two views before the
+ *     sub-pixel step, in the warped target's columns (the row shift is added to both
+ *     disparities and cancels); a partner column outside the image fails the check.
  * Layouts: images are row-major uint8 with a row pitch in bytes; cost and
  * aggregated volumes are double [H][W][D]; disparity maps are double [H][W].
  */
@@ -234,4 +240,57 @@ void oracle_valid_mask(int W, int H, int D, int rw, int rb, const float *shift, 
             mask[(size_t)v * W + u] = (uint8_t)ok;
         }
     }
+}
+
+/* The target view: the cost of target pixel x = (u, v) at disparity d, i.e. eq. (c) with the
+ * target block around x and the reference block around x + [d, 0] -- eq. (c) with the roles of
+ * the two images exchanged and the disparity negated. */
+double oracle_cost_tar(const uint8_t *ref, const uint8_t *tgtw, int W, int H, int pitch,
+                       int u, int v, int d, int rw)
+{
+    return oracle_cost(tgtw, ref, W, H, pitch, u, v, -d, rw);
+}
+
+/* Target-view WTA for rows [v0, v1): target-view costs of rows [v0 - rb, v1 + rb), eq. (fbs)
+ * with the warped target as the guide, lowest d on ties.  dstar / ebest / esecond are
+ * indexed [(v - v0)][u] (u a column of the warped target).  Returns 0, or -1 when out of
+ * memory. */
+int oracle_target_view_rows(const uint8_t *ref, const uint8_t *tgtw, int W, int H, int pitch,
+                            int D, int rw, int rb, double sigma0, double sigma1, int v0, int v1,
+                            int32_t *dstar, double *ebest, double *esecond)
+{
+    int cv0 = v0 - rb < 0 ? 0 : v0 - rb;
+    int cv1 = v1 + rb > H ? H : v1 + rb;
+    double *c = (double *)malloc(sizeof(double) * (size_t)(cv1 - cv0) * W * D);
+    double *E = (double *)malloc(sizeof(double) * (size_t)(v1 - v0) * W * D);
+    float *zero = (float *)calloc((size_t)H, sizeof(float));
+    if (!c || !E || !zero) { free(c); free(E); free(zero); return -1; }
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int v = cv0; v < cv1; ++v)
+        for (int u = 0; u < W; ++u)
+            for (int d = 0; d < D; ++d)
+                c[((size_t)(v - cv0) * W + u) * D + d] = oracle_cost_tar(ref, tgtw, W, H, pitch, u, v, d, rw);
+    oracle_aggregate_rows(tgtw, W, H, pitch, D, rb, sigma0, sigma1, c, cv0, cv1, v0, v1, E, NULL);
+    oracle_wta_rows(W, D, E, zero, v0, v1, NULL, dstar, ebest, esecond);
+    free(c);
+    free(E);
+    free(zero);
+    return 0;
+}
+
+/* eq. (lrc): reference pixel (u, v) keeps its disparity when
+ * (d_ref(u, v) - d_tar(u - d_ref(u, v), v))^2 <= delta_r; both maps are integer WTA disparities
+ * [H][W] of the warped pair, and a partner column u - d_ref < 0 fails. */
+void oracle_lr_check(int W, int H, const int32_t *dref, const int32_t *dtar, double delta_r, uint8_t *ok)
+{
+    for (int v = 0; v < H; ++v)
+        for (int u = 0; u < W; ++u) {
+            int dr = dref[(size_t)v * W + u], x = u - dr;
+            int pass = 0;
+            if (x >= 0 && x < W) {
+                double diff = (double)(dr - dtar[(size_t)v * W + x]);
+                pass = diff * diff <= delta_r;
+            }
+            ok[(size_t)v * W + u] = (uint8_t)pass;
+        }
 }

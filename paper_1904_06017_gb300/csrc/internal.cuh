@@ -12,9 +12,9 @@
 
 namespace sgb {
 
-// Tiling of the fused kernel: a CTA of 8 warps owns a tile of output pixels; lane =
-// column, each warp covers 32 columns x kPY rows, and WC warp columns x (8 / WC) warp rows
-// give tiles of 32 x 64 (WC = 1), 64 x 32 (WC = 2, the default) or 128 x 16 (WC = 4).
+// Tiling of the fused kernel: a CTA of kWarps warps owns a tile of output pixels; lane =
+// column, each warp covers 32 columns x kPY rows, and WC warp columns x (kWarps / WC) warp rows
+// give tiles of 32 x 72 (WC = 1), 64 x 36 (WC = 2, the default) or 128 x 18 (WC = 4).
 constexpr int kPY = 6;
 constexpr int kWarps = 12;
 constexpr int kThreads = 32 * kWarps;
