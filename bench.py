@@ -469,6 +469,25 @@ def run_ours(args):
                           "fused_ms": fms / max(nf, 1), "steps": nvar,
                           "wta_disagree_vs_f32": float(np.mean(wv != wta_ref))}
 
+    # ---- target view + LR-consistency check (eq. lrc) on the same pair
+    wta_r = torch.empty((H, W), dtype=torch.int32, device=dev)
+    lr_ok = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    st.warp_target(tgt, shift, tw)
+    st.cost_aggregate_wta(ref, tw, shift, disp, wta_r, valid)
+    st.lr_check(ref, tw, shift, wta_r, lr_ok)
+    evl = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nvar)]
+    for i in range(nvar):
+        flush.fill_(i & 0xFF)
+        evl[i][0].record(stream)
+        st.lr_check(ref, tw, shift, wta_r, lr_ok)
+        evl[i][1].record(stream)
+    torch.cuda.synchronize()
+    st.check_device_status()
+    vm = valid.bool()
+    lr = {"ms_per_call": sum(a.elapsed_time(b) for a, b in evl) / nvar, "calls": nvar, "delta_r": 1.0,
+          "kept_fraction": float(lr_ok.float().mean()),
+          "kept_fraction_of_valid": float(lr_ok[vm].float().mean()) if bool(vm.any()) else None}
+
     if rank != 0:
         st.close()
         if world > 1:
@@ -499,7 +518,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "width": W, "height": H, "max_disp": D, "win": win, "bil": bil,
                        "pairs_per_step_per_gpu": 1, "l2": "flushed before each step (256 MiB write, untimed)"},
             "pairs_per_s": pairs_per_s, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-            "roofline": roof, "clocks": clk, "cost_storage_variants": variants,
+            "roofline": roof, "clocks": clk, "cost_storage_variants": variants, "lr_check": lr,
             "dt": {"psi": r.psi, "alpha0": r.alpha0, "alpha1": r.alpha1, "iters": r.iters, "status": r.status,
                    "true_roll": s.roll}}
     if not args.no_batch:

@@ -256,6 +256,31 @@ int stereo_disparity_transform_noalloc(int32_t width, int32_t height, const floa
                                        float *disp_out_dev, stereo_dt_result *res_dev,
                                        stereo_stream_t stream);
 
+/* ---------------------------------------------------------------- LR-consistency check
+ * §3.2.1 stores the matching costs in two volumes, one per view, and §3.2.2 removes occluded
+ * reference pixels with eq. (lrc): p is dropped when
+ *     (l_ref(p) - l_tar(p - [l_ref(p), 0]))^2 > delta_r        (the paper takes delta_r = 1).
+ * This call computes the target view and the check for a pair whose reference view already
+ * ran through stereo_cost_aggregate_wta (with a wta_dev output):
+ *   - the target view matches the w x w block of the warped target around x against the
+ *     reference block around x + [d, 0] (eq. c with the images exchanged, the same clamp and
+ *     statistics readings), aggregates with eq. (omega_s)/(fbs) guided by the warped target,
+ *     and takes the lowest d of the minimum (WTA);
+ *   - both views are compared as integer WTA disparities before the sub-pixel step, in the
+ *     warped target's columns: the row shift s_i(v) is added to both and cancels;
+ *   - a partner column u - wta_ref(u) outside the image fails the check.
+ * ref_dev, tgt_warped_dev, shift_dev: the inputs of that reference-view call; wta_ref_dev:
+ * its int32 [H][W] output.  wta_tgt_dev: int32 [H][W] target-view disparities (column u of
+ * the warped target), or NULL.  lr_ok_dev: uint8 [H][W], 1 where the pixel is kept.
+ * delta_r: the threshold, >= 0.  Runs the fused kernel a second time, on the horizontally
+ * mirrored pair with the roles of the images exchanged, which is the target view exactly;
+ * it reuses the context's staging buffers.  Asynchronous on the stream.
+ * Errors: STEREO_EINVAL (null pointer, negative or non-finite delta_r, a context made by a
+ * batch), STEREO_ECUDA. */
+int stereo_lr_check(stereo_ctx *ctx, const uint8_t *ref_dev, const uint8_t *tgt_warped_dev,
+                    const float *shift_dev, const int32_t *wta_ref_dev, int32_t *wta_tgt_dev,
+                    uint8_t *lr_ok_dev, float delta_r, stereo_stream_t stream);
+
 /* ---------------------------------------------------------------- diagnostics */
 
 /* Synchronise the stream, read and clear the context's device status word.

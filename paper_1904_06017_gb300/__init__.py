@@ -23,7 +23,7 @@ __all__ = [
     "stereo_cost_volume", "stereo_aggregate_volume", "stereo_wta_volume",
     "stereo_check_device_status", "stereo_profile_enable", "stereo_profile_read",
     "stereo_fp32_peak_probe", "stereo_last_error", "stereo_version", "Stereo",
-    "stereo_disparity_transform_noalloc", "stereo_pair_desc", "stereo_batch_params",
+    "stereo_disparity_transform_noalloc", "stereo_lr_check", "stereo_pair_desc", "stereo_batch_params",
     "stereo_batch_params_default", "stereo_batch_create", "stereo_batch_run", "stereo_batch_config",
     "stereo_batch_check_device_status", "stereo_batch_destroy", "StereoBatch",
     "STEREO_OK", "STEREO_EINVAL", "STEREO_ENOMEM", "STEREO_ECUDA", "STEREO_ETIMEOUT",
@@ -119,6 +119,7 @@ def load_library():
         "stereo_batch_config": [P, P, P, P, P],
         "stereo_batch_check_device_status": [P],
         "stereo_batch_destroy": [P],
+        "stereo_lr_check": [P, P, P, P, P, P, P, F, P],
         "stereo_diff_params_default": [P],
         "stereo_softargmin_workspace_bytes": [P, P],
         "stereo_softargmin_fwd": [P, P, P, P, P, P, ctypes.c_size_t, P],
@@ -244,6 +245,13 @@ def stereo_disparity_transform_noalloc(width, height, disp, mask, psi_init, delt
         float(lambda0), float(delta_psi), int(max_iters), _ptr(disp_out), _ptr(res), _stream(stream)))
 
 
+def stereo_lr_check(ctx, ref, tgt_warped, shift, wta_ref, lr_ok, wta_tgt=None, delta_r=1.0, stream=None):
+    """Target view and eq. (lrc) for a pair whose reference view already ran (wta_ref is
+    that call's int32 WTA output); lr_ok receives 1 where a pixel is kept."""
+    _check(load_library().stereo_lr_check(ctx, _ptr(ref), _ptr(tgt_warped), _ptr(shift), _ptr(wta_ref),
+                                          _ptr(wta_tgt), _ptr(lr_ok), float(delta_r), _stream(stream)))
+
+
 def stereo_cost_volume(ctx, ref, tgt_warped, cost, stream=None):
     _check(load_library().stereo_cost_volume(ctx, _ptr(ref), _ptr(tgt_warped), _ptr(cost),
                                              _stream(stream)))
@@ -317,6 +325,9 @@ class Stereo:
 
     def disparity_transform(self, disp, mask, psi_init, delta_t, out, res=None, stream=None):
         return stereo_disparity_transform(self.ctx, disp, mask, psi_init, delta_t, out, res, stream)
+
+    def lr_check(self, ref, tgt_warped, shift, wta_ref, lr_ok, wta_tgt=None, delta_r=1.0, stream=None):
+        stereo_lr_check(self.ctx, ref, tgt_warped, shift, wta_ref, lr_ok, wta_tgt, delta_r, stream)
 
     def cost_volume(self, ref, tgt_warped, cost, stream=None):
         stereo_cost_volume(self.ctx, ref, tgt_warped, cost, stream)

@@ -109,6 +109,10 @@ static void free_ctx(stereo_ctx *c)
     cudaFree(c->dt_coef);
     cudaFree(c->res_dev);
     cudaFree(c->status_dev);
+    cudaFree(c->lr_ref);
+    cudaFree(c->lr_tgt);
+    cudaFree(c->lr_wta);
+    cudaFree(c->lr_disp);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     delete c;
 }
@@ -140,7 +144,19 @@ int stereo_params_default(stereo_params *p)
 
 int stereo_create(const stereo_params *p, stereo_ctx **out)
 {
-    return create_context(p, 0, 0, out);
+    int rc = create_context(p, 0, 0, out);
+    if (rc) return rc;
+    stereo_ctx *c = *out;
+    const size_t img = (size_t)c->p.height * c->p.pitch, map = (size_t)c->p.height * c->p.width;
+    if ((rc = cuda_error(cudaMalloc(&c->lr_ref, img), "cudaMalloc lr_ref")) ||
+        (rc = cuda_error(cudaMalloc(&c->lr_tgt, img), "cudaMalloc lr_tgt")) ||
+        (rc = cuda_error(cudaMalloc(&c->lr_wta, map * sizeof(int32_t)), "cudaMalloc lr_wta")) ||
+        (rc = cuda_error(cudaMalloc(&c->lr_disp, map * sizeof(float)), "cudaMalloc lr_disp"))) {
+        free_ctx(c);
+        *out = nullptr;
+        return rc;
+    }
+    return STEREO_OK;
 }
 
 }  // extern "C"

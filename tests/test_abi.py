@@ -107,6 +107,7 @@ def test_null_pointers_rejected(lib):
     assert lib.stereo_cost_aggregate_wta(None, None, None, None, None, None, None, None) == sg.STEREO_EINVAL
     assert lib.stereo_disparity_transform(None, None, None, 0.0, 0.0, None, None, None) == sg.STEREO_EINVAL
     assert lib.stereo_destroy(None) == sg.STEREO_OK
+    assert lib.stereo_lr_check(None, None, None, None, None, None, None, 1.0, None) == sg.STEREO_EINVAL
 
 
 def test_version(lib):
