@@ -8,5 +8,6 @@ from .road_pairs import (  # noqa: F401
     make_batch_scenes,
     texture,
     crop_pair,
+    make_roll_sequence,
     jitter,
 )

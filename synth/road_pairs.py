@@ -218,3 +218,11 @@ def jitter(img: np.ndarray, seed: int, amp: float = 0.5) -> np.ndarray:
     """img as float64 plus uniform noise in [-amp, amp): grey levels off the integer grid."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return img.astype(np.float64) + rng.uniform(-amp, amp, size=img.shape)
+
+
+def make_roll_sequence(n_frames: int, width: int, height: int, D: int, seed: int, roll0_deg: float,
+                       drift_deg: float, **kw) -> list:
+    """A video of one road: n_frames pairs drawn from the same seed (same texture, potholes
+    and noise), the roll angle moving by drift_deg per frame from roll0_deg."""
+    return [make_scene(width, height, D, seed, roll=math.radians(roll0_deg + t * drift_deg), **kw)
+            for t in range(n_frames)]
