@@ -13,7 +13,9 @@ aggregated cost:
 with y_p(psi) = v cos(psi) - u sin(psi) (eq. y).  Every step is a plain PyTorch float64
 operation, so torch.autograd gives the exact adjoint; the tests pin it to central finite
 differences.  The target enters through the row-shift warp of §3.1 (a gather whose adjoint
-is the matching scatter), so gradients reach the original target image.
+is the matching scatter), so gradients reach the original target image.  With the
+linear-interpolation warp (warp_mode 1) a fractional shift s(v) is read between the two
+neighbouring target columns and added back unrounded, so gradients reach s(v) as well.
 
 refine_roll() is gradient descent on the roll angle with the line fit eliminated
 (alpha = alpha(psi) of eq. alpha3 at every step, so the psi-gradient of eq. E2 is the
@@ -40,6 +42,19 @@ def warp(tgt, shift):
     si = torch.from_numpy(round_shift(shift))
     cols = torch.clamp(torch.arange(W)[None, :] - si[:, None], 0, W - 1)
     return torch.gather(tgt, 1, cols)
+
+
+def warp_linear(tgt, shift):
+    """§3.1 with a fractional shift read by linear interpolation: the point u - s(v) of target
+    row v, out = (1 - f) tgt(clamp(x0)) + f tgt(clamp(x0 + 1)) with x0 = floor(u - s), f the
+    fraction.  `shift` is a float64 tensor (it may require grad) holding float32 values."""
+    H, W = tgt.shape
+    x = torch.arange(W, dtype=torch.float64)[None, :] - shift[:, None]
+    x0 = torch.floor(x.detach())
+    f = x - x0
+    i0 = torch.clamp(x0.long(), 0, W - 1)
+    i1 = torch.clamp(x0.long() + 1, 0, W - 1)
+    return (1.0 - f) * torch.gather(tgt, 1, i0) + f * torch.gather(tgt, 1, i1)
 
 
 def _window_sd(blocks):
@@ -116,8 +131,20 @@ def dt_energy(l, mask, psi, alpha0, alpha1):
     return (r * r).sum()
 
 
-def disparity(ref, tgt, shift, D, win, bil, sigma0, sigma1, T):
-    """Warp, cost, aggregation and soft-argmin: l [H, W]."""
+def soft_argmin_linear(E, shift, T):
+    """l(p) = sum_d d softmax_d(-E(p,d)/T) + s(v) with the fractional shift added back."""
+    D = E.shape[0]
+    P = torch.softmax(-E / T, dim=0)
+    d = torch.arange(D, dtype=E.dtype)[:, None, None]
+    return (P * d).sum(0) + shift[:, None]
+
+
+def disparity(ref, tgt, shift, D, win, bil, sigma0, sigma1, T, warp_mode=0):
+    """Warp, cost, aggregation and soft-argmin: l [H, W].  warp_mode 0: the rounded shift of
+    §3.1 (`shift` a float32 array); 1: the linear-interpolation warp (`shift` a float64 tensor)."""
+    if warp_mode == 1:
+        c = cost_volume(ref, warp_linear(tgt, shift), D, win)
+        return soft_argmin_linear(aggregate(ref, c, bil, sigma0, sigma1), shift, T)
     c = cost_volume(ref, warp(tgt, shift), D, win)
     return soft_argmin(aggregate(ref, c, bil, sigma0, sigma1), shift, T)
 
@@ -138,6 +165,25 @@ def disparity_vjp(ref, tgt, shift, D, win, bil, sigma0, sigma1, T, grad_l):
     l = disparity(r, t, shift, D, win, bil, sigma0, sigma1, T)
     (l * _t(grad_l)).sum().backward()
     return l.detach().numpy(), r.grad.numpy(), t.grad.numpy()
+
+
+def _shift_t(shift, grad=False):
+    return torch.tensor(np.asarray(shift, np.float32).astype(np.float64), dtype=torch.float64,
+                        requires_grad=grad)
+
+
+def disparity_linear_value(ref, tgt, shift, D, win, bil, sigma0, sigma1, T):
+    """l with the linear-interpolation warp, as a float64 numpy array."""
+    with torch.no_grad():
+        return disparity(_t(ref), _t(tgt), _shift_t(shift), D, win, bil, sigma0, sigma1, T, 1).numpy()
+
+
+def disparity_linear_vjp(ref, tgt, shift, D, win, bil, sigma0, sigma1, T, grad_l):
+    """(l, dS/dref, dS/dtgt, dS/dshift) with the linear-interpolation warp."""
+    r, t, s = _t(ref, True), _t(tgt, True), _shift_t(shift, True)
+    l = disparity(r, t, s, D, win, bil, sigma0, sigma1, T, 1)
+    (l * _t(grad_l)).sum().backward()
+    return l.detach().numpy(), r.grad.numpy(), t.grad.numpy(), s.grad.numpy()
 
 
 def energy_value(l, mask, psi, alpha0, alpha1):

@@ -238,3 +238,51 @@ def test_refine_roll_on_the_soft_argmin_of_a_crop(crop):
     mask = oracle.valid_mask(W, H, D, WIN, BIL, sh).astype(np.float64)
     traj = diff.refine_roll(l, mask, 0.0, 50)
     assert abs(traj[-1][0] - _plane_fit_psi(l, mask)) < 1e-10
+
+
+def test_linear_warp_closed_forms():
+    rng = np.random.default_rng(31)
+    tgt = rng.uniform(0, 255, (6, 20))
+    sh = np.array([0, 3, -2, 7, 25, -30], np.float32)          # integers: the rounded warp exactly
+    w = diff.warp_linear(torch.tensor(tgt), torch.tensor(sh.astype(np.float64))).numpy()
+    assert np.array_equal(w, diff.warp(torch.tensor(tgt), sh).numpy())
+    ramp = np.tile(np.arange(20, dtype=np.float64) * 3.0 + 1.0, (3, 1))    # 3x + 1
+    sh = np.array([0.25, 2.5, -1.75], np.float32)
+    w = diff.warp_linear(torch.tensor(ramp), torch.tensor(sh.astype(np.float64))).numpy()
+    u = np.arange(20)[None, :] - sh.astype(np.float64)[:, None]
+    inside = (u >= 0) & (u <= 19)
+    assert np.allclose(w[inside], (3.0 * u + 1.0)[inside], atol=1e-12, rtol=0)
+    assert np.all(w[u < 0] == 1.0) and np.all(w[u > 19] == 58.0)   # clamped to the edge pixels
+
+
+def test_linear_warp_shift_gradient_matches_central_differences(crop):
+    _, ref, tgt, sh = crop
+    D = 16
+    shf = (sh + np.linspace(-0.4, 0.35, sh.size)).astype(np.float32)   # fractional shifts
+    gl = np.random.default_rng(32).normal(size=ref.shape)
+    l, g_r, g_t, g_s = diff.disparity_linear_vjp(ref, tgt, shf, D, WIN, BIL, S0, S1, T, gl)
+    scale = 1e-3 * np.abs(g_s).max()
+    for v in (0, 7, 23, 47):
+        h = 1e-4
+
+        def S(x):
+            s2 = shf.astype(np.float64).copy()
+            s2[v] = x
+            with torch.no_grad():
+                lx = diff.disparity(torch.tensor(ref.astype(np.float64)), torch.tensor(tgt.astype(np.float64)),
+                                    torch.tensor(s2), D, WIN, BIL, S0, S1, T, 1).numpy()
+            return float((lx * gl).sum())
+
+        fd = (S(float(shf[v]) + h) - S(float(shf[v]) - h)) / (2 * h)
+        assert abs(g_s[v] - fd) <= 1e-5 * max(abs(fd), scale), (v, g_s[v], fd)
+    # the target adjoint of the interpolating warp, at an interior and an edge pixel
+    for (v, u) in ((20, 30), (5, 0), (40, 63)):
+        h = 1e-6 * max(abs(float(tgt[v, u])), 1.0)
+
+        def St(x):
+            t2 = tgt.astype(np.float64).copy()
+            t2[v, u] = x
+            return float((diff.disparity_linear_value(ref, t2, shf, D, WIN, BIL, S0, S1, T) * gl).sum())
+
+        fd = (St(tgt[v, u] + h) - St(tgt[v, u] - h)) / (2 * h)
+        assert abs(g_t[v, u] - fd) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(g_t).max())
