@@ -10,7 +10,8 @@
  *            population statistics; c = 1 where sigma_ref * sigma_tgt = 0
  *   E(p,d) = sum_q w(p,q) c(q,d) / sum_q w(p,q)        (eq. omega_s, eq. fbs; out-of-image q
  *            left out; sigma0, sigma1 used as printed, without a factor 2)
- *   l(p)   = sum_d d softmax_d(-E(p,d) / T) + s_i(v)   (s_i = floor(s(v) + 0.5), §3.1)
+ *   l(p)   = sum_d d softmax_d(-E(p,d) / T) + s_i(v)   (s_i = floor(s(v) + 0.5), §3.1; with
+ *            STEREO_WARP_LINEAR the fractional s(v) itself, the target read by interpolation)
  *   L      = sum_p m(p) (l(p) - alpha0 - alpha1 y_p(psi))^2,  y_p = v cos(psi) - u sin(psi)
  *            (eq. E2, eq. y; raw pixel coordinates, u the column, v the row)
  *
@@ -38,6 +39,12 @@
 extern "C" {
 #endif
 
+/* How the target row is shifted by s(v) (§3.1). */
+#define STEREO_WARP_ROUND 0   /* s_i = floor(s + 0.5), the pixel copied; s_i is added back */
+#define STEREO_WARP_LINEAR 1  /* the point u - s(v) read by linear interpolation between the two
+                                 neighbouring columns (each clamped to the edge); s(v) itself,
+                                 unrounded, is added back -- l is then differentiable in s(v) */
+
 typedef struct {
     int32_t width, height;   /* 1 <= W, H <= 8192 */
     int32_t batch;           /* pairs per call, 1..64 */
@@ -46,10 +53,11 @@ typedef struct {
     int32_t bil;             /* bilateral window k, odd, 1..15 */
     float sigma0, sigma1;    /* eq. (omega_s) */
     float temperature;       /* T > 0 of the soft-argmin */
+    int32_t warp_mode;       /* STEREO_WARP_ROUND (default) or STEREO_WARP_LINEAR */
 } stereo_diff_params;
 
 /* Defaults: win = 9, bil = 11, sigma0 = 1.5, sigma1 = 5.5 (§4.4.1), temperature = 0.1,
- * batch = 1; sizes and max_disp left 0 for the caller to set. */
+ * batch = 1, warp_mode = STEREO_WARP_ROUND; sizes and max_disp left 0 for the caller to set. */
 int stereo_diff_params_default(stereo_diff_params *p);
 
 /* Bytes of device workspace the soft-argmin forward and backward need for *p (the
@@ -69,16 +77,19 @@ int stereo_softargmin_fwd(const stereo_diff_params *p, const float *ref_dev, con
                           size_t workspace_bytes, stereo_stream_t stream);
 
 /* Backward (vector-Jacobian product): given grad_disp_dev = dS/dl for a scalar S, write
- * grad_ref_dev = dS/dref and grad_tgt_dev = dS/dtgt (float32 [batch][height][width],
- * overwritten, not accumulated).  ref_dev, tgt_dev, shift_dev and the workspace must be
- * those of the matching forward call.  grad_ref_dev or grad_tgt_dev may be NULL to skip
- * that output.  The cost adjoint of eq. (c) is taken with the statistics of each window
- * pair; a pair with sigma_ref * sigma_tgt = 0 (c fixed at 1) passes no gradient.
+ * grad_ref_dev = dS/dref and grad_tgt_dev = dS/dtgt (float32 [batch][height][width]) and
+ * grad_shift_dev = dS/ds(v) (float32 [batch][height]), overwritten, not accumulated.
+ * ref_dev, tgt_dev, shift_dev and the workspace must be those of the matching forward call.
+ * Any of the three outputs may be NULL to skip it.  The cost adjoint of eq. (c) is taken
+ * with the statistics of each window pair; a pair with sigma_ref * sigma_tgt = 0 (c fixed at
+ * 1) passes no gradient.  With STEREO_WARP_ROUND the shift enters only through its rounding,
+ * so dS/ds = 0; with STEREO_WARP_LINEAR it is the derivative of the interpolation (taken
+ * inside the interval between two columns) plus that of the add-back.
  * Errors: as the forward. */
 int stereo_softargmin_bwd(const stereo_diff_params *p, const float *ref_dev, const float *tgt_dev,
                           const float *shift_dev, const float *grad_disp_dev, float *grad_ref_dev,
-                          float *grad_tgt_dev, void *workspace_dev, size_t workspace_bytes,
-                          stereo_stream_t stream);
+                          float *grad_tgt_dev, float *grad_shift_dev, void *workspace_dev,
+                          size_t workspace_bytes, stereo_stream_t stream);
 
 /* Bytes of device workspace the energy calls below need for `batch` pairs (partial sums
  * of 64 blocks per pair and the refinement state).  Host only. */

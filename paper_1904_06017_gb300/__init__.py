@@ -123,7 +123,7 @@ def load_library():
         "stereo_diff_params_default": [P],
         "stereo_softargmin_workspace_bytes": [P, P],
         "stereo_softargmin_fwd": [P, P, P, P, P, P, ctypes.c_size_t, P],
-        "stereo_softargmin_bwd": [P, P, P, P, P, P, P, P, ctypes.c_size_t, P],
+        "stereo_softargmin_bwd": [P, P, P, P, P, P, P, P, P, ctypes.c_size_t, P],
         "stereo_dt_energy_workspace_bytes": [I32, P],
         "stereo_dt_energy_fwd": [I32, I32, I32, P, P, P, P, P, ctypes.c_size_t, P],
         "stereo_dt_energy_bwd": [I32, I32, I32, P, P, P, P, P, P, P, ctypes.c_size_t, P],

@@ -57,7 +57,7 @@ __device__ __forceinline__ int row_shift(float s, int W)
 
 // ------------------------------------------------------------------ layout of the workspace
 struct Dims {
-    int W, H, B, D, rw, rb, n;
+    int W, H, B, D, rw, rb, n, warp_mode;
     int We;            // W + D - 1: target statistics columns (u - d + D - 1)
     int Wr, Hr;        // W + 2rw, H + 2rw: extended reference grid of the cost adjoint
     int Wt;            // W + 2rw + D - 1: extended target columns
@@ -115,6 +115,8 @@ int check_params(const stereo_diff_params *p, Dims *d, const char *who)
         return set_error(STEREO_EINVAL, "%s: sigma0, sigma1 must be positive and finite", who);
     if (!(p->temperature > 0.f) || !isfinite(p->temperature))
         return set_error(STEREO_EINVAL, "%s: temperature must be positive and finite", who);
+    if (p->warp_mode != STEREO_WARP_ROUND && p->warp_mode != STEREO_WARP_LINEAR)
+        return set_error(STEREO_EINVAL, "%s: warp_mode %d unknown", who, p->warp_mode);
     d->W = p->width;
     d->H = p->height;
     d->B = p->batch;
@@ -122,6 +124,7 @@ int check_params(const stereo_diff_params *p, Dims *d, const char *who)
     d->rw = p->win / 2;
     d->rb = p->bil / 2;
     d->n = p->win * p->win;
+    d->warp_mode = p->warp_mode;
     d->We = d->W + d->D - 1;
     d->Wr = d->W + 2 * d->rw;
     d->Hr = d->H + 2 * d->rw;
@@ -141,14 +144,37 @@ int check_ws(const Dims &d, void *ws, size_t bytes, Ws *w, const char *who)
 }
 
 // ------------------------------------------------------------------ forward kernels
+// The linear-interpolation warp reads u - s = u + k + f with k = floor(-s) and f in [0, 1):
+// both neighbours are the columns u + k and u + k + 1 of every pixel of the row.  k is
+// limited to +-2W, where both neighbours clamp to the same edge pixel whatever f is.
+struct LinShift {
+    int k;
+    float f;
+};
+
+__device__ __forceinline__ LinShift lin_shift(float s, int W)
+{
+    const float ns = -s, fl = floorf(ns), lim = 2.0f * (float)W;
+    LinShift r;
+    r.k = (int)fminf(fmaxf(fl, -lim), lim);
+    r.f = ns - fl;
+    return r;
+}
+
 __global__ void __launch_bounds__(256) k_dwarp(const float *__restrict__ tgt, const float *__restrict__ shift,
-                                               float *__restrict__ tw, int W, int H)
+                                               float *__restrict__ tw, int W, int H, int mode)
 {
     const int u = blockIdx.x * blockDim.x + threadIdx.x, v = blockIdx.y, b = blockIdx.z;
     if (u >= W) return;
-    const int si = row_shift(shift[(size_t)b * H + v], W);
     const size_t row = ((size_t)b * H + v) * W;
-    tw[row + u] = tgt[row + clampi(u - si, 0, W - 1)];
+    const float s = shift[(size_t)b * H + v];
+    if (mode == STEREO_WARP_LINEAR) {
+        const LinShift ls = lin_shift(s, W);
+        const float A = tgt[row + clampi(u + ls.k, 0, W - 1)], B = tgt[row + clampi(u + ls.k + 1, 0, W - 1)];
+        tw[row + u] = fmaf(ls.f, B - A, A);
+        return;
+    }
+    tw[row + u] = tgt[row + clampi(u - row_shift(s, W), 0, W - 1)];
 }
 
 // Window mean and population standard deviation over (2rw+1)^2 clamp-to-edge reads, on an
@@ -261,6 +287,7 @@ struct AggArgs {
     const float *cost;     // GC: c(x, d) of the centre pixel
     float *gw;             // GC out: image gradient through the weights
     int W, H, D;
+    int warp_mode;         // FWD: the add-back is s_i (rounded) or s(v) (linear warp)
     float kappa;           // sqrt(log2 e) / sigma1: scaled intensities
     float k0;              // -log2 e / sigma0^2
     float kT;              // log2 e / T
@@ -451,7 +478,8 @@ __global__ void __launch_bounds__(256) k_dagg(const AggArgs a)
             const float lbar = st2[i] / st1[i];
             a.lbar[o] = lbar;
             a.lse[o] = st0[i] + log2f(st1[i]);
-            a.disp[o] = lbar + row_shift_value(a.shift[(size_t)b * H + py[i]]);
+            const float sv = a.shift[(size_t)b * H + py[i]];
+            a.disp[o] = lbar + (a.warp_mode == STEREO_WARP_LINEAR ? sv : row_shift_value(sv));
         }
         return;
     }
@@ -662,12 +690,55 @@ __global__ void __launch_bounds__(256) k_dtgt_diag(const float *__restrict__ gam
     gtwx[((size_t)b * Hr + row) * Wt + c] = s;
 }
 
+// The folded gradient of the warped target at column xw of row y: every extended target
+// position Xt that reads column xw after clamping (the whole left or right overhang at the
+// edges), over the rows that clamp to y.
+__device__ __forceinline__ float fold_tw(const float *__restrict__ gtwx, int b, int xw, int ylo, int yhi, int W,
+                                         int D, int rw, int Hr, int Wt)
+{
+    const int tlo = xw == 0 ? -rw - (D - 1) : xw, thi = xw == W - 1 ? W - 1 + rw : xw;
+    float s = 0.f;
+    for (int Y = ylo; Y <= yhi; ++Y) {
+        const float *row = gtwx + ((size_t)b * Hr + Y + rw) * Wt + rw + (D - 1);
+        for (int Xt = tlo; Xt <= thi; ++Xt) s += row[Xt];
+    }
+    return s;
+}
+
+// The sum, over the warped columns xw that read source column x through clamp(xw - si),
+// of the folded warped-target gradient: the adjoint of one integer-shift gather.
+__device__ __forceinline__ float unwarp_sum(const float *__restrict__ gtwx, int b, int x, int si, int ylo, int yhi,
+                                            int W, int D, int rw, int Hr, int Wt)
+{
+    int lo, hi;
+    if (W == 1) {
+        lo = 0;
+        hi = 0;
+    } else if (x == 0) {
+        lo = 0;
+        hi = min(W - 1, si);
+    } else if (x == W - 1) {
+        lo = max(0, W - 1 + si);
+        hi = W - 1;
+    } else {
+        lo = hi = x + si;
+        if (lo < 0 || lo > W - 1) {
+            lo = 1;
+            hi = 0;
+        }
+    }
+    float s = 0.f;
+    for (int xw = lo; xw <= hi; ++xw) s += fold_tw(gtwx, b, xw, ylo, yhi, W, D, rw, Hr, Wt);
+    return s;
+}
+
 // Fold the extended grids back onto the image (every clamp-to-edge position adds to the
-// edge pixel it read) and undo the warp (every warped column adds to the column it read).
+// edge pixel it read) and undo the warp (every warped column adds to the column it read;
+// the linear warp reads two columns, with weights 1 - f and f).
 __global__ void __launch_bounds__(256) k_dfold(const float *__restrict__ grefx, const float *__restrict__ gw,
                                                const float *__restrict__ gtwx, const float *__restrict__ shift,
                                                float *__restrict__ gref, float *__restrict__ gtgt, int W, int H,
-                                               int D, int rw, int Wr, int Hr, int Wt)
+                                               int D, int rw, int Wr, int Hr, int Wt, int mode)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, b = blockIdx.z;
     if (x >= W) return;
@@ -681,33 +752,49 @@ __global__ void __launch_bounds__(256) k_dfold(const float *__restrict__ grefx, 
         gref[pix] = s + gw[pix];
     }
     if (gtgt) {
-        const int si = row_shift(shift[(size_t)b * H + y], W);
-        int lo, hi;                              // warped columns reading source column x
-        if (W == 1) {
-            lo = 0;
-            hi = 0;
-        } else if (x == 0) {
-            lo = 0;
-            hi = min(W - 1, si);
-        } else if (x == W - 1) {
-            lo = max(0, W - 1 + si);
-            hi = W - 1;
+        const float sv = shift[(size_t)b * H + y];
+        if (mode == STEREO_WARP_LINEAR) {
+            // tw(xw) = (1 - f) tgt(clamp(xw + k)) + f tgt(clamp(xw + k + 1))
+            const LinShift ls = lin_shift(sv, W);
+            const float ga = unwarp_sum(gtwx, b, x, -ls.k, ylo, yhi, W, D, rw, Hr, Wt);
+            const float gb = unwarp_sum(gtwx, b, x, -ls.k - 1, ylo, yhi, W, D, rw, Hr, Wt);
+            gtgt[pix] = fmaf(ls.f, gb - ga, ga);
         } else {
-            lo = hi = x + si;
-            if (lo < 0 || lo > W - 1) {
-                lo = 1;
-                hi = 0;
-            }
+            gtgt[pix] = unwarp_sum(gtwx, b, x, row_shift(sv, W), ylo, yhi, W, D, rw, Hr, Wt);
         }
-        float s = 0.f;
-        for (int xw = lo; xw <= hi; ++xw) {
-            const int tlo = xw == 0 ? -rw - (D - 1) : xw, thi = xw == W - 1 ? W - 1 + rw : xw;
-            for (int Y = ylo; Y <= yhi; ++Y) {
-                const float *row = gtwx + ((size_t)b * Hr + Y + rw) * Wt + rw + (D - 1);
-                for (int Xt = tlo; Xt <= thi; ++Xt) s += row[Xt];
-            }
+    }
+}
+
+// dS/ds(v) of the linear warp, one block per row: sum over u of the folded warped-target
+// gradient times d tw(u)/ds = tgt(clamp(u + k)) - tgt(clamp(u + k + 1)), plus the add-back
+// term sum_u dS/dl(u).  (The rounded warp has dS/ds = 0.)
+__global__ void __launch_bounds__(256) k_dshift_grad(const float *__restrict__ gtwx, const float *__restrict__ tgt,
+                                                     const float *__restrict__ shift,
+                                                     const float *__restrict__ gdisp, float *__restrict__ gshift,
+                                                     int W, int H, int D, int rw, int Hr, int Wt, int mode)
+{
+    __shared__ float red[8];
+    const int y = blockIdx.x, b = blockIdx.y;
+    float acc = 0.f;
+    if (mode == STEREO_WARP_LINEAR) {
+        const LinShift ls = lin_shift(shift[(size_t)b * H + y], W);
+        const int ylo = y == 0 ? -rw : y, yhi = y == H - 1 ? H - 1 + rw : y;
+        const float *trow = tgt + ((size_t)b * H + y) * W;
+        const float *grow = gdisp + ((size_t)b * H + y) * W;
+        for (int u = threadIdx.x; u < W; u += blockDim.x) {
+            const float A = trow[clampi(u + ls.k, 0, W - 1)], B = trow[clampi(u + ls.k + 1, 0, W - 1)];
+            acc = fmaf(fold_tw(gtwx, b, u, ylo, yhi, W, D, rw, Hr, Wt), A - B, acc);
+            acc += grow[u];
         }
-        gtgt[pix] = s;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        gshift[(size_t)b * H + y] = t;
     }
 }
 
@@ -775,6 +862,7 @@ AggArgs agg_args(const stereo_diff_params *p, const Dims &d, const Ws &w, const 
     a.W = d.W;
     a.H = d.H;
     a.D = d.D;
+    a.warp_mode = d.warp_mode;
     a.kappa = sqrtf(kLog2e) / p->sigma1;
     a.k0 = -kLog2e / (p->sigma0 * p->sigma0);
     a.kT = kLog2e / p->temperature;
@@ -826,7 +914,7 @@ extern "C" int stereo_softargmin_fwd(const stereo_diff_params *p, const float *r
     if ((rc = check_ws(d, ws, ws_bytes, &w, who))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const int B = d.B;
-    k_dwarp<<<dim3((d.W + 255) / 256, d.H, B), 256, 0, st>>>(tgt, shift, w.tw, d.W, d.H);
+    k_dwarp<<<dim3((d.W + 255) / 256, d.H, B), 256, 0, st>>>(tgt, shift, w.tw, d.W, d.H, d.warp_mode);
     const size_t ssm = (size_t)(32 + 2 * d.rw) * (8 + 2 * d.rw) * sizeof(float);
     k_dstats<<<dim3((d.W + 31) / 32, (d.H + 7) / 8, B), 256, ssm, st>>>(ref, d.W, d.H, d.W, 0, d.rw, w.mur,
                                                                         w.sdr);
@@ -848,7 +936,7 @@ extern "C" int stereo_softargmin_fwd(const stereo_diff_params *p, const float *r
 
 extern "C" int stereo_softargmin_bwd(const stereo_diff_params *p, const float *ref, const float *tgt,
                                      const float *shift, const float *gdisp, float *gref, float *gtgt,
-                                     void *ws, size_t ws_bytes, stereo_stream_t stream)
+                                     float *gshift, void *ws, size_t ws_bytes, stereo_stream_t stream)
 {
     static const char *who = "stereo_softargmin_bwd";
     Dims d;
@@ -857,7 +945,7 @@ extern "C" int stereo_softargmin_bwd(const stereo_diff_params *p, const float *r
     if (rc) return rc;
     if (!ref || !tgt || !shift || !gdisp) return set_error(STEREO_EINVAL, "%s: null pointer", who);
     if ((rc = check_ws(d, ws, ws_bytes, &w, who))) return rc;
-    if (!gref && !gtgt) return STEREO_OK;
+    if (!gref && !gtgt && !gshift) return STEREO_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const int B = d.B;
     AggArgs a = agg_args(p, d, w, ref);
@@ -883,7 +971,8 @@ extern "C" int stereo_softargmin_bwd(const stereo_diff_params *p, const float *r
     c.sdt = w.sdt;
     c.cost = w.cost;
     c.gc = w.gc;
-    c.gamma = gtgt ? w.gamma : nullptr;
+    const bool need_tw = gtgt || gshift;    // the warped-target gradient feeds both
+    c.gamma = need_tw ? w.gamma : nullptr;
     c.grefx = w.grefx;
     c.W = d.W;
     c.H = d.H;
@@ -893,10 +982,14 @@ extern "C" int stereo_softargmin_bwd(const stereo_diff_params *p, const float *r
     c.We = d.We;
     c.inv_n = 1.0f / (float)d.n;
     if ((e = launch_cb(c, d.rw, B, st)) != cudaSuccess) return cuda_error(e, who);
-    if (gtgt)
+    if (need_tw)
         k_dtgt_diag<<<dim3((d.Wt + 255) / 256, d.Hr, B), 256, 0, st>>>(w.gamma, w.gtwx, d.D, d.rw, d.Wr,
                                                                        d.Hr, d.Wt);
-    k_dfold<<<dim3((d.W + 255) / 256, d.H, B), 256, 0, st>>>(w.grefx, w.gw, w.gtwx, shift, gref, gtgt, d.W,
-                                                             d.H, d.D, d.rw, d.Wr, d.Hr, d.Wt);
+    if (gref || gtgt)
+        k_dfold<<<dim3((d.W + 255) / 256, d.H, B), 256, 0, st>>>(w.grefx, w.gw, w.gtwx, shift, gref, gtgt, d.W,
+                                                                 d.H, d.D, d.rw, d.Wr, d.Hr, d.Wt, d.warp_mode);
+    if (gshift)
+        k_dshift_grad<<<dim3(d.H, B), 256, 0, st>>>(w.gtwx, tgt, shift, gdisp, gshift, d.W, d.H, d.D, d.rw, d.Hr,
+                                                   d.Wt, d.warp_mode);
     return cuda_error(cudaGetLastError(), who);
 }

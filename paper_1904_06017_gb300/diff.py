@@ -10,6 +10,10 @@ angle and the line coefficients:
     L = DTEnergy.apply(l, theta, mask)                                       # [B]; theta [B, 3]
     L.sum().backward()            # gradients into ref, tgt (float32) and theta (float64)
 
+With warp_mode = STEREO_WARP_LINEAR the row shifts are read by interpolation and the shift
+tensor receives a gradient as well, so warp coefficients from which torch computes s(v)
+(eq. relation_vd: s(v) = c0 + c1 v - delta_p) are refined by the same backward pass.
+
 Both Functions marshal tensors into the C calls; the forward and backward arithmetic is
 the library's CUDA kernels, and there is no CPU path.  ``refine_roll`` runs the library's
 gradient refinement of the roll angle.
@@ -22,8 +26,8 @@ import torch
 
 from . import STEREO_EINVAL, StereoError, _check, _ptr, _stream, load_library
 
-__all__ = ["stereo_diff_params", "stereo_diff_params_default", "stereo_softargmin_workspace_bytes",
-           "stereo_softargmin_fwd", "stereo_softargmin_bwd", "stereo_dt_energy_workspace_bytes",
+__all__ = ["STEREO_WARP_ROUND", "STEREO_WARP_LINEAR", "stereo_diff_params", "stereo_diff_params_default",
+           "stereo_softargmin_workspace_bytes", "stereo_softargmin_fwd", "stereo_softargmin_bwd", "stereo_dt_energy_workspace_bytes",
            "stereo_dt_energy_fwd", "stereo_dt_energy_bwd", "stereo_dt_refine_roll", "SoftArgmin",
            "DTEnergy", "soft_argmin_disparity", "dt_energy", "refine_roll"]
 
@@ -31,7 +35,11 @@ __all__ = ["stereo_diff_params", "stereo_diff_params_default", "stereo_softargmi
 class stereo_diff_params(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("max_disp", ctypes.c_int32), ("win", ctypes.c_int32), ("bil", ctypes.c_int32),
-                ("sigma0", ctypes.c_float), ("sigma1", ctypes.c_float), ("temperature", ctypes.c_float)]
+                ("sigma0", ctypes.c_float), ("sigma1", ctypes.c_float), ("temperature", ctypes.c_float),
+                ("warp_mode", ctypes.c_int32)]
+
+
+STEREO_WARP_ROUND, STEREO_WARP_LINEAR = 0, 1
 
 
 def stereo_diff_params_default(**overrides) -> stereo_diff_params:
@@ -58,10 +66,12 @@ def stereo_softargmin_fwd(params, ref, tgt, shift, disp, workspace, stream=None)
                                                 _stream(stream)))
 
 
-def stereo_softargmin_bwd(params, ref, tgt, shift, grad_disp, grad_ref, grad_tgt, workspace, stream=None):
+def stereo_softargmin_bwd(params, ref, tgt, shift, grad_disp, grad_ref, grad_tgt, workspace, stream=None,
+                          grad_shift=None):
     _check(load_library().stereo_softargmin_bwd(ctypes.byref(params), _ptr(ref), _ptr(tgt), _ptr(shift),
                                                 _ptr(grad_disp), _ptr(grad_ref), _ptr(grad_tgt),
-                                                _ptr(workspace), _nbytes(workspace), _stream(stream)))
+                                                _ptr(grad_shift), _ptr(workspace), _nbytes(workspace),
+                                                _stream(stream)))
 
 
 def stereo_dt_energy_workspace_bytes(batch: int) -> int:
@@ -110,15 +120,17 @@ def _f32(x):
 
 class SoftArgmin(torch.autograd.Function):
     """l = sum_d d softmax_d(-E(p,d)/T) + s_i(v) over float32 images [B, H, W] with row-shift
-    tables [B, H]; differentiable in ref and tgt."""
+    tables [B, H]; differentiable in ref and tgt, and with warp_mode = STEREO_WARP_LINEAR
+    (fractional shifts read by interpolation, s(v) added back unrounded) in the shifts too."""
 
     @staticmethod
-    def forward(ctx, ref, tgt, shift, max_disp, win=9, bil=11, sigma0=1.5, sigma1=5.5, temperature=0.1):
+    def forward(ctx, ref, tgt, shift, max_disp, win=9, bil=11, sigma0=1.5, sigma1=5.5, temperature=0.1,
+                warp_mode=STEREO_WARP_ROUND):
         r, t, s = _f32(ref), _f32(tgt), _f32(shift)
         B, H, W = r.shape
         p = stereo_diff_params_default(width=W, height=H, batch=B, max_disp=int(max_disp), win=int(win),
                                        bil=int(bil), sigma0=float(sigma0), sigma1=float(sigma1),
-                                       temperature=float(temperature))
+                                       temperature=float(temperature), warp_mode=int(warp_mode))
         ws = torch.empty(stereo_softargmin_workspace_bytes(p), dtype=torch.uint8, device=r.device)
         disp = torch.empty((B, H, W), dtype=torch.float32, device=r.device)
         stereo_softargmin_fwd(p, r, t, s, disp, ws)
@@ -129,12 +141,14 @@ class SoftArgmin(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_disp):
         r, t, s, ws = ctx.saved_tensors
-        need_r, need_t = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        need_r, need_t, need_s = ctx.needs_input_grad[0], ctx.needs_input_grad[1], ctx.needs_input_grad[2]
         gr = torch.empty_like(r) if need_r else None
         gt = torch.empty_like(t) if need_t else None
-        if need_r or need_t:
-            stereo_softargmin_bwd(ctx.params, r, t, s, grad_disp.to(torch.float32).contiguous(), gr, gt, ws)
-        return gr, gt, None, None, None, None, None, None, None
+        gs = torch.empty_like(s) if need_s else None
+        if need_r or need_t or need_s:
+            stereo_softargmin_bwd(ctx.params, r, t, s, grad_disp.to(torch.float32).contiguous(), gr, gt, ws,
+                                  grad_shift=gs)
+        return gr, gt, gs, None, None, None, None, None, None, None
 
 
 class DTEnergy(torch.autograd.Function):
@@ -164,11 +178,11 @@ class DTEnergy(torch.autograd.Function):
 
 
 def soft_argmin_disparity(ref, tgt, shift, max_disp, win=9, bil=11, sigma0=1.5, sigma1=5.5,
-                          temperature=0.1):
+                          temperature=0.1, warp_mode=STEREO_WARP_ROUND):
     """SoftArgmin on [H, W] or [B, H, W] images (the output has the input's batch form)."""
     unbatched = ref.dim() == 2
     out = SoftArgmin.apply(_batched(ref, 3), _batched(tgt, 3), _batched(shift, 2), max_disp, win, bil,
-                           sigma0, sigma1, temperature)
+                           sigma0, sigma1, temperature, warp_mode)
     return out[0] if unbatched else out
 
 

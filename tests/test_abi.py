@@ -122,8 +122,8 @@ def test_diff_struct_layout_matches_header(tmp_path):
 #include <stdio.h>
 #include "stereo_diff.h"
 int main(void) {
-  printf("%zu %zu %zu\n", sizeof(stereo_diff_params), offsetof(stereo_diff_params, sigma0),
-         offsetof(stereo_diff_params, temperature));
+  printf("%zu %zu %zu %zu\n", sizeof(stereo_diff_params), offsetof(stereo_diff_params, sigma0),
+         offsetof(stereo_diff_params, temperature), offsetof(stereo_diff_params, warp_mode));
   return 0;
 }''')
     exe = tmp_path / "layout_diff"
@@ -131,7 +131,7 @@ int main(void) {
     vals = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
                                            check=True).stdout.split()]
     assert vals == [ctypes.sizeof(sgd.stereo_diff_params), sgd.stereo_diff_params.sigma0.offset,
-                    sgd.stereo_diff_params.temperature.offset]
+                    sgd.stereo_diff_params.temperature.offset, sgd.stereo_diff_params.warp_mode.offset]
 
 
 def test_diff_defaults_and_workspace_size(lib):
@@ -175,8 +175,11 @@ def test_diff_rejects_null_and_small_workspaces(lib):
     assert "aligned" in sg.stereo_last_error()
     assert lib.stereo_softargmin_fwd(ctypes.byref(p), fake, fake, fake, fake, fake, 256, None) == sg.STEREO_EINVAL
     assert "needed" in sg.stereo_last_error()
-    assert lib.stereo_softargmin_bwd(ctypes.byref(p), fake, fake, fake, None, fake, fake, fake, 1 << 40,
+    assert lib.stereo_softargmin_bwd(ctypes.byref(p), fake, fake, fake, None, fake, fake, None, fake, 1 << 40,
                                      None) == sg.STEREO_EINVAL
+    p.warp_mode = 2
+    assert lib.stereo_softargmin_fwd(ctypes.byref(p), fake, fake, fake, fake, fake, 1 << 40, None) == sg.STEREO_EINVAL
+    assert "warp_mode" in sg.stereo_last_error()
     assert lib.stereo_dt_energy_fwd(64, 48, 1, fake, None, fake, fake, fake, 16, None) == sg.STEREO_EINVAL
     assert lib.stereo_dt_energy_bwd(0, 48, 1, fake, None, fake, fake, fake, fake, fake, 1 << 20,
                                     None) == sg.STEREO_EINVAL

@@ -43,14 +43,14 @@ def dev(x, dtype=torch.float32):
     return torch.tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
 
 
-def gpu_forward(refs, tgts, shifts, D, win=WIN, bil=BIL, s0=S0, s1=S1, temp=T):
+def gpu_forward(refs, tgts, shifts, D, win=WIN, bil=BIL, s0=S0, s1=S1, temp=T, mode=0):
     """Batched forward through the C calls; returns (l [B,H,W] numpy, params, tensors, ws)."""
     r = dev(np.stack(refs))
     t = dev(np.stack(tgts))
     s = dev(np.stack(shifts))
     B, H, W = r.shape
     p = sgd.stereo_diff_params_default(width=W, height=H, batch=B, max_disp=D, win=win, bil=bil,
-                                       sigma0=s0, sigma1=s1, temperature=temp)
+                                       sigma0=s0, sigma1=s1, temperature=temp, warp_mode=mode)
     ws = torch.empty(sgd.stereo_softargmin_workspace_bytes(p), dtype=torch.uint8, device="cuda")
     l = torch.empty((B, H, W), dtype=torch.float32, device="cuda")
     sgd.stereo_softargmin_fwd(p, r, t, s, l, ws)
@@ -58,13 +58,15 @@ def gpu_forward(refs, tgts, shifts, D, win=WIN, bil=BIL, s0=S0, s1=S1, temp=T):
     return l.cpu().numpy().astype(np.float64), p, (r, t, s), ws
 
 
-def gpu_backward(p, rts, ws, gl):
+def gpu_backward(p, rts, ws, gl, want_shift=False):
     r, t, s = rts
     gr = torch.empty_like(r)
     gt = torch.empty_like(t)
-    sgd.stereo_softargmin_bwd(p, r, t, s, dev(gl), gr, gt, ws)
+    gs = torch.full_like(s, 7.0) if want_shift else None
+    sgd.stereo_softargmin_bwd(p, r, t, s, dev(gl), gr, gt, ws, grad_shift=gs)
     torch.cuda.synchronize()
-    return gr.cpu().numpy().astype(np.float64), gt.cpu().numpy().astype(np.float64)
+    out = (gr.cpu().numpy().astype(np.float64), gt.cpu().numpy().astype(np.float64))
+    return out + (gs.cpu().numpy().astype(np.float64),) if want_shift else out
 
 
 def check_grad(g, go, name, floor=0.0):
@@ -309,3 +311,67 @@ def test_full_workload_batch_sampled_against_the_oracle():
                 b, x, y, gr[b, y, x], g_ref, gt[b, y, xs], g_tw))
             assert abs(gr[b, y, x] - g_ref) <= G_TOL * np.abs(gr[b]).max()
             assert abs(gt[b, y, xs] - g_tw) <= G_TOL * np.abs(gt[b]).max()
+
+
+def test_linear_warp_matches_the_oracle(scene):
+    """Fractional row shifts read by interpolation: l, both image gradients and dS/ds(v)."""
+    ref, tgt, sh = synth.crop_pair(scene, 448, 300, 64, 48)
+    D = 16
+    H, W = ref.shape
+    shf = (sh + np.linspace(-0.45, 0.4, H)).astype(np.float32)
+    l, p, rts, ws = gpu_forward([ref.astype(np.float64)], [tgt.astype(np.float64)], [shf], D,
+                                mode=sgd.STEREO_WARP_LINEAR)
+    gl = np.random.default_rng(17).normal(size=(H, W))
+    lo, gro, gto, gso = odiff.disparity_linear_vjp(ref, tgt, shf, D, WIN, BIL, S0, S1, T, gl)
+    assert np.abs(l[0] - lo).max() <= L_TOL
+    gr, gt, gs = gpu_backward(p, rts, ws, gl[None].astype(np.float32), want_shift=True)
+    check_grad(gr[0], gro, "dS/dref")
+    check_grad(gt[0], gto, "dS/dtgt")
+    check_grad(gs[0], gso, "dS/ds")
+
+
+def test_rounded_warp_has_no_shift_gradient(scene):
+    ref, tgt, sh = synth.crop_pair(scene, 448, 300, 64, 48)
+    l, p, rts, ws = gpu_forward([ref.astype(np.float64)], [tgt.astype(np.float64)], [sh], 16)
+    _, _, gs = gpu_backward(p, rts, ws, np.ones((1, 48, 64), np.float32), want_shift=True)
+    assert np.all(gs == 0.0)
+
+
+def test_warp_coefficients_refined_through_autograd(scene):
+    """s(v) = c0 + c1 v (eq. relation_vd) computed by torch from two float64 parameters: the
+    backward of SoftArgmin (linear warp) and DTEnergy reaches c0 and c1; checked against the
+    oracle's FP64 chain and against its central differences."""
+    ref, tgt, sh = synth.crop_pair(scene, 448, 300, 64, 48)
+    D = 16
+    H, W = ref.shape
+    v = np.arange(H, dtype=np.float64)
+    c1_0 = float(np.polyfit(v, sh.astype(np.float64), 1)[0])
+    c0_0 = float(sh[0]) + 0.3
+    c = torch.tensor([c0_0, c1_0], dtype=torch.float64, device="cuda", requires_grad=True)
+    vt = torch.arange(H, dtype=torch.float64, device="cuda")
+    s = c[0] + c[1] * vt
+    r = dev(ref)
+    t = dev(tgt)
+    l = sgd.soft_argmin_disparity(r, t, s, D, WIN, BIL, S0, S1, T, warp_mode=sgd.STEREO_WARP_LINEAR)
+    theta = torch.tensor([0.02, 30.0, 0.1], dtype=torch.float64, device="cuda")
+    L = sgd.dt_energy(l, theta)
+    L.backward()
+    g = c.grad.cpu().numpy()
+
+    def loss(c0, c1):
+        sv = (c0 + c1 * v).astype(np.float32)
+        lx = odiff.disparity_linear_value(ref, tgt, sv, D, WIN, BIL, S0, S1, T)
+        return odiff.energy_value(lx, np.ones((H, W)), 0.02, 30.0, 0.1)
+
+    ct = torch.tensor([c0_0, c1_0], dtype=torch.float64, requires_grad=True)
+    so = ct[0] + ct[1] * torch.arange(H, dtype=torch.float64)
+    lo = odiff.disparity(torch.tensor(ref.astype(np.float64)), torch.tensor(tgt.astype(np.float64)), so, D, WIN,
+                         BIL, S0, S1, T, 1)
+    odiff.dt_energy(lo, torch.ones((H, W), dtype=torch.float64), torch.tensor(0.02, dtype=torch.float64),
+                    torch.tensor(30.0, dtype=torch.float64), torch.tensor(0.1, dtype=torch.float64)).backward()
+    go = ct.grad.numpy()
+    print("\ndL/dc0, dL/dc1: GPU %s, oracle %s" % (g, go))
+    assert g == pytest.approx(go, rel=1e-3)
+    h = 1e-3
+    fd0 = (loss(c0_0 + h, c1_0) - loss(c0_0 - h, c1_0)) / (2 * h)
+    assert go[0] == pytest.approx(fd0, rel=1e-3)
