@@ -281,6 +281,43 @@ int stereo_lr_check(stereo_ctx *ctx, const uint8_t *ref_dev, const uint8_t *tgt_
                     const float *shift_dev, const int32_t *wta_ref_dev, int32_t *wta_tgt_dev,
                     uint8_t *lr_ok_dev, float delta_r, stereo_stream_t stream);
 
+/* ---------------------------------------------------------------- self-estimated warp model
+ * The paper obtains the perspective transformation of §3.1 from correspondences it does not
+ * specify; its road disparity is affine in the row, du(v) = c0 + c1 v (eq. relation_vd).
+ * This object estimates c0, c1 from the unwarped pair itself, with a coarse first pass:
+ *   1. both images are averaged over factor x factor blocks (the integer block sum plus
+ *      factor^2/2, divided by factor^2: the mean rounded half up); a remainder of fewer than
+ *      `factor` rows or columns is left out;
+ *   2. the reference view (eq. c, eq. fbs, WTA, eq. subpixel) runs on the coarse pair over the
+ *      full range Dc = ceil(max_disp / factor), with no warp;
+ *   3. FP64 least squares over the coarse pixels the geometric validity keeps:
+ *      factor * l_c(u_c, v_c) = a + b v_c, then c1 = b / factor and c0 = a - c1 (factor - 1) / 2
+ *      (coarse row v_c is centred on full row factor v_c + (factor - 1) / 2).
+ * max_disp: the full-resolution disparity range of the unwarped pair (1 .. 256 * factor).
+ * factor: 1..8, with width / factor >= 1 and height / factor >= 1.  win, bil, sigma0, sigma1:
+ * as in stereo_params, applied at the coarse resolution.  Allocates its coarse buffers and a
+ * coarse context.  Errors: STEREO_EINVAL, STEREO_ENOMEM, STEREO_ECUDA, STEREO_ENOTSUP. */
+typedef struct stereo_warp_est stereo_warp_est;
+
+int stereo_warp_est_create(int32_t width, int32_t height, int32_t pitch, int32_t max_disp, int32_t factor,
+                           int32_t win, int32_t bil, float sigma0, float sigma1, stereo_warp_est **out);
+
+/* Estimate from ref_dev, tgt_dev (uint8 [height][pitch], the unwarped pair).  coef_dev:
+ * double [3] in device memory = (c0, c1, n) with n the number of fitted coarse pixels; c0 and
+ * c1 are NaN when fewer than two distinct coarse rows are fitted.  shift_dev: float [height]
+ * receiving the row shift s(v) = c0 + c1 v - delta_p for stereo_warp_target, or NULL.
+ * Asynchronous on the stream. */
+int stereo_warp_est_run(stereo_warp_est *e, const uint8_t *ref_dev, const uint8_t *tgt_dev, double delta_p,
+                        double *coef_dev, float *shift_dev, stereo_stream_t stream);
+
+/* The coarse disparity map and validity of the last run (device pointers owned by the object,
+ * float / uint8 [height_c][width_c], valid until it is destroyed) and their size. */
+int stereo_warp_est_coarse(const stereo_warp_est *e, const float **disp_dev, const uint8_t **valid_dev,
+                           int32_t *width_c, int32_t *height_c);
+
+/* Free the object (synchronises the device).  NULL is a no-op. */
+int stereo_warp_est_destroy(stereo_warp_est *e);
+
 /* ---------------------------------------------------------------- diagnostics */
 
 /* Synchronise the stream, read and clear the context's device status word.

@@ -23,7 +23,8 @@ __all__ = [
     "stereo_cost_volume", "stereo_aggregate_volume", "stereo_wta_volume",
     "stereo_check_device_status", "stereo_profile_enable", "stereo_profile_read",
     "stereo_fp32_peak_probe", "stereo_last_error", "stereo_version", "Stereo",
-    "stereo_disparity_transform_noalloc", "stereo_lr_check", "stereo_pair_desc", "stereo_batch_params",
+    "stereo_disparity_transform_noalloc", "stereo_lr_check", "WarpEstimator", "stereo_pair_desc",
+    "stereo_batch_params",
     "stereo_batch_params_default", "stereo_batch_create", "stereo_batch_run", "stereo_batch_config",
     "stereo_batch_check_device_status", "stereo_batch_destroy", "StereoBatch",
     "STEREO_OK", "STEREO_EINVAL", "STEREO_ENOMEM", "STEREO_ECUDA", "STEREO_ETIMEOUT",
@@ -120,6 +121,10 @@ def load_library():
         "stereo_batch_check_device_status": [P],
         "stereo_batch_destroy": [P],
         "stereo_lr_check": [P, P, P, P, P, P, P, F, P],
+        "stereo_warp_est_create": [I32, I32, I32, I32, I32, I32, I32, F, F, P],
+        "stereo_warp_est_run": [P, P, P, D, P, P, P],
+        "stereo_warp_est_coarse": [P, P, P, P, P],
+        "stereo_warp_est_destroy": [P],
         "stereo_diff_params_default": [P],
         "stereo_softargmin_workspace_bytes": [P, P],
         "stereo_softargmin_fwd": [P, P, P, P, P, P, ctypes.c_size_t, P],
@@ -426,3 +431,63 @@ class StereoBatch:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- self-estimated warp model
+
+class WarpEstimator:
+    """stereo_warp_est_*: the row-shift model du(v) = c0 + c1 v (eq. relation_vd) estimated
+    from a coarse full-range stereo pass over the unwarped pair."""
+
+    def __init__(self, width, height, max_disp, factor=4, win=5, bil=7, sigma0=3.0, sigma1=10.0, pitch=None):
+        pitch = pitch if pitch is not None else (width + 15) // 16 * 16
+        e = ctypes.c_void_p()
+        _check(load_library().stereo_warp_est_create(int(width), int(height), int(pitch), int(max_disp),
+                                                     int(factor), int(win), int(bil), float(sigma0),
+                                                     float(sigma1), ctypes.byref(e)))
+        self.est = e
+        self.height = int(height)
+
+    def run(self, ref, tgt, coef, shift=None, delta_p=0.0, stream=None):
+        """coef: CUDA float64 tensor of 3 (c0, c1, n); shift: CUDA float32 [height] or None."""
+        _check(load_library().stereo_warp_est_run(self.est, _ptr(ref), _ptr(tgt), float(delta_p), _ptr(coef),
+                                                  _ptr(shift), _stream(stream)))
+
+    def coarse(self):
+        """(disp, valid) of the last run: copies of the object's coarse map as CUDA tensors."""
+        import torch
+        d = ctypes.c_void_p()
+        v = ctypes.c_void_p()
+        wc = ctypes.c_int32()
+        hc = ctypes.c_int32()
+        _check(load_library().stereo_warp_est_coarse(self.est, ctypes.byref(d), ctypes.byref(v), ctypes.byref(wc),
+                                                     ctypes.byref(hc)))
+        n = wc.value * hc.value
+        disp = torch.as_tensor(_DeviceBuffer(d.value, 4 * n), device="cuda").view(torch.float32)
+        valid = torch.as_tensor(_DeviceBuffer(v.value, n), device="cuda")
+        return disp.reshape(hc.value, wc.value).clone(), valid.reshape(hc.value, wc.value).clone()
+
+    def close(self):
+        if getattr(self, "est", None) is not None:
+            _check(load_library().stereo_warp_est_destroy(self.est))
+            self.est = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DeviceBuffer:
+    """A raw device allocation seen as a uint8 tensor (the CUDA array interface)."""
+
+    def __init__(self, ptr, nbytes):
+        self.__cuda_array_interface__ = {"shape": (int(nbytes),), "typestr": "|u1", "data": (int(ptr), False),
+                                         "version": 2}
