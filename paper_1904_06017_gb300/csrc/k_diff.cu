@@ -540,30 +540,53 @@ struct CbArgs {
 
 // Extended reference positions X in [-rw, W-1+rw] x [-rw, H-1+rw], a 32 x 8 tile per block.
 // kCbDC disparities at a time: the four window-pair terms A, A mu_a, C, C mu_b of the pairs q
-// in the tile's halo are staged and box-summed (rows, then columns); the d-independent
-// terms of the reference gradient are summed over d per q and box-summed once at the end.
+// in the tile's halo are staged and box-summed with running sums (along rows, then along
+// columns); the d-independent terms of the reference gradient are summed over d per q and
+// box-summed once at the end.  Row strides are padded to odd lengths so that the running
+// sums of neighbouring rows hit distinct shared-memory banks.
 constexpr int kCbDC = 4;
+
+// Running box sums of one plane row: out[x] = sum_{j < WN} in[x + j], x < 32.
+template <int WN>
+__device__ __forceinline__ void row_box(const float *in, float *out)
+{
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < WN; ++j) s += in[j];
+    out[0] = s;
+#pragma unroll 8
+    for (int x = 1; x < 32; ++x) {
+        s += in[x + WN - 1] - in[x - 1];
+        out[x] = s;
+    }
+}
 
 template <int RW>
 __global__ void __launch_bounds__(256) k_dcost_bwd(const CbArgs a)
 {
     constexpr int QW = 32 + 2 * RW, QH = 8 + 2 * RW, NQ = QW * QH, NS = (NQ + 255) / 256;
-    constexpr int WN = 2 * RW + 1, DC = kCbDC;
+    constexpr int WN = 2 * RW + 1, DC = kCbDC, NP = 4 * DC;   // planes: 4 terms x DC disparities
+    constexpr int SW = QW | 1, SP = SW * QH;                    // staged row stride (odd), plane size
+    constexpr int HW_ = 33, HP = HW_ * QH;                      // row-summed row stride (odd), plane size
     extern __shared__ float cb_smem[];
-    float *st = cb_smem;                       // [4][DC][NQ]
-    float *hb = cb_smem + 4 * DC * NQ;         // [4][DC][QH][32]
+    float *st = cb_smem;                       // [NP][QH][SW]
+    float *hb = st + NP * SP;                  // [NP][QH][33]
+    float *vb = hb + NP * HP;                  // [NP][8][32]
     const int b = blockIdx.z;
     const int W = a.W, H = a.H, D = a.D;
     const size_t HW = (size_t)H * W;
     const int X0 = blockIdx.x * 32 - RW, Y0 = blockIdx.y * 8 - RW;   // image coords of the tile origin
     float qmu[NS], qisa[NS], sAmb[NS], sB[NS], sBmu[NS];
     size_t vbase[NS], sbase[NS];       // cost / gc entry of (q, d = 0); statistics entry of (q, 0)
+    int qofs[NS];                      // q's offset inside a staged plane
     bool qin[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         const int j = threadIdx.x + 256 * s;
-        const int qy = Y0 - RW + j / QW, qx = X0 - RW + j % QW;
+        const int r = j / QW, c = j % QW;
+        const int qy = Y0 - RW + r, qx = X0 - RW + c;
         qin[s] = j < NQ && qy >= 0 && qy < H && qx >= 0 && qx < W;
+        qofs[s] = r * SW + c;
         const size_t qo = qin[s] ? (size_t)qy * W + qx : 0;
         vbase[s] = (size_t)b * D * HW + qo;
         sbase[s] = qin[s] ? ((size_t)b * H + qy) * a.We + qx + D - 1 : 0;
@@ -579,70 +602,86 @@ __global__ void __launch_bounds__(256) k_dcost_bwd(const CbArgs a)
     const float rv = a.ref[b * HW + (size_t)yc * W + clampi(X, 0, W - 1)];
     const float *twrow = a.tw + b * HW + (size_t)yc * W;
     float gacc = 0.f;
+    // the loads of a round are issued one round ahead, so that they are in flight while the
+    // previous round's box sums run
+    float g[NS][DC], cc[NS][DC], sb[NS][DC], mb[NS][DC];
+    auto load_round = [&](int d0) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+#pragma unroll
+            for (int k = 0; k < DC; ++k) {
+                const bool ok = qin[s] && d0 + k < D;
+                const size_t vo = vbase[s] + (size_t)(ok ? d0 + k : 0) * HW, so = sbase[s] - (ok ? d0 + k : 0);
+                g[s][k] = ok ? a.gc[vo] : 0.f;
+                cc[s][k] = ok ? a.cost[vo] : 1.f;
+                sb[s][k] = ok ? a.sdt[so] : 0.f;
+                mb[s][k] = ok ? a.mut[so] : 0.f;
+            }
+    };
+    load_round(0);
     for (int d0 = 0; d0 < D; d0 += DC) {
+        // ---- stage the window-pair terms of the halo for DC disparities
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             const int j = threadIdx.x + 256 * s;
             if (j >= NQ) break;
-            float g[DC], cc[DC], sb[DC], mb[DC];
-#pragma unroll
-            for (int k = 0; k < DC; ++k) {      // all loads of the DC disparities first
-                const bool ok = qin[s] && d0 + k < D;
-                const size_t vo = vbase[s] + (size_t)(ok ? d0 + k : 0) * HW, so = sbase[s] - (ok ? d0 + k : 0);
-                g[k] = ok ? a.gc[vo] : 0.f;
-                cc[k] = ok ? a.cost[vo] : 1.f;
-                sb[k] = ok ? a.sdt[so] : 0.f;
-                mb[k] = ok ? a.mut[so] : 0.f;
-            }
 #pragma unroll
             for (int k = 0; k < DC; ++k) {
                 float A = 0.f, C = 0.f, Bq = 0.f;
-                if (qisa[s] > 0.f && sb[k] > 0.f) {
-                    const float isb = __frcp_rn(sb[k]);
-                    const float gn = g[k] * a.inv_n, gnc = gn * (1.f - cc[k]);
+                if (qisa[s] > 0.f && sb[s][k] > 0.f) {
+                    const float isb = __frcp_rn(sb[s][k]);
+                    const float gn = g[s][k] * a.inv_n, gnc = gn * (1.f - cc[s][k]);
                     A = -gn * qisa[s] * isb;
                     Bq = gnc * qisa[s] * qisa[s];
                     C = gnc * isb * isb;
                 }
-                sAmb[s] = fmaf(A, mb[k], sAmb[s]);
+                sAmb[s] = fmaf(A, mb[s][k], sAmb[s]);
                 sB[s] += Bq;
                 sBmu[s] = fmaf(Bq, qmu[s], sBmu[s]);
-                st[(0 * DC + k) * NQ + j] = A;
-                st[(1 * DC + k) * NQ + j] = A * qmu[s];
-                st[(2 * DC + k) * NQ + j] = C;
-                st[(3 * DC + k) * NQ + j] = C * mb[k];
+                st[(0 * DC + k) * SP + qofs[s]] = A;
+                st[(1 * DC + k) * SP + qofs[s]] = A * qmu[s];
+                st[(2 * DC + k) * SP + qofs[s]] = C;
+                st[(3 * DC + k) * SP + qofs[s]] = C * mb[s][k];
             }
         }
+        if (d0 + DC < D) load_round(d0 + DC);
         __syncthreads();
-        for (int e = threadIdx.x; e < 4 * DC * QH * 32; e += 256) {
-            const int kk = e / (QH * 32), rem = e - kk * QH * 32, row = rem >> 5, xc = rem & 31;
-            const float *src = st + kk * NQ + row * QW + xc;
-            float sum = 0.f;
+        // ---- box sums along rows: one running sum per (plane, halo row)
+        for (int t = threadIdx.x; t < NP * QH; t += 256) {
+            const int p = t / QH, row = t - p * QH;
+            row_box<WN>(st + p * SP + row * SW, hb + p * HP + row * HW_);
+        }
+        __syncthreads();
+        // ---- box sums along columns: one running sum per (plane, column) over the 8 tile rows
+        for (int t = threadIdx.x; t < NP * 32; t += 256) {
+            const int p = t >> 5, xc = t & 31;
+            const float *col = hb + p * HP + xc;
+            float *out = vb + p * 256 + xc;
+            float s = 0.f;
 #pragma unroll
-            for (int j = 0; j < WN; ++j) sum += src[j];
-            hb[e] = sum;
+            for (int i = 0; i < WN; ++i) s += col[i * HW_];
+            out[0] = s;
+#pragma unroll
+            for (int y = 1; y < 8; ++y) {
+                s += col[(y + WN - 1) * HW_] - col[(y - 1) * HW_];
+                out[y * 32] = s;
+            }
         }
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < DC; ++k) {
             const int d = d0 + k;
-            float bx[4];
-#pragma unroll
-            for (int qn = 0; qn < 4; ++qn) {
-                const float *col = hb + ((qn * DC + k) * QH + ty) * 32 + tx;
-                float sum = 0.f;
-#pragma unroll
-                for (int i = 0; i < WN; ++i) sum += col[i * 32];
-                bx[qn] = sum;
-            }
+            const float bA = vb[(0 * DC + k) * 256 + ty * 32 + tx], bAm = vb[(1 * DC + k) * 256 + ty * 32 + tx];
+            const float bC = vb[(2 * DC + k) * 256 + ty * 32 + tx], bCm = vb[(3 * DC + k) * 256 + ty * 32 + tx];
             if (xin && d < D) {
                 const float t = twrow[clampi(X - d, 0, W - 1)];
                 if (a.gamma)
                     a.gamma[(((size_t)b * D + d) * a.Hr + (Y + RW)) * a.Wr + (X + RW)] =
-                        fmaf(rv, bx[0], -bx[1]) + fmaf(t, bx[2], -bx[3]);
-                gacc = fmaf(t, bx[0], gacc);
+                        fmaf(rv, bA, -bAm) + fmaf(t, bC, -bCm);
+                gacc = fmaf(t, bA, gacc);
             }
         }
+        // the next round's staging writes st only: hb and vb are rewritten after its barrier
     }
     // the d-independent terms: - box(sum_d A mu_b) + r box(sum_d B) - box(sum_d B mu_a)
     __syncthreads();
@@ -650,27 +689,23 @@ __global__ void __launch_bounds__(256) k_dcost_bwd(const CbArgs a)
     for (int s = 0; s < NS; ++s) {
         const int j = threadIdx.x + 256 * s;
         if (j >= NQ) break;
-        st[0 * NQ + j] = sAmb[s];
-        st[1 * NQ + j] = sB[s];
-        st[2 * NQ + j] = sBmu[s];
+        st[0 * SP + qofs[s]] = sAmb[s];
+        st[1 * SP + qofs[s]] = sB[s];
+        st[2 * SP + qofs[s]] = sBmu[s];
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < 3 * QH * 32; e += 256) {
-        const int kk = e / (QH * 32), rem = e - kk * QH * 32, row = rem >> 5, xc = rem & 31;
-        const float *src = st + kk * NQ + row * QW + xc;
-        float sum = 0.f;
-#pragma unroll
-        for (int j = 0; j < WN; ++j) sum += src[j];
-        hb[e] = sum;
+    for (int t = threadIdx.x; t < 3 * QH; t += 256) {
+        const int p = t / QH, row = t - p * QH;
+        row_box<WN>(st + p * SP + row * SW, hb + p * HP + row * HW_);
     }
     __syncthreads();
     float bx[3];
 #pragma unroll
     for (int qn = 0; qn < 3; ++qn) {
-        const float *col = hb + (qn * QH + ty) * 32 + tx;
+        const float *col = hb + qn * HP + ty * HW_ + tx;
         float sum = 0.f;
 #pragma unroll
-        for (int i = 0; i < WN; ++i) sum += col[i * 32];
+        for (int i = 0; i < WN; ++i) sum += col[i * HW_];
         bx[qn] = sum;
     }
     if (xin)
@@ -830,8 +865,8 @@ cudaError_t launch_agg(const AggArgs &a, int rb, int B, cudaStream_t st)
 template <int RW>
 cudaError_t launch_cb_rw(const CbArgs &a, int B, cudaStream_t st)
 {
-    constexpr int QW = 32 + 2 * RW, QH = 8 + 2 * RW;
-    const size_t smem = (size_t)4 * kCbDC * (QW * QH + QH * 32) * sizeof(float);
+    constexpr int QW = 32 + 2 * RW, QH = 8 + 2 * RW, NP = 4 * kCbDC;
+    const size_t smem = (size_t)NP * ((QW | 1) * QH + 33 * QH + 8 * 32) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_dcost_bwd<RW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
