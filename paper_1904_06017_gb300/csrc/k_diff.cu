@@ -43,6 +43,16 @@ enum { AGG_FWD = 0, AGG_H = 1, AGG_GC = 2 };
 
 __device__ __forceinline__ int clampi(int x, int lo, int hi) { return min(max(x, lo), hi); }
 
+// 2^x on the MUFU unit (relative error about 2^-22; -inf and huge negative x give +0).
+__device__ __forceinline__ float ex2_fast(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float lane(const float2 &v, int k) { return (k & 1) ? v.y : v.x; }
+
 // §3.1 integer row shift floor(s + 0.5) (exact in FP32 for |s| < 2^22), as the value added
 // back to the disparity.
 __device__ __forceinline__ float row_shift_value(float s) { return floorf(s + 0.5f); }
@@ -369,15 +379,17 @@ __global__ void __launch_bounds__(256) k_dagg(const AggArgs a)
         }
         __syncthreads();
 
-        float acc0[kAggRows][DC], acc1[kAggRows][TWO ? DC : 1], Z[kAggRows];
+        // accumulators in pairs of disparities (packed f32x2 FMAs)
+        float2 acc0[kAggRows][DC / 2], acc1[kAggRows][TWO ? DC / 2 : 1];
+        float Z[kAggRows];
 #pragma unroll
         for (int i = 0; i < kAggRows; ++i) {
             Z[i] = 0.f;
             if constexpr (TWO) S[i] = 0.f;
 #pragma unroll
-            for (int k = 0; k < DC; ++k) {
-                acc0[i][k] = 0.f;
-                if constexpr (TWO) acc1[i][k] = 0.f;
+            for (int k = 0; k < DC / 2; ++k) {
+                acc0[i][k] = make_float2(0.f, 0.f);
+                if constexpr (TWO) acc1[i][k] = make_float2(0.f, 0.f);
             }
         }
 #pragma unroll 1
@@ -396,24 +408,22 @@ __global__ void __launch_bounds__(256) k_dagg(const AggArgs a)
                     const int dy = r - RB - i;
                     if (dy < -RB || dy > RB) continue;
                     const float dd = sIp[i] - sq;
-                    const float w = exp2f(kx + ky[dy + RB] - dd * dd);
+                    const float w = ex2_fast(fmaf(-dd, dd, kx + ky[dy + RB]));
                     Z[i] += w;
+                    const float2 w2 = make_float2(w, w);
 #pragma unroll
                     for (int q = 0; q < NQ; ++q) {
-                        acc0[i][4 * q + 0] = fmaf(w, v4[q].x, acc0[i][4 * q + 0]);
-                        acc0[i][4 * q + 1] = fmaf(w, v4[q].y, acc0[i][4 * q + 1]);
-                        acc0[i][4 * q + 2] = fmaf(w, v4[q].z, acc0[i][4 * q + 2]);
-                        acc0[i][4 * q + 3] = fmaf(w, v4[q].w, acc0[i][4 * q + 3]);
+                        acc0[i][2 * q + 0] = __ffma2_rn(w2, make_float2(v4[q].x, v4[q].y), acc0[i][2 * q + 0]);
+                        acc0[i][2 * q + 1] = __ffma2_rn(w2, make_float2(v4[q].z, v4[q].w), acc0[i][2 * q + 1]);
                     }
                     if constexpr (TWO) {
                         const float wd = -w * dd;
                         S[i] += wd;
+                        const float2 wd2 = make_float2(wd, wd);
 #pragma unroll
                         for (int q = 0; q < NQ; ++q) {
-                            acc1[i][4 * q + 0] = fmaf(wd, v4[q].x, acc1[i][4 * q + 0]);
-                            acc1[i][4 * q + 1] = fmaf(wd, v4[q].y, acc1[i][4 * q + 1]);
-                            acc1[i][4 * q + 2] = fmaf(wd, v4[q].z, acc1[i][4 * q + 2]);
-                            acc1[i][4 * q + 3] = fmaf(wd, v4[q].w, acc1[i][4 * q + 3]);
+                            acc1[i][2 * q + 0] = __ffma2_rn(wd2, make_float2(v4[q].x, v4[q].y), acc1[i][2 * q + 0]);
+                            acc1[i][2 * q + 1] = __ffma2_rn(wd2, make_float2(v4[q].z, v4[q].w), acc1[i][2 * q + 1]);
                         }
                     }
                 }
@@ -430,7 +440,7 @@ __global__ void __launch_bounds__(256) k_dagg(const AggArgs a)
                 float z[DC], mc = st0[i];
 #pragma unroll
                 for (int k = 0; k < DC; ++k) {
-                    z[k] = -(acc0[i][k] * invZ) * a.kT;
+                    z[k] = -(lane(acc0[i][k >> 1], k) * invZ) * a.kT;
                     if (d0 + k < D) mc = fmaxf(mc, z[k]);
                 }
                 const float sc = exp2f(st0[i] - mc);
@@ -450,12 +460,12 @@ __global__ void __launch_bounds__(256) k_dagg(const AggArgs a)
                 for (int k = 0; k < DC; ++k) {
                     const int d = d0 + k;
                     if (d >= D) break;
-                    const float E = acc0[i][k] * invZ;
+                    const float E = lane(acc0[i][k >> 1], k) * invZ;
                     const float P = exp2f(-E * a.kT - st1[i]);
                     const float hv = -st0[i] * a.invT * P * ((float)d - st2[i]) * invZ;
                     a.h[((size_t)b * D + d) * HW + pix] = hv;
                     beta[i] = fmaf(hv, E, beta[i]);
-                    tacc[i] = fmaf(hv, acc1[i][k], tacc[i]);
+                    tacc[i] = fmaf(hv, lane(acc1[i][k >> 1], k), tacc[i]);
                 }
             } else {
 #pragma unroll
@@ -463,8 +473,8 @@ __global__ void __launch_bounds__(256) k_dagg(const AggArgs a)
                     const int d = d0 + k;
                     if (d >= D) break;
                     const size_t o = ((size_t)b * D + d) * HW + pix;
-                    a.gc[o] = acc0[i][k];
-                    tacc[i] = fmaf(a.cost[o], acc1[i][k], tacc[i]);
+                    a.gc[o] = lane(acc0[i][k >> 1], k);
+                    tacc[i] = fmaf(a.cost[o], lane(acc1[i][k >> 1], k), tacc[i]);
                 }
             }
         }
@@ -517,7 +527,7 @@ __global__ void __launch_bounds__(256) k_dagg(const AggArgs a)
                 const int dy = r - RB - i;
                 if (dy < -RB || dy > RB) continue;
                 const float dd = sIp[i] - sq;
-                const float w = exp2f(kx + ky[dy + RB] - dd * dd);
+                const float w = ex2_fast(fmaf(-dd, dd, kx + ky[dy + RB]));
                 sbeta[i] = fmaf(-w * dd, bq, sbeta[i]);
             }
         }

@@ -3,8 +3,10 @@
 //
 // Every reduction runs in two fixed-order stages: kDteBlocks blocks per pair write FP64
 // partial sums, one finishing thread per pair adds them in index order.  Per pixel the
-// energy and its adjoint work in FP32 with FP64 accumulation; the refinement sums, which
-// feed the FP64 normal equations of eq. (alpha3), are formed in FP64 per pixel.
+// energy and its adjoint work in FP32 with FP64 accumulation.  The refinement reduces the
+// map once to ten FP64 moments in centred coordinates; every step then evaluates the sums it
+// needs at its angle from them (exact algebra) and solves the normal equations of eq. (alpha3)
+// in FP64.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -117,41 +119,34 @@ __global__ void k_dte_finish(const double *__restrict__ part, const double *__re
     }
 }
 
-// The ten sums of the refinement at the current psi, FP64 per pixel:
-// n, Sy, Syy, Sl, Sly, Sx, Sxy, Sxx, Slx, Sll over the fitted pixels.
-__global__ void __launch_bounds__(kDteThreads) k_dref_sums(const float *__restrict__ disp,
-                                                           const uint8_t *__restrict__ mask,
-                                                           const double *__restrict__ state,
-                                                           double *__restrict__ part, int W, int H)
+// The ten moments of the fitted pixels in coordinates centred on the image, FP64:
+// n, S_u, S_v, S_l, S_uu, S_uv, S_vv, S_ul, S_vl, S_ll with u' = u - (W-1)/2, v' = v - (H-1)/2.
+// Every sum the refinement needs at an angle psi is a fixed combination of them.
+__global__ void __launch_bounds__(kDteThreads) k_dref_moments(const float *__restrict__ disp,
+                                                              const uint8_t *__restrict__ mask,
+                                                              double *__restrict__ part, int W, int H)
 {
-    __shared__ double sc[2];
     const int b = blockIdx.y;
-    if (threadIdx.x == 0) {
-        sc[0] = cos(state[2 * b]);
-        sc[1] = sin(state[2 * b]);
-    }
-    __syncthreads();
-    const double c = sc[0], s = sc[1];
     const int HW = W * H;
     const float *L = disp + (size_t)b * HW;
     const uint8_t *M = mask ? mask + (size_t)b * HW : nullptr;
+    const double uc = 0.5 * (W - 1), vc = 0.5 * (H - 1);
     double acc[kDteSums];
 #pragma unroll
     for (int k = 0; k < kDteSums; ++k) acc[k] = 0.0;
     for (int i = blockIdx.x * kDteThreads + threadIdx.x; i < HW; i += kDteBlocks * kDteThreads) {
         if (M && !M[i]) continue;
         const int v = i / W, u = i - v * W;
-        const double y = (double)v * c - (double)u * s, x = (double)u * c + (double)v * s;
-        const double l = (double)L[i];
+        const double x = (double)u - uc, y = (double)v - vc, l = (double)L[i];
         acc[0] += 1.0;
-        acc[1] += y;
-        acc[2] = fma(y, y, acc[2]);
+        acc[1] += x;
+        acc[2] += y;
         acc[3] += l;
-        acc[4] = fma(l, y, acc[4]);
-        acc[5] += x;
-        acc[6] = fma(x, y, acc[6]);
-        acc[7] = fma(x, x, acc[7]);
-        acc[8] = fma(l, x, acc[8]);
+        acc[4] = fma(x, x, acc[4]);
+        acc[5] = fma(x, y, acc[5]);
+        acc[6] = fma(y, y, acc[6]);
+        acc[7] = fma(x, l, acc[7]);
+        acc[8] = fma(y, l, acc[8]);
         acc[9] = fma(l, l, acc[9]);
     }
     block_sum_store<kDteSums>(acc, part + ((size_t)b * kDteBlocks + blockIdx.x) * kDteSums);
@@ -165,40 +160,58 @@ __device__ double wrap_half_pi_d(double psi)
     return psi;
 }
 
-// One refinement step per pair: the line fit of eq. (alpha3) from the FP64 normal
-// equations, E and g = dE/dpsi there (eq. d_e_min), the Gauss-Newton curvature, and the
-// step psi <- wrap(psi - g / H).  Writes trajectory entry k.
-__global__ void k_dref_step(const double *__restrict__ part, double *__restrict__ state,
-                            double *__restrict__ traj, int k, int steps, int B)
+// All refinement steps of one pair (one thread per pair).  At each angle the sums over the
+// fitted pixels of y, y^2, l y, x, x y, x^2, l x (raw coordinates, x = u cos + v sin, y = v cos
+// - u sin, eq. x, eq. y) follow from the centred moments; then the line fit of eq. (alpha3)
+// from the FP64 normal equations, E and g = dE/dpsi there (eq. d_e_min), the Gauss-Newton
+// curvature and the step psi <- wrap(psi - g / H).  Trajectory entry k is written at each step.
+__global__ void k_dref_run(const double *__restrict__ part, const double *__restrict__ state, double *__restrict__ traj,
+                           int steps, int W, int H, int B)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
-    double S[kDteSums];
-    for (int q = 0; q < kDteSums; ++q) S[q] = 0.0;
+    double m[kDteSums];
+    for (int q = 0; q < kDteSums; ++q) m[q] = 0.0;
     for (int j = 0; j < kDteBlocks; ++j)
-        for (int q = 0; q < kDteSums; ++q) S[q] += part[((size_t)b * kDteBlocks + j) * kDteSums + q];
-    const double n = S[0], Sy = S[1], Syy = S[2], Sl = S[3], Sly = S[4], Sx = S[5], Sxy = S[6],
-                 Sxx = S[7], Slx = S[8], Sll = S[9];
-    const double psi = state[2 * b];
-    const double det = n * Syy - Sy * Sy;
-    double a0 = 0.0, a1 = 0.0, g = 0.0, Hc = 0.0;
-    if (n > 0.0 && det > 0.0) {
-        a0 = (Syy * Sl - Sy * Sly) / det;
-        a1 = (n * Sly - Sy * Sl) / det;
-        g = 2.0 * a1 * (Slx - a0 * Sx - a1 * Sxy);
-        const double xt2 = Sxx - (Syy * Sx * Sx - 2.0 * Sy * Sx * Sxy + n * Sxy * Sxy) / det;
-        Hc = 2.0 * a1 * a1 * xt2;
-    } else if (n > 0.0) {
-        a0 = Sl / n;
+        for (int q = 0; q < kDteSums; ++q) m[q] += part[((size_t)b * kDteBlocks + j) * kDteSums + q];
+    const double n = m[0], Su = m[1], Sv = m[2], Sl = m[3], Suu = m[4], Suv = m[5], Svv = m[6], Sul = m[7],
+                 Svl = m[8], Sll = m[9];
+    const double uc = 0.5 * (W - 1), vc = 0.5 * (H - 1);
+    double psi = state[2 * b];
+    for (int k = 0; k <= steps; ++k) {
+        const double c = cos(psi), s = sin(psi);
+        // raw x = x' + xc, y = y' + yc with the centred rotated coordinates x', y'
+        const double xc = uc * c + vc * s, yc = vc * c - uc * s;
+        const double Sx1 = Su * c + Sv * s, Sy1 = Sv * c - Su * s;                // sums of x', y'
+        const double Sxx1 = c * c * Suu + 2.0 * c * s * Suv + s * s * Svv;
+        const double Syy1 = c * c * Svv - 2.0 * c * s * Suv + s * s * Suu;
+        const double Sxy1 = c * s * (Svv - Suu) + (c * c - s * s) * Suv;
+        const double Slx1 = Sul * c + Svl * s, Sly1 = Svl * c - Sul * s;
+        const double Sy = Sy1 + n * yc, Sx = Sx1 + n * xc;
+        const double Syy = Syy1 + 2.0 * yc * Sy1 + n * yc * yc;
+        const double Sxx = Sxx1 + 2.0 * xc * Sx1 + n * xc * xc;
+        const double Sxy = Sxy1 + xc * Sy1 + yc * Sx1 + n * xc * yc;
+        const double Sly = Sly1 + yc * Sl, Slx = Slx1 + xc * Sl;
+        const double det = n * Syy - Sy * Sy;
+        double a0 = 0.0, a1 = 0.0, g = 0.0, Hc = 0.0;
+        if (n > 0.0 && det > 0.0) {
+            a0 = (Syy * Sl - Sy * Sly) / det;
+            a1 = (n * Sly - Sy * Sl) / det;
+            g = 2.0 * a1 * (Slx - a0 * Sx - a1 * Sxy);
+            const double xt2 = Sxx - (Syy * Sx * Sx - 2.0 * Sy * Sx * Sxy + n * Sxy * Sxy) / det;
+            Hc = 2.0 * a1 * a1 * xt2;
+        } else if (n > 0.0) {
+            a0 = Sl / n;
+        }
+        const double E = Sll - 2.0 * a0 * Sl - 2.0 * a1 * Sly + a0 * a0 * n + 2.0 * a0 * a1 * Sy + a1 * a1 * Syy;
+        double *t = traj + ((size_t)b * (steps + 1) + k) * 5;
+        t[0] = psi;
+        t[1] = a0;
+        t[2] = a1;
+        t[3] = g;
+        t[4] = E;
+        if (k < steps && Hc > 0.0 && isfinite(g / Hc)) psi = wrap_half_pi_d(psi - g / Hc);
     }
-    const double E = Sll - 2.0 * a0 * Sl - 2.0 * a1 * Sly + a0 * a0 * n + 2.0 * a0 * a1 * Sy + a1 * a1 * Syy;
-    double *t = traj + ((size_t)b * (steps + 1) + k) * 5;
-    t[0] = psi;
-    t[1] = a0;
-    t[2] = a1;
-    t[3] = g;
-    t[4] = E;
-    if (k < steps && Hc > 0.0 && isfinite(g / Hc)) state[2 * b] = wrap_half_pi_d(psi - g / Hc);
 }
 
 __global__ void k_dref_init(double *state, double psi, int B)
@@ -294,9 +307,7 @@ extern "C" int stereo_dt_refine_roll(int32_t W, int32_t H, int32_t B, const floa
     cudaStream_t st = (cudaStream_t)stream;
     double *part = (double *)ws, *state = dte_state(B, ws);
     k_dref_init<<<(B + 63) / 64, 64, 0, st>>>(state, psi_init, B);
-    for (int k = 0; k <= steps; ++k) {
-        k_dref_sums<<<dim3(kDteBlocks, B), kDteThreads, 0, st>>>(disp, mask, state, part, W, H);
-        k_dref_step<<<(B + 63) / 64, 64, 0, st>>>(part, state, traj, k, steps, B);
-    }
+    k_dref_moments<<<dim3(kDteBlocks, B), kDteThreads, 0, st>>>(disp, mask, part, W, H);
+    k_dref_run<<<(B + 63) / 64, 64, 0, st>>>(part, state, traj, steps, W, H, B);
     return cuda_error(cudaGetLastError(), who);
 }
