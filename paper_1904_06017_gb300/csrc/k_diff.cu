@@ -33,13 +33,20 @@ namespace sgb {
 namespace {
 
 constexpr int kAggRows = 4;          // pixels per thread in k_dagg (a column segment)
-constexpr int kAggTile = 32;         // k_dagg tile: 32 x 32 pixels, 256 threads
+
+enum { AGG_FWD = 0, AGG_H = 1, AGG_GC = 2 };
+
+// k_dagg tiles: the recomputing backward pass (AGG_H) double-buffers its disparity chunks on
+// 64 x 24 tiles of 12 warps (one block per SM); the other two stream each chunk into one
+// buffer on 32 x 32 tiles of 8 warps, several blocks per SM hiding the copies instead.
+__host__ __device__ constexpr bool agg_dbuf(int mode) { return mode == AGG_H; }
+__host__ __device__ constexpr int agg_tx(int mode) { return agg_dbuf(mode) ? 64 : 32; }
+__host__ __device__ constexpr int agg_ty(int mode) { return agg_dbuf(mode) ? 24 : 32; }
+__host__ __device__ constexpr int agg_threads(int mode) { return agg_dbuf(mode) ? 384 : 256; }
 constexpr int kAggDC = 8;            // disparities per chunk in k_dagg
 constexpr int kCostDC = 16;          // disparities per block in k_dcost
 constexpr float kFar = 1e18f;        // scaled intensity of an out-of-image neighbour: weight 0
 constexpr float kLog2e = 1.4426950408889634f;
-
-enum { AGG_FWD = 0, AGG_H = 1, AGG_GC = 2 };
 
 __device__ __forceinline__ int clampi(int x, int lo, int hi) { return min(max(x, lo), hi); }
 
@@ -305,25 +312,63 @@ struct AggArgs {
     float gw_scale;        // 2 / (sigma1^2 kappa)
 };
 
-// One 32 x 32 tile per block; thread (tx, ty) owns the pixels (x0 + tx, y0 + 4 ty + i),
+// The disparity chunks of a tile are staged in two shared-memory buffers: while chunk k is
+// aggregated, the copies of chunk k + 1 are in flight (cp.async, 4 bytes per element, zero
+// fill outside the image and beyond D).
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, bool valid)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// One tile per block (agg_tx x agg_ty); thread (tx, ty) owns the pixels (x0 + tx, y0 + 4 ty + i),
 // i < 4, and kAggDC disparities at a time.  The weights of eq. (omega_s) are formed as
 // exp2(kx + ky - (sI_p - sI_q)^2) with sI = kappa I; an out-of-image neighbour has
 // sI = kFar and a zero value, so its weight and every product with it are exactly 0.
 template <int MODE, int RB>
-__global__ void __launch_bounds__(256) k_dagg(const AggArgs a)
+__global__ void __launch_bounds__(agg_threads(MODE)) k_dagg(const AggArgs a)
 {
     constexpr int DC = kAggDC, NQ = DC / 4, NR = kAggRows + 2 * RB;
-    constexpr int TW = kAggTile + 2 * RB, TH = kAggTile + 2 * RB;
+    constexpr bool DB = agg_dbuf(MODE);
+    constexpr int kAggTX = agg_tx(MODE), kAggTY = agg_ty(MODE), kAggThreads = agg_threads(MODE);
+    constexpr int TW = kAggTX + 2 * RB, TH = kAggTY + 2 * RB;
     constexpr bool TWO = MODE != AGG_FWD;
     extern __shared__ float4 smem4[];
-    float4 *V = smem4;                              // [NQ][TH][TW]
-    float *sI = (float *)(V + NQ * TH * TW);        // [TH][TW]
-    const int b = blockIdx.z, x0 = blockIdx.x * kAggTile, y0 = blockIdx.y * kAggTile;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    float4 *Vbuf = smem4;                                     // [1 or 2][NQ][TH][TW]
+    float *sI = (float *)(Vbuf + (DB ? 2 : 1) * NQ * TH * TW); // [TH][TW]
+    const int b = blockIdx.z, x0 = blockIdx.x * kAggTX, y0 = blockIdx.y * kAggTY;
+    constexpr int WCOL = kAggTX / 32;               // warp columns of the tile
+    const int warp = threadIdx.x >> 5;
+    const int tx = (warp % WCOL) * 32 + (threadIdx.x & 31), ty = warp / WCOL;
     const int W = a.W, H = a.H, D = a.D;
     const size_t HW = (size_t)H * W;
     const float *img = a.img + b * HW;
-    for (int i = threadIdx.x; i < TH * TW; i += 256) {
+    auto issue_chunk = [&](int d0, float4 *V) {
+        for (int i = threadIdx.x; i < TH * TW; i += kAggThreads) {
+            const int r = i / TW, c = i - r * TW, y = y0 - RB + r, x = x0 - RB + c;
+            const bool in = y >= 0 && y < H && x >= 0 && x < W;
+            const float *src = a.vol + ((size_t)b * D) * HW + (in ? (size_t)y * W + x : 0);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                float *dst = reinterpret_cast<float *>(&V[(q * TH + r) * TW + c]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int d = d0 + 4 * q + j;
+                    const bool ok = in && d < D;
+                    cp_async4(dst + j, ok ? src + (size_t)d * HW : a.vol, ok);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    if constexpr (DB) issue_chunk(0, Vbuf);
+    for (int i = threadIdx.x; i < TH * TW; i += kAggThreads) {
         const int r = i / TW, c = i - r * TW, y = y0 - RB + r, x = x0 - RB + c;
         sI[i] = (y >= 0 && y < H && x >= 0 && x < W) ? img[(size_t)y * W + x] * a.kappa : kFar;
     }
@@ -360,22 +405,18 @@ __global__ void __launch_bounds__(256) k_dagg(const AggArgs a)
 #pragma unroll
     for (int i = 0; i < kAggRows; ++i) S[i] = beta[i] = tacc[i] = 0.f;
 
-    for (int d0 = 0; d0 < D; d0 += DC) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < TH * TW; i += 256) {
-            const int r = i / TW, c = i - r * TW, y = y0 - RB + r, x = x0 - RB + c;
-            const bool in = y >= 0 && y < H && x >= 0 && x < W;
-            const float *src = a.vol + ((size_t)b * D) * HW + (in ? (size_t)y * W + x : 0);
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                float e[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int d = d0 + 4 * q + j;
-                    e[j] = (in && d < D) ? src[(size_t)d * HW] : 0.f;
-                }
-                V[(q * TH + r) * TW + c] = make_float4(e[0], e[1], e[2], e[3]);
+    for (int d0 = 0, kc = 0; d0 < D; d0 += DC, ++kc) {
+        const float4 *V = Vbuf + (DB ? (kc & 1) * NQ * TH * TW : 0);
+        if constexpr (DB) {
+            if (d0 + DC < D) {
+                issue_chunk(d0 + DC, Vbuf + ((kc + 1) & 1) * NQ * TH * TW);
+                cp_async_wait<1>();      // this chunk's copies are complete
+            } else {
+                cp_async_wait<0>();
             }
+        } else {
+            issue_chunk(d0, Vbuf);
+            cp_async_wait<0>();
         }
         __syncthreads();
 
@@ -478,6 +519,7 @@ __global__ void __launch_bounds__(256) k_dagg(const AggArgs a)
                 }
             }
         }
+        __syncthreads();   // every thread is done with this buffer before it is refilled
     }
 
     if constexpr (MODE == AGG_FWD) {
@@ -505,8 +547,8 @@ __global__ void __launch_bounds__(256) k_dagg(const AggArgs a)
     }
     // AGG_GC: the weights' term of beta, sum_q w (sI_q - sI_x) beta(q), over a staged tile
     __syncthreads();
-    float *sb = (float *)V;
-    for (int i = threadIdx.x; i < TH * TW; i += 256) {
+    float *sb = (float *)Vbuf;
+    for (int i = threadIdx.x; i < TH * TW; i += kAggThreads) {
         const int r = i / TW, c = i - r * TW, y = y0 - RB + r, x = x0 - RB + c;
         sb[i] = (y >= 0 && y < H && x >= 0 && x < W) ? a.beta[b * HW + (size_t)y * W + x] : 0.f;
     }
@@ -847,13 +889,14 @@ __global__ void __launch_bounds__(256) k_dshift_grad(const float *__restrict__ g
 template <int MODE, int RB>
 cudaError_t launch_agg_rb(const AggArgs &a, int B, cudaStream_t st)
 {
-    constexpr int T = kAggTile + 2 * RB;
-    const size_t smem = (size_t)T * T * (sizeof(float4) * (kAggDC / 4) + sizeof(float));
+    constexpr int TW = agg_tx(MODE) + 2 * RB, TH = agg_ty(MODE) + 2 * RB;
+    constexpr int NB = agg_dbuf(MODE) ? 2 : 1;
+    const size_t smem = (size_t)TW * TH * (NB * sizeof(float4) * (kAggDC / 4) + sizeof(float));
     cudaError_t e = cudaFuncSetAttribute(k_dagg<MODE, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((a.W + kAggTile - 1) / kAggTile, (a.H + kAggTile - 1) / kAggTile, B);
-    k_dagg<MODE, RB><<<grid, 256, smem, st>>>(a);
+    dim3 grid((a.W + agg_tx(MODE) - 1) / agg_tx(MODE), (a.H + agg_ty(MODE) - 1) / agg_ty(MODE), B);
+    k_dagg<MODE, RB><<<grid, agg_threads(MODE), smem, st>>>(a);
     return cudaGetLastError();
 }
 
