@@ -878,6 +878,8 @@ FusedKernel pick_rb(int rb)
 // unit per storage type and tile family keeps the instantiations compiling in parallel.
 FusedKernel pick_fused_f32(int rb, int dc, int wc);    // k_fused_f32.cu: WC = 2, DC in {12, 4}
 FusedKernel pick_fused_f32_tiles(int rb, int dc, int wc);  // k_fused_f32_tiles.cu: WC in {1, 4}, DC = 12
+FusedKernel pick_fused_f32_wc4(int rb);                // k_fused_f32_wc4.cu: WC = 4, DC = 12
+FusedKernel pick_fused_f32_dc4(int rb);                // k_fused_f32_dc4.cu: WC = 2, DC = 4
 FusedKernel pick_fused_f16(int rb, int dc, int wc);    // k_fused_f16.cu: WC = 2, DC = 12
 FusedKernel pick_fused_bf16(int rb, int dc, int wc);   // k_fused_bf16.cu: WC = 2, DC = 12
 FusedKernel pick_fused_ws(int rb, int dc);             // k_fused_ws.cu: warp-specialised, FP32, DC = 12

@@ -10,7 +10,7 @@ FusedKernel pick_fused_f32(int rb, int dc, int wc)
 {
     if (wc != 2) return pick_fused_f32_tiles(rb, dc, wc);
     if (dc == 12) return pick_rb<12, float, 2>(rb);
-    if (dc == 4) return pick_rb<4, float, 2>(rb);
+    if (dc == 4) return pick_fused_f32_dc4(rb);
     return nullptr;
 }
 
