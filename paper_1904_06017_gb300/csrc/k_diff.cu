@@ -231,14 +231,16 @@ __global__ void __launch_bounds__(256) k_dstats(const float *__restrict__ img, i
 }
 
 // eq. (c) for a 32 x 8 pixel tile and kCostDC disparities: the centred reference window
-// times the target window, corrected by the target mean through sum_i (a_i - mu_a).
+// times the target window, corrected by the target mean through sum_i (a_i - mu_a).  Along a
+// block row the target values of the DC disparities slide by one column per step, so they
+// are kept in a register window that takes one new shared-memory load per step.
+template <int RW>
 __global__ void __launch_bounds__(256) k_dcost(const float *__restrict__ ref, const float *__restrict__ tw,
                                                const float *__restrict__ mur, const float *__restrict__ sdr,
                                                const float *__restrict__ mut, const float *__restrict__ sdt,
-                                               float *__restrict__ cost, int W, int H, int D, int rw,
-                                               int nchunk)
+                                               float *__restrict__ cost, int W, int H, int D, int nchunk)
 {
-    constexpr int DC = kCostDC;
+    constexpr int DC = kCostDC, rw = RW;
     extern __shared__ float s[];
     const int sw = 32 + 2 * rw, sh = 8 + 2 * rw, st = 32 + 2 * rw + DC - 1;
     float *rs = s, *ts = s + sw * sh;
@@ -261,19 +263,29 @@ __global__ void __launch_bounds__(256) k_dcost(const float *__restrict__ ref, co
     if (u >= W || v >= H) return;
     const size_t pix = b * HW + (size_t)v * W + u;
     const float ma = mur[pix], sa = sdr[pix];
-    const int w = 2 * rw + 1;
+    constexpr int w = 2 * RW + 1;
     float acc[DC];
 #pragma unroll
     for (int k = 0; k < DC; ++k) acc[k] = 0.f;
     float asum = 0.f;
+#pragma unroll 1
     for (int dy = 0; dy < w; ++dy) {
         const float *rrow = rs + (ty + dy) * sw + tx;
         const float *trow = ts + (ty + dy) * st + tx + (DC - 1);
+        float win[DC];                      // win[k] = trow[dx - k]
+#pragma unroll
+        for (int k = 0; k < DC; ++k) win[k] = trow[-k];
+#pragma unroll
         for (int dx = 0; dx < w; ++dx) {
+            if (dx > 0) {
+#pragma unroll
+                for (int k = DC - 1; k > 0; --k) win[k] = win[k - 1];
+                win[0] = trow[dx];
+            }
             const float a = rrow[dx] - ma;
             asum += a;
 #pragma unroll
-            for (int k = 0; k < DC; ++k) acc[k] = fmaf(a, trow[dx - k], acc[k]);
+            for (int k = 0; k < DC; ++k) acc[k] = fmaf(a, win[k], acc[k]);
         }
     }
     const int We = W + D - 1;
@@ -1010,8 +1022,22 @@ extern "C" int stereo_softargmin_fwd(const stereo_diff_params *p, const float *r
                                                                          d.rw, w.mut, w.sdt);
     const int nchunk = (d.D + kCostDC - 1) / kCostDC;
     const size_t csm = ((size_t)(32 + 2 * d.rw) + (32 + 2 * d.rw + kCostDC - 1)) * (8 + 2 * d.rw) * sizeof(float);
-    k_dcost<<<dim3((d.W + 31) / 32, (d.H + 7) / 8, B * nchunk), 256, csm, st>>>(
-        ref, w.tw, w.mur, w.sdr, w.mut, w.sdt, w.cost, d.W, d.H, d.D, d.rw, nchunk);
+    {
+        const dim3 grid((d.W + 31) / 32, (d.H + 7) / 8, B * nchunk);
+#define SGB_DCOST(R)                                                                                  \
+    k_dcost<R><<<grid, 256, csm, st>>>(ref, w.tw, w.mur, w.sdr, w.mut, w.sdt, w.cost, d.W, d.H, d.D, nchunk)
+        switch (d.rw) {
+        case 0: SGB_DCOST(0); break;
+        case 1: SGB_DCOST(1); break;
+        case 2: SGB_DCOST(2); break;
+        case 3: SGB_DCOST(3); break;
+        case 4: SGB_DCOST(4); break;
+        case 5: SGB_DCOST(5); break;
+        case 6: SGB_DCOST(6); break;
+        default: SGB_DCOST(7); break;
+        }
+#undef SGB_DCOST
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, who);
     AggArgs a = agg_args(p, d, w, ref);
