@@ -193,7 +193,7 @@ static std::string tune_key(const stereo_batch *b)
 {
     std::string k;
     char buf[96];
-    snprintf(buf, sizeof(buf), "c5 w%d k%d t%d sm%d |", b->bp.win, b->bp.bil, b->bp.cost_dtype, b->nsm);
+    snprintf(buf, sizeof(buf), "c6 w%d k%d t%d sm%d |", b->bp.win, b->bp.bil, b->bp.cost_dtype, b->nsm);
     k += buf;
     for (const stereo_pair_desc &d : b->pairs) {
         snprintf(buf, sizeof(buf), " %dx%dx%d", d.width, d.height, d.max_disp);
@@ -258,11 +258,12 @@ static int autotune(stereo_batch *b, int *wc_out, int *dc_out, int *source)
 {
     const char *path = getenv("STEREO_AUTOTUNE_CACHE");
     const std::string key = tune_key(b);
-    if (cache_lookup(path, key, wc_out, dc_out) && pick_fused(b->bp.cost_dtype, b->bp.bil / 2, *dc_out, *wc_out)) {
+    if (cache_lookup(path, key, wc_out, dc_out) && pick_fused(b->bp.cost_dtype, b->bp.bil / 2, *dc_out, *wc_out) &&
+        (*wc_out != kTcWC || tc_supported(b->bp.cost_dtype, b->bp.bil, b->bp.sigma1))) {
         *source = 1;
         return STEREO_OK;
     }
-    const int cand[][2] = {{kWsWC, 12}, {2, 12}, {1, 12}, {4, 12}, {2, 4}};
+    const int cand[][2] = {{kTcWC, 16}, {kWsWC, 12}, {2, 12}, {1, 12}, {4, 12}, {2, 4}};
     double best_ms = 1e30;
     int best_wc = 0, best_dc = 0;
     cudaEvent_t e0, e1;
@@ -270,6 +271,7 @@ static int autotune(stereo_batch *b, int *wc_out, int *dc_out, int *source)
     cudaEventCreate(&e1);
     for (const auto &c : cand) {
         if (!pick_fused(b->bp.cost_dtype, b->bp.bil / 2, c[1], c[0])) continue;
+        if (c[0] == kTcWC && !tc_supported(b->bp.cost_dtype, b->bp.bil, b->bp.sigma1)) continue;
         if (build(b, c[0], c[1]) != STEREO_OK) continue;   // e.g. shared memory does not fit
         int rc = enqueue_pre(b, b->cap);
         if (!rc) rc = enqueue_fused(b, b->cap);   // warm-up
@@ -329,9 +331,12 @@ int stereo_batch_create(const stereo_batch_params *p, int32_t n, const stereo_pa
     if (!p || !pairs || !out) return set_error(STEREO_EINVAL, "stereo_batch_create: null pointer");
     *out = nullptr;
     if (n < 1 || n > 4096) return set_error(STEREO_EINVAL, "stereo_batch_create: n = %d outside 1..4096", n);
-    if ((p->tile_wc && p->tile_wc != 1 && p->tile_wc != 2 && p->tile_wc != 4 && p->tile_wc != kWsWC) ||
-        (p->tile_dc && p->tile_dc != 4 && p->tile_dc != 12))
-        return set_error(STEREO_EINVAL, "stereo_batch_create: tile_wc must be 0, 1, 2, 4 or 8 and tile_dc 0, 4 or 12");
+    if ((p->tile_wc && p->tile_wc != 1 && p->tile_wc != 2 && p->tile_wc != 4 && p->tile_wc != kWsWC &&
+         p->tile_wc != kTcWC) ||
+        (p->tile_dc && p->tile_dc != 4 && p->tile_dc != 12 && p->tile_dc != 16))
+        return set_error(STEREO_EINVAL, "stereo_batch_create: tile_wc must be 0, 1, 2, 4, 8 or 16 and tile_dc 0, 4, 12 or 16");
+    if (p->tile_wc == kTcWC && !tc_supported(p->cost_dtype, p->bil, p->sigma1))
+        return set_error(STEREO_ENOTSUP, "stereo_batch_create: tile_wc 16 needs FP16 / BF16 storage, bil <= 13 and sigma1 <= 150");
     for (int i = 0; i < n; ++i) {
         const stereo_pair_desc &d = pairs[i];
         if (!d.ref_dev || !d.tgt_dev || !d.shift_dev || !d.tgt_warped_dev || !d.disp_dev || !d.valid_dev ||

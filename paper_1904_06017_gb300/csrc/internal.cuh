@@ -29,10 +29,20 @@ constexpr int kWsThreads = 32 * (kWsProdWarps + kWsConsWarps);
 constexpr int kWsPY = 4;
 constexpr int kWsBand = 3;          // cost rows per band of the producers' two-pass window sums
 constexpr int kWsMaxRB = 5;         // the two cost buffers fit shared memory up to bil = 11
-__host__ __device__ constexpr int tile_x(int wc) { return wc == kWsWC ? 64 : 32 * wc; }
+// The tensor-core form (tile code kTcWC, FP16 / BF16 storage): 64 x 36 tiles, kWarps warps,
+// 16 disparities per chunk, aggregation by mma.sync over 4 x 4 pixel patches, bil <= 13.
+constexpr int kTcWC = 16;
+constexpr int kTcMaxRB = 6;
+constexpr float kTcMaxSigma1 = 150.f;   // -s^2 stays a normal FP16 number
+__host__ __device__ constexpr int tile_x(int wc) { return wc == kWsWC || wc == kTcWC ? 64 : 32 * wc; }
 __host__ __device__ constexpr int tile_y(int wc)
 {
-    return wc == kWsWC ? kWsPY * (kWsConsWarps / 2) : kPY * (kWarps / wc);
+    return wc == kWsWC ? kWsPY * (kWsConsWarps / 2) : wc == kTcWC ? 36 : kPY * (kWarps / wc);
+}
+// Whether the tensor-core form can run these parameters.
+inline bool tc_supported(int cost_dtype, int bil, float sigma1)
+{
+    return cost_dtype != STEREO_F32 && bil / 2 <= kTcMaxRB && sigma1 <= kTcMaxSigma1;
 }
 __host__ __device__ constexpr int fused_threads(int wc) { return wc == kWsWC ? kWsThreads : kThreads; }
 constexpr int kMaxRB = 7;          // bil <= 15

@@ -109,6 +109,62 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
+// ----------------------------------------------------------------- tile claim and staging
+// Claims the launch's next tile: a single pair walks its tiles in a fixed order (blockIdx.x,
+// + gridDim.x, ...); a batch claims work-list items (pair, tile) with an atomic counter,
+// heaviest first.  Copies the tile's pair arguments to s_args and returns its descriptor, or
+// nullptr once the work list is exhausted.  Called by all NT threads of the CTA.
+template <int NT>
+__device__ __forceinline__ const PairDesc *claim_tile(const PairDesc &single, const PairDesc *pairs,
+                                                      const int2 *items, int nitems, int *counter, int iter,
+                                                      FusedArgs &s_args, int &s_item, int tid, int &tx, int &ty)
+{
+    if (tid == 0) s_item = pairs ? atomicAdd(counter, 1) : (int)blockIdx.x + iter * (int)gridDim.x;
+    __syncthreads();
+    const int item = s_item;
+    if (item >= nitems) return nullptr;
+    int p = 0;
+    if (pairs) {
+        const int2 it = items[item];
+        p = it.x;
+        tx = it.y & 0xffff;
+        ty = it.y >> 16;
+    } else {
+        tx = item % single.ntx;
+        ty = item / single.ntx;
+    }
+    const PairDesc *pd = pairs ? pairs + p : &single;
+    const int *src = reinterpret_cast<const int *>(&pd->a);
+    int *dst = reinterpret_cast<int *>(&s_args);
+    for (int i = tid; i < (int)(sizeof(FusedArgs) / 4); i += NT) dst[i] = src[i];
+    __syncthreads();
+    return pd;
+}
+
+// Stages the reference tile and the warped-target strip of the tile at (x0, y0) into sref /
+// stgt with TMA; the mbarrier completes once per tile (phase iter & 1).  The wait is bounded
+// (about a second of clock cycles): false, with the status word set, when the copies did not
+// land.  The caller's barrier before this call orders the previous tile's shared-memory
+// accesses before the copies that overwrite the same bytes.
+__device__ __forceinline__ bool stage_images(const PairDesc *pd, const FusedArgs &a, uint8_t *sref, uint8_t *stgt,
+                                             uint64_t *bar, int *flag, int x0, int y0, int iter, int tid)
+{
+    if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, (uint32_t)(a.box_h * (a.ref_box_w + a.tgt_box_w)));
+        tma_load_3d(sref, &pd->tmap_ref, 0, (x0 + a.ref_box_x) / 16, y0, bar);
+        tma_load_3d(stgt, &pd->tmap_tgt, 0, x0 / 16, y0, bar);
+        const long long t0 = clock64();
+        bool ok = false;
+        while (!(ok = mbar_try_wait(bar, (uint32_t)(iter & 1))) && clock64() - t0 < (1ll << 31)) {
+        }
+        *flag = ok ? 1 : 0;
+        if (!ok) atomicOr(a.status, 1);
+    }
+    __syncthreads();
+    return *flag != 0;
+}
+
 // Cost storage in shared memory: FP32, or FP16 / BF16 (rounded to nearest, widened back to
 // FP32 when loaded; aggregation always accumulates in FP32).  store4 writes the costs of
 // four consecutive disparities; load4 reads them back as two float2 pairs.
@@ -211,7 +267,7 @@ __device__ __forceinline__ void group_sync()
 }
 
 template <int RB, int DC, int RW, typename T, int TX, int TY, int NT = kThreads, int BAR = 0,
-          int KBAND = kBand>
+          int KBAND = kBand, bool SWZ = false>
 __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sref, const uint8_t *stgt,
                                            T *cbuf, int *vband, int2 *sstr, int2 *sstt,
                                            int x0, int y0, int d0, int tid)
@@ -358,10 +414,22 @@ __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sr
                     S.w += v[j + WS].w - v[j].w;
                 }
             }
-            T *co = cbuf + (size_t)yq * crow + 4 * dq;
+            if constexpr (SWZ) {
+                // 16 disparities per position as two 16-byte halves, the half index XORed with
+                // bit 2 of the column (the tensor-core aggregation's ldmatrix layout)
+                static_assert(DC == 16, "the swizzled layout holds 16 disparities per position");
+                T *co = cbuf + (size_t)yq * crow + 4 * (dq & 1);
 #pragma unroll
-            for (int j = 0; j < kSeg; ++j)
-                if (j < nout) CostStore<T>::store4(co + (size_t)(xs + j) * DC, out[j]);
+                for (int j = 0; j < kSeg; ++j) {
+                    const int x = xs + j;
+                    if (j < nout) CostStore<T>::store4(co + (size_t)x * DC + ((((dq >> 1) ^ (x >> 2)) & 1) << 3), out[j]);
+                }
+            } else {
+                T *co = cbuf + (size_t)yq * crow + 4 * dq;
+#pragma unroll
+                for (int j = 0; j < kSeg; ++j)
+                    if (j < nout) CostStore<T>::store4(co + (size_t)(xs + j) * DC, out[j]);
+            }
         }
         group_sync<BAR, NT>();
 #pragma unroll
@@ -394,30 +462,10 @@ k_fused(const __grid_constant__ PairDesc single, const PairDesc *__restrict__ pa
     int *flag = &s_flag;
     if (tid == 0) mbar_init(bar, 1);
 
-    // Tiles: a single pair walks its tiles in a fixed order (blockIdx.x, + gridDim.x, ...);
-    // a batch claims work-list items (pair, tile) with an atomic counter, heaviest first.
     for (int iter = 0;; ++iter) {
-        if (tid == 0) s_item = pairs ? atomicAdd(counter, 1) : (int)blockIdx.x + iter * (int)gridDim.x;
-        __syncthreads();
-        const int item = s_item;
-        if (item >= nitems) return;
-        int p = 0, tx, ty;
-        if (pairs) {
-            const int2 it = items[item];
-            p = it.x;
-            tx = it.y & 0xffff;
-            ty = it.y >> 16;
-        } else {
-            tx = item % single.ntx;
-            ty = item / single.ntx;
-        }
-        const PairDesc *pd = pairs ? pairs + p : &single;
-        {
-            const int *src = reinterpret_cast<const int *>(&pd->a);
-            int *dst = reinterpret_cast<int *>(&s_args);
-            for (int i = tid; i < (int)(sizeof(FusedArgs) / 4); i += kThreads) dst[i] = src[i];
-        }
-        __syncthreads();
+        int tx = 0, ty = 0;
+        const PairDesc *pd = claim_tile<kThreads>(single, pairs, items, nitems, counter, iter, s_args, s_item, tid, tx, ty);
+        if (!pd) return;
 
         const int CW = TX + 2 * a.m;
         const int RP = a.ref_box_w, TP = a.tgt_box_w;
@@ -433,26 +481,10 @@ k_fused(const __grid_constant__ PairDesc single, const PairDesc *__restrict__ pa
         (void)CW;
         const int x0 = tx * TX, y0 = ty * TY;
 
-        // ---- 1. stage the image tiles with TMA (the mbarrier completes once per tile)
+        // ---- 1. stage the image tiles with TMA
         for (int i = tid; i < KB * KB; i += kThreads) sK[i] = a.K[i];
         __syncthreads();
-        if (tid == 0) {
-            // the previous tile's ordinary shared-memory accesses (ordered by the barrier
-            // above) come before the tensor copies that overwrite the same bytes
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(bar, (uint32_t)(a.box_h * (RP + TP)));
-            tma_load_3d(sref, &pd->tmap_ref, 0, (x0 + a.ref_box_x) / 16, y0, bar);
-            tma_load_3d(stgt, &pd->tmap_tgt, 0, x0 / 16, y0, bar);
-            // bounded wait (about a second of clock cycles), then give up with a status flag
-            const long long t0 = clock64();
-            bool ok = false;
-            while (!(ok = mbar_try_wait(bar, (uint32_t)(iter & 1))) && clock64() - t0 < (1ll << 31)) {
-            }
-            *flag = ok ? 1 : 0;
-            if (!ok) atomicOr(a.status, 1);
-        }
-        __syncthreads();
-        if (*flag == 0) return;
+        if (!stage_images(pd, a, sref, stgt, bar, flag, x0, y0, iter, tid)) return;
 
     const int rw = a.rw;
     // scaled reference intensities of the cost positions (tile + bilateral halo); a
@@ -643,27 +675,9 @@ k_fused_ws(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
     if (tid == 0) mbar_init(bar, 1);
 
     for (int iter = 0;; ++iter) {
-        if (tid == 0) s_item = pairs ? atomicAdd(counter, 1) : (int)blockIdx.x + iter * (int)gridDim.x;
-        __syncthreads();
-        const int item = s_item;
-        if (item >= nitems) return;
-        int p = 0, tx, ty;
-        if (pairs) {
-            const int2 it = items[item];
-            p = it.x;
-            tx = it.y & 0xffff;
-            ty = it.y >> 16;
-        } else {
-            tx = item % single.ntx;
-            ty = item / single.ntx;
-        }
-        const PairDesc *pd = pairs ? pairs + p : &single;
-        {
-            const int *src = reinterpret_cast<const int *>(&pd->a);
-            int *dst = reinterpret_cast<int *>(&s_args);
-            for (int i = tid; i < (int)(sizeof(FusedArgs) / 4); i += kWsThreads) dst[i] = src[i];
-        }
-        __syncthreads();
+        int tx = 0, ty = 0;
+        const PairDesc *pd = claim_tile<kWsThreads>(single, pairs, items, nitems, counter, iter, s_args, s_item, tid, tx, ty);
+        if (!pd) return;
 
         const int RP = a.ref_box_w, TP = a.tgt_box_w;
         const SmemLayout L = smem_layout(RB, a.m, DC, RP, TP, a.box_h, (int)sizeof(T), TX, TY, 2, kWsBand);
@@ -678,23 +692,10 @@ k_fused_ws(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
         float *sK = reinterpret_cast<float *>(smem + L.sK);
         const int x0 = tx * TX, y0 = ty * TY;
 
-        // ---- 1. stage the image tiles with TMA (bounded wait, as in k_fused)
+        // ---- 1. stage the image tiles with TMA
         for (int i = tid; i < KB * KB; i += kWsThreads) sK[i] = a.K[i];
         __syncthreads();
-        if (tid == 0) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(bar, (uint32_t)(a.box_h * (RP + TP)));
-            tma_load_3d(sref, &pd->tmap_ref, 0, (x0 + a.ref_box_x) / 16, y0, bar);
-            tma_load_3d(stgt, &pd->tmap_tgt, 0, x0 / 16, y0, bar);
-            const long long t0 = clock64();
-            bool ok = false;
-            while (!(ok = mbar_try_wait(bar, (uint32_t)(iter & 1))) && clock64() - t0 < (1ll << 31)) {
-            }
-            *flag = ok ? 1 : 0;
-            if (!ok) atomicOr(a.status, 1);
-        }
-        __syncthreads();
-        if (*flag == 0) return;
+        if (!stage_images(pd, a, sref, stgt, bar, flag, x0, y0, iter, tid)) return;
 
         const int rw = a.rw;
         for (int i = tid; i < QH * QW; i += kWsThreads) {
@@ -883,6 +884,7 @@ FusedKernel pick_fused_f32_dc4(int rb);                // k_fused_f32_dc4.cu: WC
 FusedKernel pick_fused_f16(int rb, int dc, int wc);    // k_fused_f16.cu: WC = 2, DC = 12
 FusedKernel pick_fused_bf16(int rb, int dc, int wc);   // k_fused_bf16.cu: WC = 2, DC = 12
 FusedKernel pick_fused_ws(int rb, int dc);             // k_fused_ws.cu: warp-specialised, FP32, DC = 12
+FusedKernel pick_fused_tc(int cost_dtype, int rb);     // k_fused_tc_{f16,bf16}.cu: tensor-core aggregation, DC = 16
 FusedKernel pick_fused(int cost_dtype, int rb, int dc, int wc);
 // The descriptor of one context for one call (k_fused_f32.cu).
 void fill_pair_desc(const stereo_ctx *ctx, float *disp, int32_t *wta, uint8_t *valid, PairDesc &d);

@@ -2,7 +2,7 @@
 // side shared by all storage types (shared-memory sizing, kernel choice, launch).
 #include <string.h>
 
-#include "k_fused.cuh"
+#include "k_fused_tc.cuh"
 
 namespace sgb {
 
@@ -17,6 +17,7 @@ FusedKernel pick_fused_f32(int rb, int dc, int wc)
 FusedKernel pick_fused(int cost_dtype, int rb, int dc, int wc)
 {
     if (wc == kWsWC) return cost_dtype == STEREO_F32 && rb <= kWsMaxRB ? pick_fused_ws(rb, dc) : nullptr;
+    if (wc == kTcWC) return dc == kTcDC && rb <= kTcMaxRB ? pick_fused_tc(cost_dtype, rb) : nullptr;
     switch (cost_dtype) {
     case STEREO_F32: return pick_fused_f32(rb, dc, wc);
     case STEREO_F16: return pick_fused_f16(rb, dc, wc);
@@ -27,6 +28,7 @@ FusedKernel pick_fused(int cost_dtype, int rb, int dc, int wc)
 
 size_t fused_smem_bytes(const Geometry &g)
 {
+    if (g.wc == kTcWC) return tc_layout(g.rb, g.m, g.ref_box_w, g.tgt_box_w, g.box_h, g.esize).total;
     const bool ws = g.wc == kWsWC;
     return smem_layout(g.rb, g.m, g.dc, g.ref_box_w, g.tgt_box_w, g.box_h, g.esize, g.tx, g.ty, ws ? 2 : 1,
                        ws ? kWsBand : kBand)

@@ -207,11 +207,14 @@ int create_context(const stereo_params *p, int force_dc, int force_wc, stereo_ct
         free_ctx(c);
         return cuda_error(cudaErrorNoDevice, "stereo_create: no CUDA device");
     }
-    // disparities per chunk: 12 when the fused kernel's shared memory allows it, else 4
+    // FP16 / BF16 storage: the tensor-core form (16 disparities per chunk) where it applies;
+    // otherwise 12 disparities per chunk when the fused kernel's shared memory allows it, else 4
     const int smem_max = max_smem_optin() - kFusedStaticSmem;
-    const int wc = force_wc ? force_wc : kDefaultWC;
-    compute_geometry(*p, force_dc ? force_dc : 12, wc, c->g);
-    if (!force_dc && (int)c->g.smem_bytes > smem_max) compute_geometry(*p, 4, wc, c->g);
+    const bool tc = !force_wc && !force_dc && tc_supported(p->cost_dtype, p->bil, p->sigma1);
+    const int wc = force_wc ? force_wc : tc ? kTcWC : kDefaultWC;
+    compute_geometry(*p, force_dc ? force_dc : tc ? 16 : 12, wc, c->g);
+    if (tc && (int)c->g.smem_bytes > smem_max) compute_geometry(*p, 12, kDefaultWC, c->g);
+    if (!force_dc && c->g.wc != kTcWC && (int)c->g.smem_bytes > smem_max) compute_geometry(*p, 4, c->g.wc, c->g);
     if ((int)c->g.smem_bytes > smem_max) {
         free_ctx(c);
         return set_error(STEREO_ENOTSUP, "stereo_create: fused kernel needs %zu B of shared memory (max %d)",

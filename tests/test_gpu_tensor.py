@@ -1,0 +1,157 @@
+"""Tensor-core aggregation of the FP16 / BF16 storage forms (mma.sync over 4 x 4 pixel
+patches, FP32 accumulators), the default kernel of those forms for bil <= 13.
+
+Its costs and bilateral weights are rounded to the 16-bit type, so it is held to bounds
+derived from that rounding rather than the FP32 path's 1e-3 gap.  FP16: a cost moves by at
+most 2 * 2^-11 ~ 1e-3; a weight's exponent is formed from the exact integer intensity
+difference with three roundings of 2^-11 (about 1.5e-3 |exponent| absolute) and the power by
+ex2.approx on halves (relative error under 2^-9.9), so for the weighted-mean exponent of a
+window (a few units) a weight is off by at most about 0.4 %, and the normalised aggregated
+cost by at most 1e-3 + 0.004 * 2 ~ 9e-3.  The integer disparity must then equal the oracle's
+wherever the oracle's best and second-best normalised costs differ by more than twice that,
+2e-2.  BF16 (8-bit significands, four times the rounding, ex2 on bf16 pairs): 1e-1."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1904_06017_gb300 as sg
+import synth
+from gpu_helpers import dev_f32, dev_img, pitch_of
+
+pytestmark = pytest.mark.gpu
+
+GAP = {sg.STEREO_F16: 2e-2, sg.STEREO_BF16: 1e-1}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1904_06017_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def run_single(ref, tgtw, shift, D, win, bil, s0, s1, dtype, pitch_extra=0):
+    H, W = ref.shape
+    pitch = pitch_of(W, pitch_extra)
+    disp = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    wta = torch.empty((H, W), dtype=torch.int32, device="cuda")
+    valid = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+    with sg.Stereo(W, H, D, win=win, bil=bil, sigma0=s0, sigma1=s1, pitch=pitch, cost_dtype=dtype) as st:
+        st.cost_aggregate_wta(dev_img(ref, pitch), dev_img(tgtw, pitch), dev_f32(shift), disp, wta, valid)
+        st.check_device_status()
+    return disp.cpu().numpy(), wta.cpu().numpy(), valid.cpu().numpy()
+
+
+def check_vs_oracle(s, D, win, bil, s0, s1, dtype, min_sure):
+    tw = oracle.warp(s.tgt, s.shift)
+    disp, wta, valid = run_single(s.ref, tw, s.shift, D, win, bil, s0, s1, dtype, pitch_extra=16)
+    d_o, ds_o, eb, es = oracle.stereo(s.ref, tw, s.shift, D, win, bil, s0, s1)
+    sure = (es - eb) > GAP[dtype]
+    assert sure.mean() >= min_sure, "too few well-separated pixels (%.3f)" % sure.mean()
+    bad = int(np.count_nonzero(wta[sure] != ds_o[sure]))
+    err = np.abs(disp.astype(np.float64) - d_o)[sure]
+    print("\n%dx%d D=%d win=%d bil=%d dtype=%d: sure %.3f, WTA mismatches %d, sub-pixel error mean %.2e p99 %.2e"
+          % (s.width, s.height, D, win, bil, dtype, sure.mean(), bad, err.mean(), np.percentile(err, 99)))
+    assert bad == 0, "%d WTA mismatches on well-separated pixels" % bad
+    assert np.array_equal(valid, oracle.valid_mask(s.width, s.height, D, win, bil, s.shift))
+    return err
+
+
+@pytest.mark.parametrize("dtype", [sg.STEREO_F16, sg.STEREO_BF16])
+@pytest.mark.parametrize("W,H,D,win,bil", [(201, 75, 20, 5, 7), (65, 37, 12, 3, 1), (130, 70, 33, 3, 3),
+                                           (97, 41, 17, 5, 5), (150, 80, 48, 7, 9), (129, 52, 40, 9, 11),
+                                           (140, 90, 64, 9, 13), (70, 40, 24, 11, 15)])
+def test_tensor_form_matches_oracle(W, H, D, win, bil, dtype):
+    """Ragged tiles (widths and heights off the 64 x 36 grid), disparity ranges off the
+    16-disparity chunk, every bilateral radius the form takes; bil = 15 runs the FP16 / BF16
+    form without tensor cores."""
+    s = synth.make_scene(W, H, D, 3000 + W + D, roll=math.radians(3.0), coeffs=(4.0, 0.1, 1e-4),
+                         n_potholes=1, warp=True, win=win, bil=bil)
+    # the BF16 gap leaves fewer pixels to compare
+    min_sure = (0.5 if bil == 1 else 0.7) if dtype == sg.STEREO_F16 else 0.3
+    err = check_vs_oracle(s, D, win, bil, 3.0, 10.0, dtype, min_sure=min_sure)
+    assert err.mean() < (0.01 if dtype == sg.STEREO_F16 else 0.05)
+
+
+def test_tensor_form_paper_parameters():
+    """sigma0 = 1.5, sigma1 = 5.5, 11 x 11 neighbourhood (§4.4.1)."""
+    s = synth.make_scene(200, 90, 32, 778, roll=math.radians(2.0), n_potholes=2, warp=True, win=9, bil=11)
+    check_vs_oracle(s, 32, 9, 11, 1.5, 5.5, sg.STEREO_F16, min_sure=0.7)
+
+
+@pytest.mark.parametrize("dtype", [sg.STEREO_F16, sg.STEREO_BF16])
+def test_tensor_form_degenerate_inputs(dtype):
+    rng = np.random.default_rng(15)
+    img = synth.texture(rng, 70, 90)
+    shift = np.linspace(-4, 6, 70).astype(np.float32)
+    si = np.floor(shift.astype(np.float64) + 0.5)
+    # identical images: d* = 0 everywhere and the output is the integer row shift
+    disp, wta, _ = run_single(img, img, shift, 24, 7, 9, 3.0, 10.0, dtype)
+    assert np.all(wta == 0)
+    assert np.array_equal(disp, np.broadcast_to(si[:, None], disp.shape).astype(np.float32))
+    # one disparity
+    tgt = synth.texture(rng, 70, 90)
+    disp, wta, _ = run_single(img, tgt, shift, 1, 5, 5, 3.0, 10.0, dtype)
+    assert np.all(wta == 0)
+    # one pixel
+    one = np.array([[17]], np.uint8)
+    d1, w1, v1 = run_single(one, one, np.zeros(1, np.float32), 4, 3, 3, 3.0, 10.0, dtype)
+    assert w1[0, 0] == 0 and v1[0, 0] == 0
+
+
+SIZES = [(160, 120, 32), (211, 97, 16), (300, 180, 48), (96, 64, 24), (257, 140, 40)]
+
+
+def _batch(ss, dtype, wc, dc):
+    qs = []
+    for s, (W, H, D) in zip(ss, SIZES):
+        pitch = pitch_of(W)
+        qs.append(dict(ref=dev_img(s.ref, pitch), tgt=dev_img(s.tgt, pitch), shift=dev_f32(s.shift),
+                       tgt_warped=torch.zeros((H, pitch), dtype=torch.uint8, device="cuda"),
+                       disp=torch.zeros((H, W), dtype=torch.float32, device="cuda"),
+                       valid=torch.zeros((H, W), dtype=torch.uint8, device="cuda"),
+                       disp_out=torch.zeros((H, W), dtype=torch.float32, device="cuda"),
+                       res=torch.zeros(64, dtype=torch.uint8, device="cuda"), max_disp=D))
+    with sg.StereoBatch(qs, win=7, bil=9, sigma0=3.0, sigma1=10.0, cost_dtype=dtype, tile_wc=wc, tile_dc=dc) as b:
+        b.run()
+        torch.cuda.synchronize()
+        b.check_device_status()
+        cfg = b.config()
+    return [q["disp"].cpu().numpy() for q in qs], qs, cfg
+
+
+def test_tensor_form_batch_equals_single_and_tracks_simt_form():
+    ss = [synth.make_scene(W, H, D, 700 + i, roll=math.radians(2.0 * (i - 2)), coeffs=(6.0, 0.1, 0.0),
+                           n_potholes=1, warp=True, win=7, bil=9) for i, (W, H, D) in enumerate(SIZES)]
+    tc, qs, cfg = _batch(ss, sg.STEREO_F16, 16, 16)
+    assert cfg["tile_wc"] == 16 and cfg["tile_dc"] == 16
+    # the persistent batch launch gives what single-pair contexts give (same kernel, same tiles)
+    for (W, H, D), q, d in zip(SIZES, qs, tc):
+        tw = torch.empty_like(q["tgt"])
+        disp = torch.empty((H, W), dtype=torch.float32, device="cuda")
+        with sg.Stereo(W, H, D, win=7, bil=9, sigma0=3.0, sigma1=10.0, pitch=q["ref"].shape[1],
+                       cost_dtype=sg.STEREO_F16) as st:
+            st.warp_target(q["tgt"], q["shift"], tw)
+            st.cost_aggregate_wta(q["ref"], tw, q["shift"], disp)
+        assert np.array_equal(disp.cpu().numpy(), d)
+    # against the FP16 form without tensor cores (FP32 weights): the rounded disparities
+    # agree as closely as FP16 and FP32 storage do (a sub-pixel disparity near a half-integer
+    # rounds either way), and disparities more than half a pixel apart are rarer still
+    simt, _, cfg2 = _batch(ss, sg.STEREO_F16, 2, 12)
+    assert cfg2["tile_wc"] == 2
+    total = sum(a.size for a in tc)
+    diff = sum(int(np.count_nonzero(np.rint(a) != np.rint(b))) for a, b in zip(tc, simt))
+    far = sum(int(np.count_nonzero(np.abs(a - b) > 0.5)) for a, b in zip(tc, simt))
+    print("\nFP16 tensor-core vs FP16 SIMT aggregation: rounded disparities differ on %.2e, "
+          "by more than 0.5 px on %.2e of pixels" % (diff / total, far / total))
+    assert diff / total <= 5e-3
+    assert far / total <= 1e-3
+
+
+def test_tensor_form_rejects_unsupported_parameters():
+    ss = [synth.make_scene(W, H, D, 710 + i, warp=True, win=7, bil=9) for i, (W, H, D) in enumerate(SIZES)]
+    with pytest.raises(sg.StereoError):
+        _batch(ss, sg.STEREO_F32, 16, 16)
