@@ -25,6 +25,9 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+#include <utility>
+
 #include "internal.cuh"
 
 namespace sgb {
@@ -259,6 +262,18 @@ __host__ __device__ inline SmemLayout smem_layout(int rb, int m, int dc, int ref
 // band are in flight together instead of waiting behind stores they might alias.
 // Synchronisation of the NT threads that run cost_chunk: the whole CTA (BAR = 0) or a named
 // barrier BAR of NT threads (the producer warps of the warp-specialised form).
+// Calls f(std::integral_constant<int, i>) for i = 0 .. N-1 (compile-time loop).
+template <typename F, int... I>
+__device__ __forceinline__ void static_for_impl(F &&f, std::integer_sequence<int, I...>)
+{
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F &&f)
+{
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
 template <int BAR, int NT>
 __device__ __forceinline__ void group_sync()
 {
@@ -281,22 +296,40 @@ __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sr
     constexpr int NWV = (CW * DC + kThreads - 1) / kThreads;   // vertical walkers per thread
     constexpr int TSW = QW + DC - 1;                  // target-statistics columns of a chunk
     constexpr int NST = (kBand * (QW + TSW) + kThreads - 1) / kThreads;
-    const int RP = a.ref_box_w, TP = a.tgt_box_w;
+    // the reference box pitch and column offset follow from the radii and the tile width
+    // (the same formulas as the host's geometry); the target box depends on the search range
+    constexpr int MM = RW + RB;
+    constexpr int REFE = (MM + 15) / 16 * 16 - MM;
+    constexpr int RP = (REFE + TX + 2 * MM + 15) / 16 * 16;
+    const int TP = a.tgt_box_w;
     const size_t crow = (size_t)QW * DC;
+    // The products I_ref I_tar of a walker live in a register ring of NPH * kBand slots, product
+    // row j in slot j mod RING: the row entering a cost row's window is loaded once and read
+    // back from the ring when it leaves, w rows later.  Bands cycle through the NPH phases of
+    // the ring, so every slot index is a compile-time constant.
+    constexpr int NPH = (WS + 1 + kBand - 1) / kBand;
+    constexpr int RING = NPH * kBand;
+    static_assert(RING >= WS + 1, "the ring must hold a window and the row leaving it");
 
-    // walker start: the first w-1 product rows (row 0's window lacks only its last row)
-    int vacc[NWV];
+    // walker start: the first w-1 product rows (row 0's window lacks only its last row); the
+    // row before the first window (slot RING - 1) contributes 0
+    int vacc[NWV], ring[NWV][RING];
 #pragma unroll
     for (int k = 0; k < NWV; ++k) {
         vacc[k] = 0;
+#pragma unroll
+        for (int j = 0; j < RING; ++j) ring[k][j] = 0;
         const int w = tid + k * kThreads;
         if (w < CW * DC) {
             const int xp = w / DC, dd = w - xp * DC;
-            const uint8_t *rc = sref + a.ref_e + xp;
+            const uint8_t *rc = sref + REFE + xp;
             const uint8_t *tc = stgt + a.tgt_e + xp + (a.Dp - 1) - (d0 + dd);
             int s0 = 0;
 #pragma unroll
-            for (int i = 0; i < WS - 1; ++i) s0 += (int)rc[i * RP] * (int)tc[i * TP];
+            for (int i = 0; i < WS - 1; ++i) {
+                ring[k][i] = (int)rc[i * RP] * (int)tc[i * TP];
+                s0 += ring[k][i];
+            }
             vacc[k] = s0;
         }
     }
@@ -320,29 +353,29 @@ __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sr
     };
     int2 stv[NST];
     load_stats(stv, 0);
-    for (int yb0 = 0; yb0 < QH; yb0 += kBand) {
+    auto band = [&](auto phase, int yb0) {
+        constexpr int PH = decltype(phase)::value;
+        if (yb0 >= QH) return;
         const int nrows = min(kBand, QH - yb0);
         int2 stn[NST];
         load_stats(stn, yb0 + kBand);
-        // vertical pass: all product loads of every walker first ...
-        int pn[NWV][kBand], po[NWV][kBand];
+        // vertical pass: the product rows entering this band's windows, all loads first ...
+        int pn[NWV][kBand];
 #pragma unroll
         for (int k = 0; k < NWV; ++k) {
             const int w = tid + k * kThreads;
             const int xp = w / DC, dd = w - xp * DC;
             const bool on = w < CW * DC;
-            const uint8_t *rc = sref + a.ref_e + (on ? xp : 0);
+            const uint8_t *rc = sref + REFE + (on ? xp : 0);
             const uint8_t *tc = stgt + a.tgt_e + (on ? xp + (a.Dp - 1) - (d0 + dd) : 0);
 #pragma unroll
             for (int r = 0; r < kBand; ++r) {
-                const int yq = yb0 + r;
                 const bool live = on && r < nrows;
-                const int ya = live ? yq + WS - 1 : 0, yr = (live && yq > 0) ? yq - 1 : 0;
+                const int ya = live ? yb0 + r + WS - 1 : 0;
                 pn[k][r] = live ? (int)rc[ya * RP] * (int)tc[ya * TP] : 0;
-                po[k][r] = (live && yq > 0) ? (int)rc[yr * RP] * (int)tc[yr * TP] : 0;
             }
         }
-        // ... then the running sums and their stores
+        // ... then the running sums (the leaving row read back from the ring) and their stores
 #pragma unroll
         for (int k = 0; k < NWV; ++k) {
             const int w = tid + k * kThreads;
@@ -352,7 +385,9 @@ __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sr
 #pragma unroll
                 for (int r = 0; r < kBand; ++r) {
                     if (r < nrows) {
-                        acc += pn[k][r] - po[k][r];
+                        constexpr int base = PH * kBand;
+                        acc += pn[k][r] - ring[k][(base + r + RING - 1) % RING];
+                        ring[k][(base + r + WS - 1) % RING] = pn[k][r];
                         vo[r * CW * DC] = acc;
                     }
                 }
@@ -369,12 +404,25 @@ __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sr
             }
         }
         group_sync<BAR, NT>();
-        // horizontal pass: item = (band row, disparity quad, column segment), the segment
-        // index fastest so that neighbouring lanes hit distinct shared-memory banks
+        // horizontal pass: item = (band row, disparity quad, column segment).  Neighbouring
+        // lanes must read vband's 16-byte units in distinct bank groups: with an odd number of
+        // quads (stride kSeg * NQ units between segments, odd) the segment index runs fastest;
+        // with an even number it would repeat every two segments, so there the quad runs
+        // fastest (units dq + kSeg * NQ * seg: four quads, then the next segment 4 units on)
         const int nitems = nrows * NSEG * NQ;
         for (int it = tid; it < nitems; it += kThreads) {
-            const int seg = it % NSEG, rq = it / NSEG;
-            const int dq = rq % NQ, r = rq / NQ;
+            int seg, dq, r;
+            if constexpr (NQ % 2 == 0) {
+                dq = it % NQ;
+                const int rs = it / NQ;
+                seg = rs % NSEG;
+                r = rs / NSEG;
+            } else {
+                seg = it % NSEG;
+                const int rq = it / NSEG;
+                dq = rq % NQ;
+                r = rq / NQ;
+            }
             const int yq = yb0 + r;
             const int xs = seg * kSeg;
             const int nout = min(kSeg, QW - xs);
@@ -434,7 +482,9 @@ __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sr
         group_sync<BAR, NT>();
 #pragma unroll
         for (int k = 0; k < NST; ++k) stv[k] = stn[k];
-    }
+    };
+    for (int yb0 = 0; yb0 < QH; yb0 += RING)
+        static_for<NPH>([&](auto ph) { band(ph, yb0 + decltype(ph)::value * kBand); });
 }
 
 template <int RB, int DC, typename T, int WC>

@@ -38,8 +38,10 @@ constexpr float kTcOff = -20000.f;   // spatial exponent outside the window (wei
 //          per-warp E blocks of the aggregation ([warp][2][16][16] f32)
 //   sstr, sstt  window statistics of one band
 //   sI     [QH][kTcQWI] T  raw reference intensities of the cost positions
+//   skxy   [4 + 2 RB][32] uint4  spatial exponents Kx + Ky in the A-fragment layout, per window
+//          row and lane (four packed pairs: fragment registers 0..3)
 struct TcLayout {
-    size_t sref, stgt, cbuf, vband, sstr, sstt, sI, total;
+    size_t sref, stgt, cbuf, vband, sstr, sstt, sI, skxy, total;
 };
 
 __host__ __device__ inline TcLayout tc_layout(int rb, int m, int ref_box_w, int tgt_box_w, int box_h, int esize)
@@ -55,7 +57,8 @@ __host__ __device__ inline TcLayout tc_layout(int rb, int m, int ref_box_w, int 
     L.sstr = align_up(L.vband + (vb > eb ? vb : eb), 16);
     L.sstt = align_up(L.sstr + (size_t)kBand * QW * 8, 16);
     L.sI = align_up(L.sstt + (size_t)kBand * (QW + kTcDC - 1) * 8, 16);
-    L.total = align_up(L.sI + (size_t)QH * kTcQWI * esize, 128);
+    L.skxy = align_up(L.sI + (size_t)QH * kTcQWI * esize, 16);
+    L.total = align_up(L.skxy + (size_t)(4 + 2 * rb) * 32 * 16, 128);
     return L;
 }
 
@@ -158,6 +161,7 @@ k_fused_tc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
         int2 *sstr = reinterpret_cast<int2 *>(smem + L.sstr);
         int2 *sstt = reinterpret_cast<int2 *>(smem + L.sstt);
         T *sI = reinterpret_cast<T *>(smem + L.sI);
+        uint4 *skxy = reinterpret_cast<uint4 *>(smem + L.skxy);
         const int x0 = tx * TX, y0 = ty * TY;
 
         if (!stage_images(pd, a, sref, stgt, &s_bar, &s_flag, x0, y0, iter, tid)) return;
@@ -172,6 +176,19 @@ k_fused_tc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
             if (xq < QW && ix >= 0 && ix < a.W && iy >= 0 && iy < a.H)
                 v = (float)sref[(yq + rw) * RP + a.ref_e + xq + rw];
             sI[i] = X::from(v);
+        }
+        // spatial exponents in the fragment layout, per (window row r, lane): the four packed
+        // pairs of fragment registers 0..3 (pixel m0 / m1, columns 2 t4 + {0,1} / + {8,9})
+        for (int e = tid; e < NKS * 32; e += kThreads) {
+            const int r = e >> 5, ln = e & 31, lg = ln >> 2, lt = ln & 3, lmx = lg & 3, lmy = lg >> 2;
+            auto kx = [&](int dx) { return (dx >= 0 && dx <= 2 * RB) ? a.K[dx * KB + RB] : kTcOff; };
+            auto ky = [&](int dy) { return (dy >= 0 && dy <= 2 * RB) ? a.K[RB * KB + dy] : kTcOff; };
+            const float xl0 = kx(2 * lt - lmx), xl1 = kx(2 * lt + 1 - lmx);
+            const float xh0 = kx(2 * lt + 8 - lmx), xh1 = kx(2 * lt + 9 - lmx);
+            const float ya = ky(r - lmy), yb = ky(r - lmy - 2);
+            T2 q[4] = {X::pair(xl0 + ya, xl1 + ya), X::pair(xl0 + yb, xl1 + yb), X::pair(xh0 + ya, xh1 + ya),
+                       X::pair(xh0 + yb, xh1 + yb)};
+            skxy[e] = *reinterpret_cast<uint4 *>(q);
         }
         __syncthreads();
 
@@ -197,71 +214,60 @@ k_fused_tc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
             case 4: cost_chunk<RB, DC, 4, T, TX, TY, kThreads, 0, kBand, true>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
             default: cost_chunk<RB, DC, 5, T, TX, TY, kThreads, 0, kBand, true>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
             }
-            // ---- spatial exponents in the fragment layout: kxy[j][r] for fragment register j
-            // (pixel m0 or m1, columns 2 t4 + {0, 1} or 2 t4 + {8, 9}) and window row r
-            T2 kxy[4][NKS];
-            {
-                auto kx = [&](int dx) { return (dx >= 0 && dx <= 2 * RB) ? a.K[dx * KB + RB] : kTcOff; };
-                auto ky = [&](int dy) { return (dy >= 0 && dy <= 2 * RB) ? a.K[RB * KB + dy] : kTcOff; };
-                const float xl0 = kx(2 * t4 - mx), xl1 = kx(2 * t4 + 1 - mx);
-                const float xh0 = kx(2 * t4 + 8 - mx), xh1 = kx(2 * t4 + 9 - mx);
-#pragma unroll
-                for (int r = 0; r < NKS; ++r) {
-                    const float ya = ky(r - my0), yb = ky(r - my0 - 2);
-                    kxy[0][r] = X::pair(xl0 + ya, xl1 + ya);
-                    kxy[1][r] = X::pair(xl0 + yb, xl1 + yb);
-                    kxy[2][r] = X::pair(xh0 + ya, xh1 + ya);
-                    kxy[3][r] = X::pair(xh0 + yb, xh1 + yb);
-                }
-            }
             // ---- aggregation, two patches at a time
 #pragma unroll
             for (int pp = 0; pp < NPP; ++pp) {
+                // both patches of the pair advance together, k-step by k-step
+                T2 ipa[2], ipb[2];
+                uint32_t brow[2];
+                const T *irow[2];
+                float acc[2][2][4];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int P = warp * NPW + 2 * pp + h;
                     const int px0 = (P % NPX) * 4, py0 = (P / NPX) * 4;
-                    const T2 ipa = X::dup(sI[(py0 + RB + my0) * QWI + px0 + RB + mx]);
-                    const T2 ipb = X::dup(sI[(py0 + RB + my0 + 2) * QWI + px0 + RB + mx]);
-                    // ldmatrix row of this lane: matrix i = lane / 8 holds K rows 8 (i & 1) .. + 7
-                    // and disparity half i >> 1; K slots past the window read a clamped column
-                    // (their weights are 0)
+                    ipa[h] = X::dup(sI[(py0 + RB + my0) * QWI + px0 + RB + mx]);
+                    ipb[h] = X::dup(sI[(py0 + RB + my0 + 2) * QWI + px0 + RB + mx]);
                     const int kk = ((lane >> 3) & 1) * 8 + (lane & 7);
                     const int xq = min(px0 + kk, QW - 1);
                     const int hh = lane >> 4;
-                    const uint32_t brow =
-                        smem_addr(cbuf + ((size_t)py0 * QW + xq) * DC + ((((hh ^ (xq >> 2)) & 1)) << 3));
-                    const T *irow = sI + py0 * QWI + px0 + 2 * t4;
-                    float acc[2][4];
+                    brow[h] = smem_addr(cbuf + ((size_t)py0 * QW + xq) * DC + ((((hh ^ (xq >> 2)) & 1)) << 3));
+                    irow[h] = sI + py0 * QWI + px0 + 2 * t4;
 #pragma unroll
                     for (int nb = 0; nb < 2; ++nb)
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) acc[nb][k] = 0.f;
+                        for (int k = 0; k < 4; ++k) acc[h][nb][k] = 0.f;
+                }
 #pragma unroll
-                    for (int r = 0; r < NKS; ++r) {
-                        const T2 qlo = *reinterpret_cast<const T2 *>(irow + r * QWI);
-                        const T2 qhi = *reinterpret_cast<const T2 *>(irow + r * QWI + 8);
-                        const T2 dla = __hsub2(qlo, ipa), dlb = __hsub2(qlo, ipb);
-                        const T2 dha = __hsub2(qhi, ipa), dhb = __hsub2(qhi, ipb);
+                for (int r = 0; r < NKS; ++r) {
+                    const uint4 kq = skxy[r * 32 + lane];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const T2 qlo = *reinterpret_cast<const T2 *>(irow[h] + r * QWI);
+                        const T2 qhi = *reinterpret_cast<const T2 *>(irow[h] + r * QWI + 8);
+                        const T2 dla = __hsub2(qlo, ipa[h]), dlb = __hsub2(qlo, ipb[h]);
+                        const T2 dha = __hsub2(qhi, ipa[h]), dhb = __hsub2(qhi, ipb[h]);
                         uint32_t af[4];
-                        af[0] = X::ex2(__hfma2(__hmul2(dla, ns2), dla, kxy[0][r]));
-                        af[1] = X::ex2(__hfma2(__hmul2(dlb, ns2), dlb, kxy[1][r]));
-                        af[2] = X::ex2(__hfma2(__hmul2(dha, ns2), dha, kxy[2][r]));
-                        af[3] = X::ex2(__hfma2(__hmul2(dhb, ns2), dhb, kxy[3][r]));
+                        af[0] = X::ex2(__hfma2(__hmul2(dla, ns2), dla, *reinterpret_cast<const T2 *>(&kq.x)));
+                        af[1] = X::ex2(__hfma2(__hmul2(dlb, ns2), dlb, *reinterpret_cast<const T2 *>(&kq.y)));
+                        af[2] = X::ex2(__hfma2(__hmul2(dha, ns2), dha, *reinterpret_cast<const T2 *>(&kq.z)));
+                        af[3] = X::ex2(__hfma2(__hmul2(dhb, ns2), dhb, *reinterpret_cast<const T2 *>(&kq.w)));
                         uint32_t b0, b1, b2, b3;
-                        ldsm_x4_t(brow + (uint32_t)(r * QW * DC * (int)sizeof(T)), b0, b1, b2, b3);
-                        X::mma(acc[0], af, b0, b1);
-                        X::mma(acc[1], af, b2, b3);
+                        ldsm_x4_t(brow[h] + (uint32_t)(r * QW * DC * (int)sizeof(T)), b0, b1, b2, b3);
+                        X::mma(acc[h][0], af, b0, b1);
+                        X::mma(acc[h][1], af, b2, b3);
                     }
-                    // E block of the patch: acc[nb] = E[g][8 nb + 2 t4 + {0,1}], E[g + 8][...]
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
                     float *sb = scr + h * 256;
 #pragma unroll
                     for (int nb = 0; nb < 2; ++nb) {
                         const int u = 2 * nb + (t4 >> 1), o = 2 * (t4 & 1);
                         *reinterpret_cast<float2 *>(sb + g * 16 + ((u ^ tc_eswz(g)) << 2) + o) =
-                            make_float2(acc[nb][0], acc[nb][1]);
+                            make_float2(acc[h][nb][0], acc[h][nb][1]);
                         *reinterpret_cast<float2 *>(sb + (g + 8) * 16 + ((u ^ tc_eswz(g + 8)) << 2) + o) =
-                            make_float2(acc[nb][2], acc[nb][3]);
+                            make_float2(acc[h][nb][2], acc[h][nb][3]);
                     }
                 }
                 __syncwarp();
@@ -278,10 +284,11 @@ k_fused_tc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
                         e[4 * u + 2] = v.z;
                         e[4 * u + 3] = v.w;
                     }
+                    const int dn = min(DC, a.D - d0);
 #pragma unroll
                     for (int dd = 0; dd < DC; ++dd) {
                         const int d = d0 + dd;
-                        if (d >= a.D) break;
+                        if (dn < DC && dd >= dn) break;
                         const float v = e[dd];
                         if (v < best[pp]) {
                             best[pp] = v;
