@@ -359,41 +359,47 @@ __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sr
         const int nrows = min(kBand, QH - yb0);
         int2 stn[NST];
         load_stats(stn, yb0 + kBand);
-        // vertical pass: the product rows entering this band's windows, all loads first ...
-        int pn[NWV][kBand];
+        // vertical pass, in sub-bands of at most kSub rows: the product rows entering those
+        // rows' windows, all loads first, then the running sums (the leaving row read back
+        // from the ring) and their stores
+        constexpr int kSub = kBand < 6 ? kBand : 6;
+        static_assert(kBand % kSub == 0, "a band is a whole number of sub-bands");
+        static_for<kBand / kSub>([&](auto sub) {
+            constexpr int R0 = decltype(sub)::value * kSub;
+            int pn[NWV][kSub];
 #pragma unroll
-        for (int k = 0; k < NWV; ++k) {
-            const int w = tid + k * kThreads;
-            const int xp = w / DC, dd = w - xp * DC;
-            const bool on = w < CW * DC;
-            const uint8_t *rc = sref + REFE + (on ? xp : 0);
-            const uint8_t *tc = stgt + a.tgt_e + (on ? xp + (a.Dp - 1) - (d0 + dd) : 0);
+            for (int k = 0; k < NWV; ++k) {
+                const int w = tid + k * kThreads;
+                const int xp = w / DC, dd = w - xp * DC;
+                const bool on = w < CW * DC;
+                const uint8_t *rc = sref + REFE + (on ? xp : 0);
+                const uint8_t *tc = stgt + a.tgt_e + (on ? xp + (a.Dp - 1) - (d0 + dd) : 0);
 #pragma unroll
-            for (int r = 0; r < kBand; ++r) {
-                const bool live = on && r < nrows;
-                const int ya = live ? yb0 + r + WS - 1 : 0;
-                pn[k][r] = live ? (int)rc[ya * RP] * (int)tc[ya * TP] : 0;
-            }
-        }
-        // ... then the running sums (the leaving row read back from the ring) and their stores
-#pragma unroll
-        for (int k = 0; k < NWV; ++k) {
-            const int w = tid + k * kThreads;
-            if (w < CW * DC) {
-                int *vo = vband + w;            // [r][xp][dd] with xp * DC + dd = w
-                int acc = vacc[k];
-#pragma unroll
-                for (int r = 0; r < kBand; ++r) {
-                    if (r < nrows) {
-                        constexpr int base = PH * kBand;
-                        acc += pn[k][r] - ring[k][(base + r + RING - 1) % RING];
-                        ring[k][(base + r + WS - 1) % RING] = pn[k][r];
-                        vo[r * CW * DC] = acc;
-                    }
+                for (int r = 0; r < kSub; ++r) {
+                    const bool live = on && R0 + r < nrows;
+                    const int ya = live ? yb0 + R0 + r + WS - 1 : 0;
+                    pn[k][r] = live ? (int)rc[ya * RP] * (int)tc[ya * TP] : 0;
                 }
-                vacc[k] = acc;
             }
-        }
+#pragma unroll
+            for (int k = 0; k < NWV; ++k) {
+                const int w = tid + k * kThreads;
+                if (w < CW * DC) {
+                    int *vo = vband + w;            // [r][xp][dd] with xp * DC + dd = w
+                    int acc = vacc[k];
+#pragma unroll
+                    for (int r = 0; r < kSub; ++r) {
+                        if (R0 + r < nrows) {
+                            constexpr int base = PH * kBand + R0;
+                            acc += pn[k][r] - ring[k][(base + r + RING - 1) % RING];
+                            ring[k][(base + r + WS - 1) % RING] = pn[k][r];
+                            vo[(R0 + r) * CW * DC] = acc;
+                        }
+                    }
+                    vacc[k] = acc;
+                }
+            }
+        });
 #pragma unroll
         for (int k = 0; k < NST; ++k) {
             const int e = tid + k * kThreads;

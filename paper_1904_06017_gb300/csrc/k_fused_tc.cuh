@@ -30,13 +30,15 @@ constexpr int kTcQWI = 76;     // row length of the staged intensities (>= TX + 
 constexpr float kTcFar = 30000.f;    // intensity of positions outside the image: its squared
                                      // difference drives the exponent to -inf (weight 0)
 constexpr float kTcOff = -20000.f;   // spatial exponent outside the window (weight 0)
+// cost rows per band of the cost phase: 12 where shared memory allows (half the barriers of 6)
+__host__ __device__ constexpr int tc_band(int rb) { return rb <= 5 ? 12 : 6; }
 
 // Shared memory of the tensor-core form (offsets from the 128-byte aligned dynamic base):
 //   sref, stgt  image tiles (TMA), as in k_fused
 //   cbuf   [QH][QW][16] T  the chunk's costs, 16-byte halves swizzled by bit 2 of the column
-//   vband  [kBand][CW][16] i32 vertical window sums of the cost phase; the same bytes hold the
+//   vband  [band][CW][16] i32 vertical window sums of the cost phase; the same bytes hold the
 //          per-warp E blocks of the aggregation ([warp][2][16][16] f32)
-//   sstr, sstt  window statistics of one band
+//   sstr, sstt  window statistics of one band (band = tc_band(RB) cost rows)
 //   sI     [QH][kTcQWI] T  raw reference intensities of the cost positions
 //   skxy   [4 + 2 RB][32] uint4  spatial exponents Kx + Ky in the A-fragment layout, per window
 //          row and lane (four packed pairs: fragment registers 0..3)
@@ -49,14 +51,15 @@ __host__ __device__ inline TcLayout tc_layout(int rb, int m, int ref_box_w, int 
     TcLayout L;
     const int TX = tile_x(kTcWC), TY = tile_y(kTcWC);
     const int QH = TY + 2 * rb, QW = TX + 2 * rb, CW = TX + 2 * m;
-    const size_t vb = (size_t)kBand * CW * kTcDC * 4, eb = (size_t)kWarps * 2 * 256 * 4;
+    const int band = tc_band(rb);
+    const size_t vb = (size_t)band * CW * kTcDC * 4, eb = (size_t)kWarps * 2 * 256 * 4;
     L.sref = 0;
     L.stgt = align_up((size_t)box_h * ref_box_w, 128);
     L.cbuf = align_up(L.stgt + (size_t)box_h * tgt_box_w, 128);
     L.vband = align_up(L.cbuf + (size_t)QH * QW * kTcDC * esize, 128);
     L.sstr = align_up(L.vband + (vb > eb ? vb : eb), 16);
-    L.sstt = align_up(L.sstr + (size_t)kBand * QW * 8, 16);
-    L.sI = align_up(L.sstt + (size_t)kBand * (QW + kTcDC - 1) * 8, 16);
+    L.sstt = align_up(L.sstr + (size_t)band * QW * 8, 16);
+    L.sI = align_up(L.sstt + (size_t)band * (QW + kTcDC - 1) * 8, 16);
     L.skxy = align_up(L.sI + (size_t)QH * kTcQWI * esize, 16);
     L.total = align_up(L.skxy + (size_t)(4 + 2 * rb) * 32 * 16, 128);
     return L;
@@ -208,11 +211,11 @@ k_fused_tc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
         for (int d0 = 0; d0 < a.D; d0 += DC) {
             // ---- costs of the chunk, 16 disparities, swizzled storage
             switch (rw) {
-            case 1: cost_chunk<RB, DC, 1, T, TX, TY, kThreads, 0, kBand, true>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
-            case 2: cost_chunk<RB, DC, 2, T, TX, TY, kThreads, 0, kBand, true>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
-            case 3: cost_chunk<RB, DC, 3, T, TX, TY, kThreads, 0, kBand, true>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
-            case 4: cost_chunk<RB, DC, 4, T, TX, TY, kThreads, 0, kBand, true>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
-            default: cost_chunk<RB, DC, 5, T, TX, TY, kThreads, 0, kBand, true>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
+            case 1: cost_chunk<RB, DC, 1, T, TX, TY, kThreads, 0, tc_band(RB), true>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
+            case 2: cost_chunk<RB, DC, 2, T, TX, TY, kThreads, 0, tc_band(RB), true>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
+            case 3: cost_chunk<RB, DC, 3, T, TX, TY, kThreads, 0, tc_band(RB), true>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
+            case 4: cost_chunk<RB, DC, 4, T, TX, TY, kThreads, 0, tc_band(RB), true>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
+            default: cost_chunk<RB, DC, 5, T, TX, TY, kThreads, 0, tc_band(RB), true>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
             }
             // ---- aggregation, two patches at a time
 #pragma unroll
