@@ -511,6 +511,12 @@ def run_ours(args):
             "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal, derived)",
             "fp32_probe_tflops": {"scalar_fma": probe_s / 1e3, "packed_f32x2_fma": probe_p / 1e3},
             "fused_gpix_disp_per_s": W * H * D / (fused_avg_ms * 1e-3) / 1e9}
+    # the FP16 / BF16 forms do the same algorithmic work: their share of the same FP32 roofline
+    for v in variants.values():
+        v["fused_frac_of_fp32_roofline"] = agg_flops / (v["fused_ms"] * 1e-3) / 1e12 / peak
+    variants["kernel"] = {"f32": "k_fused (FP32 weights and accumulators)",
+                          "f16": "k_fused_tc (tensor-core aggregation, FP32 accumulators)",
+                          "bf16": "k_fused_tc (tensor-core aggregation, FP32 accumulators)"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,

@@ -76,6 +76,28 @@ def test_tensor_form_matches_oracle(W, H, D, win, bil, dtype):
     assert err.mean() < (0.01 if dtype == sg.STEREO_F16 else 0.05)
 
 
+@pytest.mark.parametrize("W,H,D,win,bil", [(300, 40, 256, 11, 11), (300, 40, 256, 9, 13)])
+def test_tensor_form_maximum_disparity(W, H, D, win, bil):
+    """D = 256: the widest target strip; with w = k = 11 the form's shared memory is at its
+    largest (about 228 KB)."""
+    s = synth.make_scene(W, H, D, 4242 + bil, roll=0.0, coeffs=(100.0, 0.0, 0.0), n_potholes=0,
+                         warp=False, win=win, bil=bil)
+    tw = s.tgt
+    disp, wta, valid = run_single(s.ref, tw, s.shift, D, win, bil, 3.0, 10.0, sg.STEREO_F16)
+    d_o, ds_o, eb, es = oracle.stereo(s.ref, tw, s.shift, D, win, bil, 3.0, 10.0)
+    sure = (es - eb) > GAP[sg.STEREO_F16]
+    assert sure.mean() >= 0.2
+    assert int(np.count_nonzero(wta[sure] != ds_o[sure])) == 0
+    assert np.array_equal(valid, oracle.valid_mask(W, H, D, win, bil, s.shift))
+
+
+def test_tensor_form_range_kernel_limit():
+    """sigma1 > 150 leaves the FP16 form on FP32 weights (the packed -s^2 would be subnormal);
+    the result must still meet the FP16 bar."""
+    s = synth.make_scene(120, 60, 24, 4300, roll=math.radians(2.0), warp=True, win=7, bil=9)
+    check_vs_oracle(s, 24, 7, 9, 3.0, 200.0, sg.STEREO_F16, min_sure=0.5)
+
+
 def test_tensor_form_paper_parameters():
     """sigma0 = 1.5, sigma1 = 5.5, 11 x 11 neighbourhood (§4.4.1)."""
     s = synth.make_scene(200, 90, 32, 778, roll=math.radians(2.0), n_potholes=2, warp=True, win=9, bil=11)
