@@ -11,13 +11,15 @@
 //       of the patch's window (4 + 2 RB rows), K = the 4 + 2 RB cost columns that row spans,
 //       padded to 16 with zero weights;
 //   A = the bilateral weights, generated in registers in the fragment layout:
-//       w = 2^(Kx(dx) + Ky(dy) - s^2 (I_q - I_p)^2), zero outside the k x k window; the
-//       exponent in packed 16-bit arithmetic on the exact integer intensity difference, the
-//       power by ex2.approx on the packed pair;
+//       w = 2^(Kx(dx) + Ky(dy) - s^2 (I_q - I_p)^2), zero outside the k x k window; Kx + Ky
+//       per (window row, lane) from a shared table, the rest of the exponent in packed 16-bit
+//       arithmetic on the exact integer intensity difference, the power by ex2.approx on the
+//       packed pair;
 //   B = the costs, gathered by ldmatrix.trans: every lane names one 16-byte row (a cost
 //       position, 8 disparities), so a k-step's 16 positions are read in one instruction.
-// The accumulated block E (16 pixels x 16 disparities) goes through a per-warp scratch to the
-// running WTA, one pixel per lane, disparities in increasing order (lowest d wins ties).
+// The two patches of a pair advance k-step by k-step together.  Their accumulated blocks E
+// (16 pixels x 16 disparities each) go through a per-warp scratch to the running WTA, one
+// pixel per lane, disparities in increasing order (lowest d wins ties).
 // The weights are rounded to the storage type and the weight normaliser is skipped, as in
 // k_fused (a positive per-pixel factor changes neither the argmin nor the parabola step).
 #pragma once
