@@ -228,7 +228,8 @@ struct SmemLayout {
     size_t sref, stgt, cbuf, cbuf1, vband, sstr, sstt, sI, sK, bar, flag, total;
 };
 
-// nbuf cost buffers (2 for the warp-specialised form), band cost rows per window-sum band.
+// nbuf cost buffers (2 for the warp-specialised form), band cost rows per window-sum band;
+// band = 0 for the tensor-core cost phase, which needs no vband / sstr / sstt.
 __host__ __device__ inline SmemLayout smem_layout(int rb, int m, int dc, int ref_box_w,
                                                   int tgt_box_w, int box_h, int esize, int tx, int ty,
                                                   int nbuf = 1, int band = kBand)
@@ -243,7 +244,7 @@ __host__ __device__ inline SmemLayout smem_layout(int rb, int m, int dc, int ref
     L.vband = L.cbuf + (size_t)nbuf * cbytes;
     L.sstr = align_up(L.vband + (size_t)band * CW * dc * 4, 16);
     L.sstt = align_up(L.sstr + (size_t)band * QW * 8, 16);
-    L.sI = align_up(L.sstt + (size_t)band * (QW + dc - 1) * 8, 16);
+    L.sI = align_up(L.sstt + (size_t)band * (QW + dc - 1) * 8, 16);   // band 0: vband = sstr = sstt = sI
     L.sK = align_up(L.sI + (size_t)QH * QW * 4, 16);
     L.bar = align_up(L.sK + (size_t)KB * KB * 4, 8);
     L.flag = L.bar + 8;
@@ -493,6 +494,201 @@ __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sr
         static_for<NPH>([&](auto ph) { band(ph, yb0 + decltype(ph)::value * kBand); });
 }
 
+// ------------------------------------------------------------- tensor-core cost phase
+// mma.sync m16n8k16, FP16 operands, FP32 accumulators: d (4 floats) += A (16 x 16) B (16 x 8).
+__device__ __forceinline__ void mma_f16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// The bytes p[0], p[1] as a packed FP16 pair (p[0] in the low half), exactly: each byte b goes
+// into a half whose high byte is 0x64 (the FP16 number 1024 + b), then 1024 is subtracted.
+__device__ __forceinline__ uint32_t u8pair_h2(const uint8_t *p)
+{
+    const uint32_t w = __byte_perm((uint32_t)p[0], (uint32_t)p[1], 0x5410) | 0x64006400u;
+    const __half2 h = __hsub2(*reinterpret_cast<const __half2 *>(&w), __half2half2(__ushort_as_half(0x6400)));
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+template <typename T> __device__ __forceinline__ T cost_from_float(float c);
+template <> __device__ __forceinline__ float cost_from_float<float>(float c) { return c; }
+template <> __device__ __forceinline__ __half cost_from_float<__half>(float c) { return __float2half_rn(c); }
+template <> __device__ __forceinline__ __nv_bfloat16 cost_from_float<__nv_bfloat16>(float c)
+{
+    return __float2bfloat16_rn(c);
+}
+
+// The costs of one chunk of DC <= 16 disparities at the tile plus its bilateral halo (QH x QW
+// positions), eq. (c), with the cross term S = sum_block I_ref(q) I_tar(q - d) on the tensor
+// cores.  The 8-bit intensities are exact in FP16, every product and every window sum is an
+// integer below 2^24, so FP32 accumulation keeps S exact.  One warp owns a block of 8 cost
+// columns and walks down its rows; for every staged row the products of that row are one mma
+// per 16 product columns:
+//   A[m][kk] = I_tar(row, x0b + kk - (d0 + m))   (16 disparities x 16 product columns, Toeplitz)
+//   B[kk][n] = I_ref(row, x0b + kk) if 0 <= kk - n <= 2 r_w, else 0   (banded)
+// and the accumulator carries S(row window) from row to row: the row entering the window is
+// added, the row leaving it is subtracted (B negated).  A row's fragments are built once and
+// kept in a register ring of w slots until the row leaves (for w = 11, where two k-steps make
+// the ring too large, the leaving row is rebuilt).  Then c = 1 - (n S - S_ref S_tar) r_ref r_tar:
+// every lane holds one window-statistics entry per row (lanes 0..7 the reference at the
+// block's 8 columns, lanes 8.. the target at x - d), loaded from device memory a window of rows
+// ahead, and the formula gathers them with warp shuffles.  Warps work independently; the
+// caller synchronises before reading cbuf.  With SWZ the 16 disparities of a position are
+// stored as two 16-byte halves swizzled by bit 2 of the column.
+template <int RB, int DC, int RW, typename T, int TX, int TY, int NT = kThreads, bool SWZ = false>
+__device__ __forceinline__ void cost_chunk_mma(const FusedArgs &a, const uint8_t *sref, const uint8_t *stgt,
+                                               T *cbuf, int x0, int y0, int d0, int tid)
+{
+    static_assert(DC <= 16, "one block of 16 disparities per mma");
+    static_assert(!SWZ || DC == 16, "the swizzled layout holds 16 disparities per position");
+    constexpr int QH = TY + 2 * RB, QW = TX + 2 * RB;
+    constexpr int NR = 2 * RW + 1;                     // rows of a window
+    constexpr int NXB = (QW + 7) / 8;                  // column blocks (one warp each at a time)
+    constexpr int NKC = (8 + 2 * RW + 15) / 16;        // k-steps per row: 8 + 2 r_w product columns
+    constexpr bool RING = NKC == 1;                    // keep every row's fragments until it leaves
+    constexpr int MM = RW + RB;
+    constexpr int REFE = (MM + 15) / 16 * 16 - MM;
+    constexpr int RP = (REFE + TX + 2 * MM + 15) / 16 * 16;
+    const int TP = a.tgt_box_w;
+    const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
+    const size_t crow = (size_t)QW * DC;
+    // B masks per k-step: K slot kk is in the window of output column g iff 0 <= kk - g <= 2 r_w
+    uint32_t mlo[NKC], mhi[NKC];
+#pragma unroll
+    for (int kc = 0; kc < NKC; ++kc) {
+        auto hm = [&](int kk) { return (kk - g >= 0 && kk - g <= 2 * RW) ? 0xffffu : 0u; };
+        const int k0 = 16 * kc + 2 * t4;
+        mlo[kc] = hm(k0) | (hm(k0 + 1) << 16);
+        mhi[kc] = hm(k0 + 8) | (hm(k0 + 9) << 16);
+    }
+    // shuffle sources of this lane's four outputs (x = xa + (k & 1), d = d0 + g + 8 (k >> 1)):
+    // the reference entry of x, the target entry of x - d
+    int src_r[2], src_t[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int xr = 2 * t4 + (k & 1), dd = g + (k >> 1) * 8;
+        if (k < 2) src_r[k] = xr;
+        src_t[k] = min(max(8 + xr - dd + DC - 1, 0), 31);
+    }
+    for (int xb = warp; xb < NXB; xb += NT / 32) {
+        const int x0b = xb * 8;
+        const uint8_t *rb = sref + REFE + x0b + 2 * t4;
+        const uint8_t *tb = stgt + a.tgt_e + (a.Dp - 1) - d0 + x0b + 2 * t4 - g;
+        // this lane's statistics entry at row 0; columns past the tile are clamped (their costs
+        // are not stored)
+        const int2 *esrc = nullptr;
+        {
+            const size_t prow0 = (size_t)(y0 - RB + a.pad_top) * a.pad_w + x0 - RB + a.pad_left;
+            if (lane < 8) esrc = a.ref_stats + prow0 + min(x0b + lane, QW - 1);
+            else if (lane < DC + 15) esrc = a.tgt_stats + prow0 + min(x0b - d0 - DC + 1 + (lane - 8), QW - 1 - d0);
+        }
+        auto ld_stats = [&](int yq) { return (esrc && yq < QH) ? __ldg(esrc + (size_t)yq * a.pad_w) : make_int2(0, 0); };
+
+        // fragments of one staged row: a0 = A[g][2t4 + {0,1}], a1 = A[g + 8][...], a2 =
+        // A[g][2t4 + 8 + {0,1}] (a3 = A[g + 8][2t4 + 8 + {0,1}] = a0, Toeplitz); b0 = B[2t4 +
+        // {0,1}][g], b1 = B[2t4 + 8 + {0,1}][g]
+        auto build = [&](int row, uint32_t (&f)[NKC][5]) {
+            const uint8_t *rr = rb + row * RP;
+            const uint8_t *tr = tb + row * TP;
+#pragma unroll
+            for (int kc = 0; kc < NKC; ++kc) {
+                f[kc][0] = u8pair_h2(tr + 16 * kc);
+                f[kc][1] = u8pair_h2(tr + 16 * kc - 8);
+                f[kc][2] = u8pair_h2(tr + 16 * kc + 8);
+                f[kc][3] = u8pair_h2(rr + 16 * kc) & mlo[kc];
+                f[kc][4] = u8pair_h2(rr + 16 * kc + 8) & mhi[kc];
+            }
+        };
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        auto apply = [&](const uint32_t (&f)[NKC][5], uint32_t sign) {   // sign 0x80008000 negates B
+#pragma unroll
+            for (int kc = 0; kc < NKC; ++kc) {
+                const uint32_t af[4] = {f[kc][0], f[kc][1], f[kc][2], f[kc][0]};
+                mma_f16_16816(acc, af, f[kc][3] ^ sign, f[kc][4] ^ sign);
+            }
+        };
+        // c of this lane's four outputs at cost row yq from S = acc and the row's entries e
+        auto emit = [&](int yq, int2 e) {
+            const int xa = x0b + 2 * t4;
+            int2 rs[2], ts[4];
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+                rs[k] = make_int2(__shfl_sync(0xffffffffu, e.x, src_r[k]), __shfl_sync(0xffffffffu, e.y, src_r[k]));
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                ts[k] = make_int2(__shfl_sync(0xffffffffu, e.x, src_t[k]), __shfl_sync(0xffffffffu, e.y, src_t[k]));
+            T *co = cbuf + (size_t)yq * crow;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int x = xa + (k & 1), dd = g + (k >> 1) * 8;
+                if (x < QW && dd < DC) {
+                    const int S = __float_as_int(acc[k] + 8388608.f) - 0x4B000000;   // exact, 0 <= S < 2^23
+                    const int2 r = rs[k & 1], t = ts[k];
+                    const float c = fmaf(-(float)(a.n * S - r.x * t.x), __int_as_float(r.y) * __int_as_float(t.y), 1.0f);
+                    size_t o = (size_t)x * DC + dd;
+                    if constexpr (SWZ) o = (size_t)x * DC + ((((dd >> 3) ^ (x >> 2)) & 1) << 3) + (dd & 7);
+                    co[o] = cost_from_float<T>(c);
+                }
+            }
+        };
+
+        int2 scur[NR], snxt[NR];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) scur[j] = ld_stats(j);
+        if constexpr (RING) {
+            // row r lives in slot r % NR from the step it enters (r - 2 r_w) to the step it leaves (r)
+            uint32_t fr[NR][NKC][5];
+#pragma unroll
+            for (int i = 0; i < NR - 1; ++i) {
+                build(i, fr[i]);
+                apply(fr[i], 0u);
+            }
+            for (int yq0 = 0; yq0 < QH; yq0 += NR) {
+#pragma unroll
+                for (int j = 0; j < NR; ++j) snxt[j] = ld_stats(yq0 + NR + j);
+#pragma unroll
+                for (int j = 0; j < NR; ++j) {
+                    const int yq = yq0 + j;
+                    if (yq < QH) {
+                        build(yq + 2 * RW, fr[(j + 2 * RW) % NR]);
+                        apply(fr[(j + 2 * RW) % NR], 0u);
+                        emit(yq, scur[j]);
+                        apply(fr[j], 0x80008000u);   // the leaving row yq (slot yq % NR = j)
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < NR; ++j) scur[j] = snxt[j];
+            }
+        } else {
+            uint32_t fn[NKC][5], fo[NKC][5];
+            for (int i = 0; i < NR - 1; ++i) {
+                build(i, fn);
+                apply(fn, 0u);
+            }
+            for (int yq0 = 0; yq0 < QH; yq0 += NR) {
+#pragma unroll
+                for (int j = 0; j < NR; ++j) snxt[j] = ld_stats(yq0 + NR + j);
+#pragma unroll
+                for (int j = 0; j < NR; ++j) {
+                    const int yq = yq0 + j;
+                    if (yq < QH) {
+                        build(yq + 2 * RW, fn);
+                        apply(fn, 0u);
+                        emit(yq, scur[j]);
+                        build(yq, fo);
+                        apply(fo, 0x80008000u);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < NR; ++j) scur[j] = snxt[j];
+            }
+        }
+    }
+}
+
 template <int RB, int DC, typename T, int WC>
 __global__ void __launch_bounds__(kThreads, 1)
 k_fused(const __grid_constant__ PairDesc single, const PairDesc *__restrict__ pairs,
@@ -525,13 +721,10 @@ k_fused(const __grid_constant__ PairDesc single, const PairDesc *__restrict__ pa
 
         const int CW = TX + 2 * a.m;
         const int RP = a.ref_box_w, TP = a.tgt_box_w;
-        const SmemLayout L = smem_layout(RB, a.m, DC, RP, TP, a.box_h, (int)sizeof(T), TX, TY);
+        const SmemLayout L = smem_layout(RB, a.m, DC, RP, TP, a.box_h, (int)sizeof(T), TX, TY, 1, 0);
         uint8_t *sref = smem + L.sref;
         uint8_t *stgt = smem + L.stgt;
         T *cbuf = reinterpret_cast<T *>(smem + L.cbuf);
-        int *vband = reinterpret_cast<int *>(smem + L.vband);
-        int2 *sstr = reinterpret_cast<int2 *>(smem + L.sstr);
-        int2 *sstt = reinterpret_cast<int2 *>(smem + L.sstt);
         float *sI = reinterpret_cast<float *>(smem + L.sI);
         float *sK = reinterpret_cast<float *>(smem + L.sK);
         (void)CW;
@@ -574,12 +767,13 @@ k_fused(const __grid_constant__ PairDesc single, const PairDesc *__restrict__ pa
     for (int d0 = 0; d0 < a.D; d0 += DC) {
         // ---- 2a/2b. costs of the chunk (block radius dispatched to a compile-time value)
         switch (rw) {
-        case 1: cost_chunk<RB, DC, 1, T, TX, TY>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
-        case 2: cost_chunk<RB, DC, 2, T, TX, TY>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
-        case 3: cost_chunk<RB, DC, 3, T, TX, TY>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
-        case 4: cost_chunk<RB, DC, 4, T, TX, TY>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
-        default: cost_chunk<RB, DC, 5, T, TX, TY>(a, sref, stgt, cbuf, vband, sstr, sstt, x0, y0, d0, tid); break;
+        case 1: cost_chunk_mma<RB, DC, 1, T, TX, TY>(a, sref, stgt, cbuf, x0, y0, d0, tid); break;
+        case 2: cost_chunk_mma<RB, DC, 2, T, TX, TY>(a, sref, stgt, cbuf, x0, y0, d0, tid); break;
+        case 3: cost_chunk_mma<RB, DC, 3, T, TX, TY>(a, sref, stgt, cbuf, x0, y0, d0, tid); break;
+        case 4: cost_chunk_mma<RB, DC, 4, T, TX, TY>(a, sref, stgt, cbuf, x0, y0, d0, tid); break;
+        default: cost_chunk_mma<RB, DC, 5, T, TX, TY>(a, sref, stgt, cbuf, x0, y0, d0, tid); break;
         }
+        __syncthreads();
         // ---- 2c. bilateral aggregation of the chunk: each thread kPY pixels x DC d
         float2 acc[kPY][DC / 2];
 #pragma unroll

@@ -29,9 +29,11 @@ FusedKernel pick_fused(int cost_dtype, int rb, int dc, int wc)
 size_t fused_smem_bytes(const Geometry &g)
 {
     if (g.wc == kTcWC) return tc_layout(g.rb, g.m, g.ref_box_w, g.tgt_box_w, g.box_h, g.esize).total;
+    // the warp-specialised form keeps the two-pass cost phase (vband, staged statistics); the
+    // others compute costs on the tensor cores and need neither
     const bool ws = g.wc == kWsWC;
     return smem_layout(g.rb, g.m, g.dc, g.ref_box_w, g.tgt_box_w, g.box_h, g.esize, g.tx, g.ty, ws ? 2 : 1,
-                       ws ? kWsBand : kBand)
+                       ws ? kWsBand : 0)
         .total;
 }
 
