@@ -130,6 +130,20 @@ int stereo_cost_aggregate_wta(stereo_ctx *ctx, const uint8_t *ref_dev,
                               float *disp_dev, int32_t *wta_dev, uint8_t *valid_dev,
                               stereo_stream_t stream);
 
+/* stereo_cost_aggregate_wta with one more optional output: best2_dev float [H][W][2]
+ * receives the normalised aggregated cost of eq. (fbs) at d* and the smallest one over
+ * d != d* (their gap is a confidence of the match; with FP16 / BF16 cost storage both
+ * carry that storage's rounding).  NULL skips it (the call is then stereo_cost_aggregate_wta).
+ * The output comes from separate kernel instantiations, built for FP32 storage with the
+ * default chunk of 12 disparities and for the tensor-core FP16 / BF16 form; a context on
+ * another form (FP16 / BF16 with bil = 15 or sigma1 > 150, or FP32 windows large enough to
+ * fall back to 4-disparity chunks) returns STEREO_ENOTSUP for a non-NULL best2_dev.
+ * Errors: as stereo_cost_aggregate_wta, and STEREO_ENOTSUP as above. */
+int stereo_cost_aggregate_wta_ex(stereo_ctx *ctx, const uint8_t *ref_dev,
+                                 const uint8_t *tgt_warped_dev, const float *shift_dev,
+                                 float *disp_dev, int32_t *wta_dev, uint8_t *valid_dev,
+                                 float *best2_dev, stereo_stream_t stream);
+
 /* §3.3: disparity transformation of a disparity map.
  * Fits over the pixels with mask_dev != 0 (all pixels when mask_dev is NULL) and a
  * finite disparity: 10 FP64 moments on the device, then the roll search of

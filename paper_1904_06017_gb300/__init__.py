@@ -19,7 +19,7 @@ import os
 __all__ = [
     "StereoError", "stereo_params", "stereo_dt_result", "load_library", "library_path",
     "stereo_params_default", "stereo_create", "stereo_destroy", "stereo_row_shift_affine",
-    "stereo_warp_target", "stereo_cost_aggregate_wta", "stereo_disparity_transform",
+    "stereo_warp_target", "stereo_cost_aggregate_wta", "stereo_cost_aggregate_wta_ex", "stereo_disparity_transform",
     "stereo_cost_volume", "stereo_aggregate_volume", "stereo_wta_volume",
     "stereo_check_device_status", "stereo_profile_enable", "stereo_profile_read",
     "stereo_fp32_peak_probe", "stereo_last_error", "stereo_version", "Stereo",
@@ -105,6 +105,7 @@ def load_library():
         "stereo_row_shift_affine": [I32, D, D, D, P],
         "stereo_warp_target": [P, P, P, P, P],
         "stereo_cost_aggregate_wta": [P, P, P, P, P, P, P, P],
+        "stereo_cost_aggregate_wta_ex": [P, P, P, P, P, P, P, P, P],
         "stereo_disparity_transform": [P, P, P, D, F, P, P, P],
         "stereo_cost_volume": [P, P, P, P, P],
         "stereo_aggregate_volume": [P, P, P, P, P],
@@ -221,6 +222,13 @@ def stereo_cost_aggregate_wta(ctx, ref, tgt_warped, shift, disp, wta=None, valid
                                                     _stream(stream)))
 
 
+def stereo_cost_aggregate_wta_ex(ctx, ref, tgt_warped, shift, disp, wta=None, valid=None, best2=None,
+                                 stream=None):
+    _check(load_library().stereo_cost_aggregate_wta_ex(ctx, _ptr(ref), _ptr(tgt_warped), _ptr(shift),
+                                                       _ptr(disp), _ptr(wta), _ptr(valid), _ptr(best2),
+                                                       _stream(stream)))
+
+
 def stereo_disparity_transform(ctx, disp, mask, psi_init, delta_t, disp_out, res=None, stream=None):
     """res: None -> the call synchronises and returns a stereo_dt_result (host);
     a CUDA uint8 tensor of >= 48 bytes -> the result stays on the device (asynchronous)."""
@@ -325,8 +333,12 @@ class Stereo:
     def warp_target(self, tgt, shift, out, stream=None):
         stereo_warp_target(self.ctx, tgt, shift, out, stream)
 
-    def cost_aggregate_wta(self, ref, tgt_warped, shift, disp, wta=None, valid=None, stream=None):
-        stereo_cost_aggregate_wta(self.ctx, ref, tgt_warped, shift, disp, wta, valid, stream)
+    def cost_aggregate_wta(self, ref, tgt_warped, shift, disp, wta=None, valid=None, stream=None, best2=None):
+        """best2 (float32 [H, W, 2], optional): normalised E at d* and the smallest E over d != d*."""
+        if best2 is None:
+            stereo_cost_aggregate_wta(self.ctx, ref, tgt_warped, shift, disp, wta, valid, stream)
+        else:
+            stereo_cost_aggregate_wta_ex(self.ctx, ref, tgt_warped, shift, disp, wta, valid, best2, stream)
 
     def disparity_transform(self, disp, mask, psi_init, delta_t, out, res=None, stream=None):
         return stereo_disparity_transform(self.ctx, disp, mask, psi_init, delta_t, out, res, stream)

@@ -105,7 +105,7 @@ int launch_warp(stereo_ctx *ctx, const uint8_t *tgt, const float *shift, uint8_t
 int launch_prep(stereo_ctx *ctx, const uint8_t *ref, const uint8_t *tgtw, cudaStream_t s);
 int launch_row_tables(stereo_ctx *ctx, const float *shift, cudaStream_t s);
 int launch_fused(stereo_ctx *ctx, const float *shift, float *disp, int32_t *wta, uint8_t *valid,
-                 cudaStream_t s);
+                 cudaStream_t s, float *best2 = nullptr);
 size_t fused_smem_bytes(const Geometry &g);
 int fused_configure(stereo_ctx *ctx);
 int compute_geometry(const stereo_params &p, int dc, int wc, Geometry &g);

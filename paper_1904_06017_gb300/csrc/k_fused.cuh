@@ -39,6 +39,7 @@ struct FusedArgs {
     float *disp;
     int32_t *wta;
     uint8_t *valid;
+    float *best2;       // optional [H][W][2]: normalised E at d* and the smallest E over d != d*
     int *status;
     int W, H, D, Dp, rw, m, n;
     int pad_left, pad_top, pad_w;
@@ -689,7 +690,9 @@ __device__ __forceinline__ void cost_chunk_mma(const FusedArgs &a, const uint8_t
     }
 }
 
-template <int RB, int DC, typename T, int WC>
+// B2: also track the smallest E over d != d* and write best2 (a separate instantiation, so
+// that the kernels without the optional output carry none of its registers or operations).
+template <int RB, int DC, typename T, int WC, bool B2 = false>
 __global__ void __launch_bounds__(kThreads, 1)
 k_fused(const __grid_constant__ PairDesc single, const PairDesc *__restrict__ pairs,
         const int2 *__restrict__ items, int nitems, int *__restrict__ counter)
@@ -754,12 +757,13 @@ k_fused(const __grid_constant__ PairDesc single, const PairDesc *__restrict__ pa
 #pragma unroll
     for (int i = 0; i < kPY; ++i) Ip[i] = sI[(yt0 + i + RB) * QW + xt + RB];
 
-    float best[kPY], bm1[kPY], bp1[kPY], prev[kPY];
+    float best[kPY], bm1[kPY], bp1[kPY], prev[kPY], sec[B2 ? kPY : 1];
     int bd[kPY];
 #pragma unroll
     for (int i = 0; i < kPY; ++i) {
         best[i] = __int_as_float(0x7f800000);
         bm1[i] = bp1[i] = prev[i] = best[i];
+        if constexpr (B2) sec[i] = best[i];
         bd[i] = -1;
     }
 
@@ -847,11 +851,13 @@ k_fused(const __grid_constant__ PairDesc single, const PairDesc *__restrict__ pa
                 if (d >= a.D) break;
                 const float v = (dd & 1) ? acc[i][dd >> 1].y : acc[i][dd >> 1].x;
                 if (v < best[i]) {
+                    if constexpr (B2) sec[i] = best[i];
                     best[i] = v;
                     bd[i] = d;
                     bm1[i] = prev[i];
-                } else if (d == bd[i] + 1) {
-                    bp1[i] = v;
+                } else {
+                    if constexpr (B2) sec[i] = fminf(sec[i], v);
+                    if (d == bd[i] + 1) bp1[i] = v;
                 }
                 prev[i] = v;
             }
@@ -876,6 +882,17 @@ k_fused(const __grid_constant__ PairDesc single, const PairDesc *__restrict__ pa
             const int ulo = a.m + a.D - 1 + max(0, rt.y);
             const int uhi = a.W - 1 - a.m + min(0, rt.z);
             a.valid[o] = (uint8_t)(v >= a.m && v <= a.H - 1 - a.m && u >= ulo && u <= uhi);
+        }
+        if constexpr (B2) {
+            // the skipped normaliser sum_q w(p,q) (out-of-image q carry weight 0)
+            float ws = 0.f;
+            for (int dx = 0; dx < KB; ++dx)
+                for (int dy = 0; dy < KB; ++dy) {
+                    const float t = sI[(yt0 + i + dy) * QW + xt + dx] - Ip[i];
+                    ws += ex2_approx(fmaf(-t, t, sK[dx * KB + dy]));
+                }
+            a.best2[2 * o] = best[i] / ws;
+            a.best2[2 * o + 1] = sec[i] / ws;
         }
     }
     }  // tile loop
@@ -1109,18 +1126,18 @@ k_fused_ws(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
 
 typedef void (*FusedKernel)(const PairDesc, const PairDesc *, const int2 *, int, int *);
 
-template <int DC, typename T, int WC>
+template <int DC, typename T, int WC, bool B2 = false>
 FusedKernel pick_rb(int rb)
 {
     switch (rb) {
-    case 0: return k_fused<0, DC, T, WC>;
-    case 1: return k_fused<1, DC, T, WC>;
-    case 2: return k_fused<2, DC, T, WC>;
-    case 3: return k_fused<3, DC, T, WC>;
-    case 4: return k_fused<4, DC, T, WC>;
-    case 5: return k_fused<5, DC, T, WC>;
-    case 6: return k_fused<6, DC, T, WC>;
-    case 7: return k_fused<7, DC, T, WC>;
+    case 0: return k_fused<0, DC, T, WC, B2>;
+    case 1: return k_fused<1, DC, T, WC, B2>;
+    case 2: return k_fused<2, DC, T, WC, B2>;
+    case 3: return k_fused<3, DC, T, WC, B2>;
+    case 4: return k_fused<4, DC, T, WC, B2>;
+    case 5: return k_fused<5, DC, T, WC, B2>;
+    case 6: return k_fused<6, DC, T, WC, B2>;
+    case 7: return k_fused<7, DC, T, WC, B2>;
     }
     return nullptr;
 }
@@ -1136,7 +1153,13 @@ FusedKernel pick_fused_bf16(int rb, int dc, int wc);   // k_fused_bf16.cu: WC = 
 FusedKernel pick_fused_ws(int rb, int dc);             // k_fused_ws.cu: warp-specialised, FP32, DC = 12
 FusedKernel pick_fused_tc(int cost_dtype, int rb);     // k_fused_tc_{f16,bf16}.cu: tensor-core aggregation, DC = 16
 FusedKernel pick_fused(int cost_dtype, int rb, int dc, int wc);
+// The instantiation with the best2 output (FP32 storage at WC = 2 with DC = 12, and the
+// tensor-core form); nullptr where there is none.  k_fused_b2_f32.cu, k_fused_tc_{f16,bf16}_b2.cu.
+FusedKernel pick_fused_b2(int cost_dtype, int rb, int dc, int wc);
+FusedKernel pick_fused_f32_b2(int rb, int dc);
+FusedKernel pick_fused_tc_b2(int cost_dtype, int rb);
 // The descriptor of one context for one call (k_fused_f32.cu).
-void fill_pair_desc(const stereo_ctx *ctx, float *disp, int32_t *wta, uint8_t *valid, PairDesc &d);
+void fill_pair_desc(const stereo_ctx *ctx, float *disp, int32_t *wta, uint8_t *valid, PairDesc &d,
+                    float *best2 = nullptr);
 
 }  // namespace sgb

@@ -48,13 +48,19 @@ int fused_configure(stereo_ctx *ctx)
     if (!k)
         return set_error(STEREO_ENOTSUP, "no fused kernel for bil=%d dc=%d cost_dtype=%d", ctx->p.bil, ctx->g.dc,
                          ctx->p.cost_dtype);
-    return cuda_error(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)ctx->g.smem_bytes),
-                      "cudaFuncSetAttribute(fused)");
+    int rc = cuda_error(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)ctx->g.smem_bytes),
+                        "cudaFuncSetAttribute(fused)");
+    FusedKernel k2 = pick_fused_b2(ctx->p.cost_dtype, ctx->g.rb, ctx->g.dc, ctx->g.wc);
+    if (!rc && k2)
+        rc = cuda_error(cudaFuncSetAttribute((const void *)k2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)ctx->g.smem_bytes),
+                        "cudaFuncSetAttribute(fused, best2)");
+    return rc;
 }
 
 // The pair descriptor of a context for one call (outputs are per call).
-void fill_pair_desc(const stereo_ctx *ctx, float *disp, int32_t *wta, uint8_t *valid, PairDesc &d)
+void fill_pair_desc(const stereo_ctx *ctx, float *disp, int32_t *wta, uint8_t *valid, PairDesc &d, float *best2)
 {
     const Geometry &g = ctx->g;
     FusedArgs &a = d.a;
@@ -69,6 +75,7 @@ void fill_pair_desc(const stereo_ctx *ctx, float *disp, int32_t *wta, uint8_t *v
     a.disp = disp;
     a.wta = wta;
     a.valid = valid;
+    a.best2 = best2;
     a.status = ctx->status_dev;
     a.W = g.W;
     a.H = g.H;
@@ -92,14 +99,18 @@ void fill_pair_desc(const stereo_ctx *ctx, float *disp, int32_t *wta, uint8_t *v
 }
 
 int launch_fused(stereo_ctx *ctx, const float *shift, float *disp, int32_t *wta, uint8_t *valid,
-                 cudaStream_t s)
+                 cudaStream_t s, float *best2)
 {
     (void)shift;   // the integer shifts come from the row table built by k_row_tables
     const Geometry &g = ctx->g;
-    FusedKernel k = pick(ctx);
-    if (!k) return set_error(STEREO_ENOTSUP, "no fused kernel for bil=%d", ctx->p.bil);
+    FusedKernel k = best2 ? pick_fused_b2(ctx->p.cost_dtype, g.rb, g.dc, g.wc) : pick(ctx);
+    if (!k)
+        return set_error(STEREO_ENOTSUP, best2 ? "the best2 output needs FP32 storage with 12 disparities per chunk or "
+                                                 "the tensor-core form (FP16 / BF16 with bil <= 13)"
+                                               : "no fused kernel for bil=%d",
+                         ctx->p.bil);
     PairDesc d;
-    fill_pair_desc(ctx, disp, wta, valid, d);
+    fill_pair_desc(ctx, disp, wta, valid, d, best2);
     const int ntiles = g.ntx * g.nty;
     k<<<ntiles, fused_threads(g.wc), g.smem_bytes, s>>>(d, nullptr, nullptr, ntiles, nullptr);
     return cuda_error(cudaGetLastError(), "k_fused launch");

@@ -122,7 +122,8 @@ __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t &r0, uint32_t 
 // LDS.128 reads are free of bank conflicts.
 __device__ __forceinline__ int tc_eswz(int m) { return (m & 2) | ((m >> 2) & 1); }
 
-template <int RB, typename T>
+// B2: also track the smallest E over d != d* and write best2 (a separate instantiation).
+template <int RB, typename T, bool B2 = false>
 __global__ void __launch_bounds__(kThreads, 1)
 k_fused_tc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__ pairs,
            const int2 *__restrict__ items, int nitems, int *__restrict__ counter)
@@ -198,12 +199,13 @@ k_fused_tc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
         __syncthreads();
 
         // WTA state of the lane's pixel in each patch pair: patch 2 pp + (lane >> 4), pixel lane & 15
-        float best[NPP], bm1[NPP], bp1[NPP], prev[NPP];
+        float best[NPP], bm1[NPP], bp1[NPP], prev[NPP], sec[B2 ? NPP : 1];
         int bd[NPP];
 #pragma unroll
         for (int i = 0; i < NPP; ++i) {
             best[i] = __int_as_float(0x7f800000);
             bm1[i] = bp1[i] = prev[i] = best[i];
+            if constexpr (B2) sec[i] = best[i];
             bd[i] = -1;
         }
         const float s2 = a.iscale * a.iscale;
@@ -296,11 +298,13 @@ k_fused_tc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
                         if (dn < DC && dd >= dn) break;
                         const float v = e[dd];
                         if (v < best[pp]) {
+                            if constexpr (B2) sec[pp] = best[pp];
                             best[pp] = v;
                             bd[pp] = d;
                             bm1[pp] = prev[pp];
-                        } else if (d == bd[pp] + 1) {
-                            bp1[pp] = v;
+                        } else {
+                            if constexpr (B2) sec[pp] = fminf(sec[pp], v);
+                            if (d == bd[pp] + 1) bp1[pp] = v;
                         }
                         prev[pp] = v;
                     }
@@ -330,21 +334,34 @@ k_fused_tc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
                 const int uhi = a.W - 1 - a.m + min(0, rt.z);
                 a.valid[o] = (uint8_t)(v >= a.m && v <= a.H - 1 - a.m && u >= ulo && u <= uhi);
             }
+            if constexpr (B2) {
+                // the skipped normaliser sum_q w(p,q), in FP32 from the same exponent
+                const int px = (P % NPX) * 4 + (m & 3), py = (P / NPX) * 4 + (m >> 2);
+                const float ip = (float)sI[(py + RB) * QWI + px + RB];
+                float ws = 0.f;
+                for (int dx = 0; dx < KB; ++dx)
+                    for (int dy = 0; dy < KB; ++dy) {
+                        const float t = ((float)sI[(py + dy) * QWI + px + dx] - ip) * a.iscale;
+                        ws += ex2_approx(fmaf(-t, t, a.K[dx * KB + dy]));
+                    }
+                a.best2[2 * o] = best[pp] / ws;
+                a.best2[2 * o + 1] = sec[pp] / ws;
+            }
         }
     }  // tile loop
 }
 
-template <typename T>
+template <typename T, bool B2 = false>
 FusedKernel pick_tc_rb(int rb)
 {
     switch (rb) {
-    case 0: return k_fused_tc<0, T>;
-    case 1: return k_fused_tc<1, T>;
-    case 2: return k_fused_tc<2, T>;
-    case 3: return k_fused_tc<3, T>;
-    case 4: return k_fused_tc<4, T>;
-    case 5: return k_fused_tc<5, T>;
-    case 6: return k_fused_tc<6, T>;
+    case 0: return k_fused_tc<0, T, B2>;
+    case 1: return k_fused_tc<1, T, B2>;
+    case 2: return k_fused_tc<2, T, B2>;
+    case 3: return k_fused_tc<3, T, B2>;
+    case 4: return k_fused_tc<4, T, B2>;
+    case 5: return k_fused_tc<5, T, B2>;
+    case 6: return k_fused_tc<6, T, B2>;
     }
     return nullptr;
 }

@@ -295,6 +295,13 @@ int stereo_cost_aggregate_wta(stereo_ctx *ctx, const uint8_t *ref, const uint8_t
                               const float *shift, float *disp, int32_t *wta, uint8_t *valid,
                               stereo_stream_t stream)
 {
+    return stereo_cost_aggregate_wta_ex(ctx, ref, tgtw, shift, disp, wta, valid, nullptr, stream);
+}
+
+int stereo_cost_aggregate_wta_ex(stereo_ctx *ctx, const uint8_t *ref, const uint8_t *tgtw,
+                                 const float *shift, float *disp, int32_t *wta, uint8_t *valid,
+                                 float *best2, stereo_stream_t stream)
+{
     if (!ctx || !ref || !tgtw || !shift || !disp)
         return set_error(STEREO_EINVAL, "stereo_cost_aggregate_wta: null pointer");
     cudaStream_t s = (cudaStream_t)stream;
@@ -306,7 +313,7 @@ int stereo_cost_aggregate_wta(stereo_ctx *ctx, const uint8_t *ref, const uint8_t
         slot = ctx->prof_n++;
         cudaEventRecord(ctx->prof_ev[2 * slot], s);
     }
-    rc = launch_fused(ctx, shift, disp, wta, valid, s);
+    rc = launch_fused(ctx, shift, disp, wta, valid, s, best2);
     if (slot >= 0) cudaEventRecord(ctx->prof_ev[2 * slot + 1], s);
     return rc;
 }

@@ -46,6 +46,19 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, n)
 
 
+def test_every_declared_function_has_a_ctypes_signature(lib):
+    """Without argtypes ctypes would pass device pointers as 32-bit ints: every entry point the
+    headers declare must have its argument and return types set by the binding."""
+    untyped = [n for n in declared_functions() if getattr(lib, n).argtypes is None]
+    assert not untyped, untyped
+    # each signature has as many arguments as the header's declaration
+    for h in HEADERS:
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for name, params in re.findall(r"\b(stereo_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src):
+            n = 0 if params.strip() in ("", "void") else params.count(",") + 1
+            assert len(getattr(lib, name).argtypes) == n, (name, n)
+
+
 def test_struct_layout_matches_header(tmp_path):
     prog = tmp_path / "layout.c"
     prog.write_text(r'''
@@ -105,6 +118,7 @@ def test_null_pointers_rejected(lib):
     assert rc == sg.STEREO_EINVAL
     assert lib.stereo_warp_target(None, None, None, None, None) == sg.STEREO_EINVAL
     assert lib.stereo_cost_aggregate_wta(None, None, None, None, None, None, None, None) == sg.STEREO_EINVAL
+    assert lib.stereo_cost_aggregate_wta_ex(None, None, None, None, None, None, None, None, None) == sg.STEREO_EINVAL
     assert lib.stereo_disparity_transform(None, None, None, 0.0, 0.0, None, None, None) == sg.STEREO_EINVAL
     assert lib.stereo_destroy(None) == sg.STEREO_OK
     assert lib.stereo_lr_check(None, None, None, None, None, None, None, 1.0, None) == sg.STEREO_EINVAL

@@ -115,6 +115,29 @@ def test_fused_ragged_sizes_and_windows(W, H, D, win, bil):
     _fused_vs_oracle(s, D, win, bil, 3.0, 10.0, pitch_extra=32, min_sure=0.6 if bil == 1 else 0.8)
 
 
+@pytest.mark.parametrize("W,H,D,win,bil", [(130, 70, 24, 9, 11), (97, 41, 17, 5, 5), (70, 33, 1, 3, 3)])
+def test_fused_best_and_second_cost(W, H, D, win, bil):
+    """The optional best2 output: the normalised E of eq. (fbs) at d* and the smallest E over
+    d != d*, against the oracle's, at every pixel (within the cost tolerance); with D = 1
+    there is no second disparity and both sides give +inf."""
+    s = synth.make_scene(W, H, D, 2000 + W + D, roll=math.radians(2.0), coeffs=(4.0, 0.1, 1e-4),
+                         n_potholes=1, warp=True, win=win, bil=bil)
+    tw = oracle.warp(s.tgt, s.shift)
+    pitch = pitch_of(W)
+    disp = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    best2 = torch.empty((H, W, 2), dtype=torch.float32, device="cuda")
+    with sg.Stereo(W, H, D, win=win, bil=bil, sigma0=3.0, sigma1=10.0, pitch=pitch) as st:
+        st.cost_aggregate_wta(dev_img(s.ref, pitch), dev_img(tw, pitch), dev_f32(s.shift), disp, best2=best2)
+        st.check_device_status()
+    b2 = best2.cpu().numpy().astype(np.float64)
+    _, _, eb, es = oracle.stereo(s.ref, tw, s.shift, D, win, bil, 3.0, 10.0)
+    check_rel(b2[..., 0], eb)
+    fin = np.isfinite(es)
+    assert np.array_equal(np.isfinite(b2[..., 1]), fin)
+    if fin.any():
+        check_rel(b2[..., 1][fin], es[fin])
+
+
 def test_fused_single_disparity_and_tiny_image():
     rng = np.random.default_rng(5)
     ref = synth.texture(rng, 20, 30)

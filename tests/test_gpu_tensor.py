@@ -98,6 +98,40 @@ def test_tensor_form_range_kernel_limit():
     check_vs_oracle(s, 24, 7, 9, 3.0, 200.0, sg.STEREO_F16, min_sure=0.5)
 
 
+@pytest.mark.parametrize("dtype", [sg.STEREO_F16, sg.STEREO_BF16])
+def test_tensor_form_best_and_second_cost(dtype):
+    """The optional best2 output (normalised E at d* and the smallest E over d != d*) against
+    the oracle: within the bound on the normalised E that sets the form's WTA gap (half the gap)."""
+    W, H, D = 150, 80, 48
+    s = synth.make_scene(W, H, D, 5150, roll=math.radians(2.0), warp=True, win=7, bil=9)
+    tw = oracle.warp(s.tgt, s.shift)
+    pitch = pitch_of(W)
+    disp = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    best2 = torch.empty((H, W, 2), dtype=torch.float32, device="cuda")
+    with sg.Stereo(W, H, D, win=7, bil=9, sigma0=3.0, sigma1=10.0, pitch=pitch, cost_dtype=dtype) as st:
+        st.cost_aggregate_wta(dev_img(s.ref, pitch), dev_img(tw, pitch), dev_f32(s.shift), disp, best2=best2)
+        st.check_device_status()
+    b2 = best2.cpu().numpy().astype(np.float64)
+    _, _, eb, es = oracle.stereo(s.ref, tw, s.shift, D, 7, 9, 3.0, 10.0)
+    err = max(np.abs(b2[..., 0] - eb).max(), np.abs(b2[..., 1] - es).max())
+    print("\nbest2 dtype=%d: max |E - oracle| = %.2e" % (dtype, err))
+    assert err <= GAP[dtype] / 2
+
+
+def test_best2_needs_a_form_that_carries_it():
+    """bil = 15 leaves FP16 storage on the SIMT form, which has no best2 instantiation."""
+    W, H, D = 70, 40, 24
+    s = synth.make_scene(W, H, D, 5170, warp=True, win=7, bil=15)
+    pitch = pitch_of(W)
+    disp = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    best2 = torch.empty((H, W, 2), dtype=torch.float32, device="cuda")
+    with sg.Stereo(W, H, D, win=7, bil=15, sigma0=3.0, sigma1=10.0, pitch=pitch, cost_dtype=sg.STEREO_F16) as st:
+        with pytest.raises(sg.StereoError):
+            st.cost_aggregate_wta(dev_img(s.ref, pitch), dev_img(s.tgt, pitch), dev_f32(s.shift), disp, best2=best2)
+        st.cost_aggregate_wta(dev_img(s.ref, pitch), dev_img(s.tgt, pitch), dev_f32(s.shift), disp)
+        st.check_device_status()
+
+
 def test_tensor_form_paper_parameters():
     """sigma0 = 1.5, sigma1 = 5.5, 11 x 11 neighbourhood (§4.4.1)."""
     s = synth.make_scene(200, 90, 32, 778, roll=math.radians(2.0), n_potholes=2, warp=True, win=9, bil=11)
