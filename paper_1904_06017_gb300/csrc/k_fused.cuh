@@ -1,24 +1,26 @@
 // k_fused.cuh -- fused matching cost (eq. c) + bilateral aggregation (eq. omega_s,
 // eq. fbs) + winner-take-all + parabola sub-pixel step (eq. subpixel), §3.2.
 //
-// One CTA (8 warps) owns a 64 x 32 block of output pixels and all D disparities:
+// One CTA of kWarps warps owns a block of output pixels (64 x 36 by default) and all D
+// disparities; the kernel is persistent over tiles (and, for a batch, over pairs):
 //  1. TMA (cp.async.bulk.tensor) stages the reference tile and the warped-target strip
 //     (replicate-padded copies) into shared memory, one box each, on an mbarrier.
-//  2. For each chunk of DC disparities, band by band of kBand cost rows:
-//     a. vertical running sums of the products I_ref(x,y) I_tar(x-d,y) over the w rows
-//        of the block (exact integers), one walker per (product column, d), the sum
-//        carried in a register from band to band;
-//     b. horizontal sums of those over the w columns (the full w x w correlation sum of
-//        eq. c), four disparities per work item, then
-//        c = 1 - (n S - S_ref S_tar) / sqrt(A_ref A_tar): the chunk's costs at the tile
-//        plus its bilateral halo live only in shared memory, never in device memory;
-//     c. aggregation: each thread owns a column of kPY pixels x DC disparities in
-//        registers; for every neighbour row it loads the DC costs once (LDS.128, the
-//        next row prefetched) and applies them to every pixel whose window holds it,
-//        with the weight w = 2^(K[dx][dy] - (s I_q - s I_p)^2) (eq. omega0 x eq. omega1
-//        in one base-2 exponent, MUFU ex2) and packed f32x2 FMAs over disparity pairs;
-//     d. running WTA over d (lowest d wins ties) keeping the neighbours of the best d.
-//  3. Epilogue: eq. (subpixel) on the winner's neighbours, add back s_i(v), write.
+//  2. For each chunk of DC disparities, the chunk's costs at the tile plus its bilateral halo,
+//     eq. (c), into shared memory (never device memory):
+//     cost_chunk_mma (k_fused) -- the cross term sum I_ref I_tar of every block on the tensor
+//        cores (exact FP16 operands, exact FP32 accumulation), one warp per 8-column block
+//        walking down its rows with the window as a running sum in the accumulator;
+//     cost_chunk (the warp-specialised form, and k_fused_tc.cuh) -- vertical running sums of
+//        the products per (product column, d) and horizontal sums over the w columns, band
+//        by band of cost rows;
+//     then c = 1 - (n S - S_ref S_tar) / sqrt(A_ref A_tar) with exact integer numerators.
+//  3. Aggregation: each thread owns a column of kPY pixels x DC disparities in registers;
+//     for every neighbour row it loads the DC costs once (LDS.128, the next row prefetched)
+//     and applies them to every pixel whose window holds it, with the weight
+//     w = 2^(K[dx][dy] - (s I_q - s I_p)^2) (eq. omega0 x eq. omega1 in one base-2
+//     exponent, MUFU ex2) and packed f32x2 FMAs over disparity pairs; then a running WTA
+//     over d (lowest d wins ties) keeping the neighbours of the best d.
+//  4. Epilogue: eq. (subpixel) on the winner's neighbours, add back s_i(v), write.
 // Normalising by sum_q w(p,q) is skipped: it is a positive per-pixel constant, so the
 // argmin and the (scale-free) parabola step do not change.
 #pragma once
@@ -226,7 +228,7 @@ template <> struct CostStore<__nv_bfloat16> {
 //   sI    [QH][QW] f32              scaled reference intensity at the cost positions
 //   sK    [KB][KB] f32              spatial part of the weight exponent
 struct SmemLayout {
-    size_t sref, stgt, cbuf, cbuf1, vband, sstr, sstt, sI, sK, bar, flag, total;
+    size_t sref, stgt, cbuf, cbuf1, vband, sstr, sstt, sI, sK, total;
 };
 
 // nbuf cost buffers (2 for the warp-specialised form), band cost rows per window-sum band;
@@ -247,9 +249,7 @@ __host__ __device__ inline SmemLayout smem_layout(int rb, int m, int dc, int ref
     L.sstt = align_up(L.sstr + (size_t)band * QW * 8, 16);
     L.sI = align_up(L.sstt + (size_t)band * (QW + dc - 1) * 8, 16);   // band 0: vband = sstr = sstt = sI
     L.sK = align_up(L.sI + (size_t)QH * QW * 4, 16);
-    L.bar = align_up(L.sK + (size_t)KB * KB * 4, 8);
-    L.flag = L.bar + 8;
-    L.total = align_up(L.flag + 8, 128);
+    L.total = align_up(L.sK + (size_t)KB * KB * 4, 128);
     return L;
 }
 
@@ -722,7 +722,6 @@ k_fused(const __grid_constant__ PairDesc single, const PairDesc *__restrict__ pa
         const PairDesc *pd = claim_tile<kThreads>(single, pairs, items, nitems, counter, iter, s_args, s_item, tid, tx, ty);
         if (!pd) return;
 
-        const int CW = TX + 2 * a.m;
         const int RP = a.ref_box_w, TP = a.tgt_box_w;
         const SmemLayout L = smem_layout(RB, a.m, DC, RP, TP, a.box_h, (int)sizeof(T), TX, TY, 1, 0);
         uint8_t *sref = smem + L.sref;
@@ -730,7 +729,6 @@ k_fused(const __grid_constant__ PairDesc single, const PairDesc *__restrict__ pa
         T *cbuf = reinterpret_cast<T *>(smem + L.cbuf);
         float *sI = reinterpret_cast<float *>(smem + L.sI);
         float *sK = reinterpret_cast<float *>(smem + L.sK);
-        (void)CW;
         const int x0 = tx * TX, y0 = ty * TY;
 
         // ---- 1. stage the image tiles with TMA
