@@ -57,6 +57,15 @@ def dist_env():
     return rank, world, local
 
 
+def measured_peaks():
+    """The generated peaks of the GB300s (empty when the file is absent)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
 def kernel_sha():
     h = hashlib.sha256()
     for f in ("internal.cuh", "k_fused.cuh", "k_fused_f32.cu"):
@@ -551,6 +560,18 @@ def run_ours(args):
     # the FP16 / BF16 forms do the same algorithmic work: their share of the same FP32 roofline
     for v in variants.values():
         v["fused_frac_of_fp32_roofline"] = agg_flops / (v["fused_ms"] * 1e-3) / 1e12 / peak
+    # the tensor-core form's executed mma work: per 4 x 4 patch, chunk of 16 disparities and
+    # window row, two m16n8k16 (4096 flop each), including the zero-weight K slots
+    peaks = measured_peaks()
+    nks = 4 + 2 * (bil // 2)
+    mma_flops = ((W + 63) // 64) * ((H + 35) // 36) * 144 * ((D + 15) // 16) * nks * 2 * 4096.0
+    for name in ("f16", "bf16"):
+        t_tf = mma_flops / (variants[name]["fused_ms"] * 1e-3) / 1e12
+        variants[name]["tensor_mma"] = {
+            "tflops": t_tf, "peak": peaks.get("bf16_tflops"), "unit": "TFLOP/s",
+            "frac": t_tf / peaks["bf16_tflops"] if peaks.get("bf16_tflops") else None,
+            "peak_basis": "measured dense bf16 (same rate for fp16), MEASURED_PEAKS.json",
+            "note": "the form is bound by weight generation and the integer cost phase, not the tensor pipe"}
     variants["kernel"] = {"f32": "k_fused (FP32 weights and accumulators)",
                           "f16": "k_fused_tc (tensor-core aggregation, FP32 accumulators)",
                           "bf16": "k_fused_tc (tensor-core aggregation, FP32 accumulators)"}
