@@ -211,11 +211,13 @@ typedef struct {
     int32_t cost_dtype;        /* STEREO_F32 | STEREO_F16 | STEREO_BF16 */
     double lambda0, delta_psi;
     int32_t max_iters;
-    int32_t tile_wc;           /* tile shape: warp columns 1 (32x64), 2 (64x32), 4 (128x16), or 8: 64x16
+    int32_t tile_wc;           /* tile shape: warp columns 1 (32x72), 2 (64x36), 4 (128x18); 8: 64x16
                                   tiles with the costs of the next chunk computed by separate producer
                                   warps while consumer warps aggregate (FP32 storage, tile_dc 12,
-                                  bil <= 11); 0 = autotune */
-    int32_t tile_dc;           /* disparities per chunk (12 or 4); 0 = autotune */
+                                  bil <= 11); 16: 64x36 tiles with the aggregation on the tensor cores
+                                  (FP16 / BF16 storage, tile_dc 16, bil <= 13, sigma1 <= 150);
+                                  0 = autotune */
+    int32_t tile_dc;           /* disparities per chunk (12 or 4; 16 with tile_wc 16); 0 = autotune */
 } stereo_batch_params;
 
 typedef struct stereo_batch stereo_batch;
