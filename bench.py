@@ -68,7 +68,7 @@ def measured_peaks():
 
 def kernel_sha():
     h = hashlib.sha256()
-    for f in ("internal.cuh", "k_fused.cuh", "k_fused_f32.cu"):
+    for f in ("internal.cuh", "k_fused_common.cuh", "k_cost.cuh", "k_fused.cuh", "k_fused_f32.cu"):
         h.update(open(os.path.join(ROOT, "paper_1904_06017_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "k_fused.cuh"
+#include "k_fused_common.cuh"
 
 struct stereo_batch {
     stereo_batch_params bp;

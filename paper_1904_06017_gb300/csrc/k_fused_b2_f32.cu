@@ -1,6 +1,7 @@
 // k_fused_b2_f32.cu -- FP32 instantiations of the fused kernel with the best2 output (the
 // smallest E over d != d* tracked beside the running WTA), for single-pair contexts (WC = 2,
 // 12 disparities per chunk); and the choice of a best2 kernel for a context.
+#include "k_fused.cuh"
 #include "k_fused_tc.cuh"
 
 namespace sgb {

@@ -2,6 +2,7 @@
 // side shared by all storage types (shared-memory sizing, kernel choice, launch).
 #include <string.h>
 
+#include "k_fused.cuh"
 #include "k_fused_tc.cuh"
 
 namespace sgb {

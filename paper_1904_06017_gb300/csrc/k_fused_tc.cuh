@@ -23,7 +23,7 @@
 // The weights are rounded to the storage type and the weight normaliser is skipped, as in
 // k_fused (a positive per-pixel factor changes neither the argmin nor the parabola step).
 #pragma once
-#include "k_fused.cuh"
+#include "k_cost.cuh"
 
 namespace sgb {
 

@@ -1,6 +1,6 @@
 // k_fused_ws.cu -- instantiations of the warp-specialised fused kernel (FP32 cost storage,
 // 12 disparities per chunk, bilateral radius up to kWsMaxRB).
-#include "k_fused.cuh"
+#include "k_fused_ws.cuh"
 
 namespace sgb {
 
