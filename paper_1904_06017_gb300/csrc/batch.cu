@@ -25,11 +25,19 @@ struct stereo_batch {
     int *d_counter = nullptr;
     int nitems = 0;
     cudaStream_t cap = nullptr;
+    // side streams of the capture: the per-pair launches before and after the fused
+    // kernel form independent chains of the graph, so the small kernels of different
+    // pairs (single-block roll searches among them) run side by side
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
 
 namespace sgb {
+
+constexpr int kBatchBranches = 16;   // side streams of the captured graph
 
 static void release_build(stereo_batch *b)
 {
@@ -138,24 +146,42 @@ static int enqueue_fused(stereo_batch *b, cudaStream_t s)
     return cuda_error(cudaGetLastError(), "batch: fused launch");
 }
 
-static int enqueue_pre(stereo_batch *b, cudaStream_t s)
+// the warp, staging and row tables of pair i (every pair has its own context and buffers)
+static int enqueue_pre_pair(stereo_batch *b, size_t i, cudaStream_t s)
 {
-    int rc = STEREO_OK;
-    for (size_t i = 0; i < b->pairs.size() && !rc; ++i) {
-        const stereo_pair_desc &d = b->pairs[i];
-        rc = launch_warp(b->ctx[i], d.tgt_dev, d.shift_dev, d.tgt_warped_dev, s);
-        if (!rc) rc = launch_prep(b->ctx[i], d.ref_dev, d.tgt_warped_dev, s);
-        if (!rc) rc = launch_row_tables(b->ctx[i], d.shift_dev, s);
-    }
+    const stereo_pair_desc &d = b->pairs[i];
+    int rc = launch_warp(b->ctx[i], d.tgt_dev, d.shift_dev, d.tgt_warped_dev, s);
+    if (!rc) rc = launch_prep(b->ctx[i], d.ref_dev, d.tgt_warped_dev, s);
+    if (!rc) rc = launch_row_tables(b->ctx[i], d.shift_dev, s);
     return rc;
 }
 
-static int enqueue_post(stereo_batch *b, cudaStream_t s)
+// the disparity transformation of pair i
+static int enqueue_post_pair(stereo_batch *b, size_t i, cudaStream_t s)
+{
+    const stereo_pair_desc &d = b->pairs[i];
+    return launch_dt(b->ctx[i], d.disp_dev, d.valid_dev, d.psi_init, d.delta_t, d.disp_out_dev, d.res_dev, s);
+}
+
+static int enqueue_pre(stereo_batch *b, cudaStream_t s)
 {
     int rc = STEREO_OK;
-    for (size_t i = 0; i < b->pairs.size() && !rc; ++i) {
-        const stereo_pair_desc &d = b->pairs[i];
-        rc = launch_dt(b->ctx[i], d.disp_dev, d.valid_dev, d.psi_init, d.delta_t, d.disp_out_dev, d.res_dev, s);
+    for (size_t i = 0; i < b->pairs.size() && !rc; ++i) rc = enqueue_pre_pair(b, i, s);
+    return rc;
+}
+
+// fn(b, i, stream) for every pair, the pairs dealt round-robin to the side streams, which
+// are forked from s before and joined into s after
+static int enqueue_branches(stereo_batch *b, cudaStream_t s, int (*fn)(stereo_batch *, size_t, cudaStream_t))
+{
+    const size_t nb = std::min(b->side.size(), b->pairs.size());
+    int rc = cuda_error(cudaEventRecord(b->fork, s), "batch: fork");
+    for (size_t k = 0; k < nb && !rc; ++k)
+        rc = cuda_error(cudaStreamWaitEvent(b->side[k], b->fork, 0), "batch: fork wait");
+    for (size_t i = 0; i < b->pairs.size() && !rc; ++i) rc = fn(b, i, b->side[i % nb]);
+    for (size_t k = 0; k < nb && !rc; ++k) {
+        rc = cuda_error(cudaEventRecord(b->join[k], b->side[k]), "batch: join");
+        if (!rc) rc = cuda_error(cudaStreamWaitEvent(s, b->join[k], 0), "batch: join wait");
     }
     return rc;
 }
@@ -164,9 +190,9 @@ static int capture(stereo_batch *b)
 {
     int rc = cuda_error(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "batch: begin capture");
     if (rc) return rc;
-    rc = enqueue_pre(b, b->cap);
+    rc = enqueue_branches(b, b->cap, enqueue_pre_pair);
     if (!rc) rc = enqueue_fused(b, b->cap);
-    if (!rc) rc = enqueue_post(b, b->cap);
+    if (!rc) rc = enqueue_branches(b, b->cap, enqueue_post_pair);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
     if (rc) {
@@ -353,6 +379,15 @@ int stereo_batch_create(const stereo_batch_params *p, int32_t n, const stereo_pa
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
     int rc = cuda_error(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "batch: create stream");
+    if (!rc) rc = cuda_error(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "batch: create event");
+    for (int k = 0; k < kBatchBranches && !rc; ++k) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        rc = cuda_error(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "batch: create stream");
+        if (!rc) b->side.push_back(st);
+        if (!rc) rc = cuda_error(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "batch: create event");
+        if (!rc) b->join.push_back(ev);
+    }
     int wc = p->tile_wc, dc = p->tile_dc;
     if (!rc && (!wc || !dc)) rc = autotune(b, &wc, &dc, &b->source);
     if (!rc) rc = build(b, wc, dc);
@@ -397,6 +432,9 @@ int stereo_batch_destroy(stereo_batch *b)
     cudaDeviceSynchronize();
     release_build(b);
     if (b->cap) cudaStreamDestroy(b->cap);
+    for (cudaStream_t st : b->side) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
     delete b;
     return STEREO_OK;
 }

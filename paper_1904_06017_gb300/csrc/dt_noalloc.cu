@@ -73,8 +73,7 @@ extern "C" int stereo_disparity_transform_noalloc(int32_t width, int32_t height,
     float *coef = reinterpret_cast<float *>(part + kNoAllocMoments);
     cudaStream_t s = (cudaStream_t)stream;
     const size_t N = (size_t)width * height;
-    int nb = (int)((N + (size_t)kDtThreads * 32 - 1) / ((size_t)kDtThreads * 32));   // 32-pixel runs per thread
-    if (nb > kDtMaxBlocks) nb = kDtMaxBlocks;
+    const int nb = dt_moment_blocks(N);
     // every partial block that the solve reads is written first by k_dt_moments, and the
     // coefficients are written by k_dt_solve before k_dt_apply reads them: nothing in the
     // scratch has to start at zero
@@ -85,7 +84,7 @@ extern "C" int stereo_disparity_transform_noalloc(int32_t width, int32_t height,
     k_dt_solve<<<1, kDtThreads, 0, s>>>(part, nb, width, height, psi_init, lambda0, delta_psi, max_iters,
                                         delta_t, r, coef);
     if ((rc = cuda_error(cudaGetLastError(), "stereo_disparity_transform_noalloc: solve launch"))) return rc;
-    dim3 block(128), grid((width + 127) / 128, height);
+    dim3 block(128), grid((width + 4 * 128 - 1) / (4 * 128), height);   // 4 pixels per thread where aligned
     k_dt_apply<<<grid, block, 0, s>>>(disp, width, height, coef, out);
     return cuda_error(cudaGetLastError(), "stereo_disparity_transform_noalloc: apply launch");
 }

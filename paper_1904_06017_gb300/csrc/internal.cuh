@@ -122,6 +122,7 @@ int launch_dt(stereo_ctx *ctx, const float *disp, const uint8_t *mask, double ps
 int run_fp32_probe(int blocks_per_sm, double *gflops_scalar, double *gflops_packed);
 
 // Kernels of the disparity transformation (k_dt.cu), shared with its no-allocation entry point.
+int dt_moment_blocks(size_t n_pixels);   // blocks of k_dt_moments for a map of n_pixels
 __global__ void k_dt_moments(const float *__restrict__ disp, const uint8_t *__restrict__ mask, int W, int H,
                              double *__restrict__ part);
 __global__ void k_dt_solve(const double *__restrict__ part, int nblocks, int W, int H, double psi_init,

@@ -6,7 +6,10 @@
 namespace sgb {
 
 // §3.1: tgt_warped(u, v) = tgt(clamp(u - s_i(v), 0, W-1), v), s_i = floor(s + 0.5).
-// One thread writes 16 consecutive bytes of an output row.
+// One thread writes 16 consecutive bytes of an output row.  Where the 16 source bytes lie
+// inside the row they come from the two aligned 16-byte words that cover them (rows are
+// [H][pitch] with pitch a multiple of 16, so the second word ends inside the row's pitch);
+// near the row ends and for unaligned buffers the bytes are read one by one.
 __global__ void k_warp(const uint8_t *__restrict__ tgt, const float *__restrict__ shift,
                        uint8_t *__restrict__ out, int W, int H, int pitch)
 {
@@ -17,11 +20,25 @@ __global__ void k_warp(const uint8_t *__restrict__ tgt, const float *__restrict_
     const uint8_t *row = tgt + (size_t)v * pitch;
     uint8_t *orow = out + (size_t)v * pitch;
     const int a = u0 - si;
-    if (u0 + 16 <= W && a >= 0 && a + 16 <= W && (a & 15) == 0) {
-        *reinterpret_cast<uint4 *>(orow + u0) = __ldg(reinterpret_cast<const uint4 *>(row + a));
+    const bool aligned = (((uintptr_t)tgt | (uintptr_t)out) & 15) == 0;
+    if (aligned && u0 + 16 <= W && a >= 0 && a + 16 <= W) {
+        const int ab = a & ~15, sh = a & 15;
+        const uint4 lo = __ldg(reinterpret_cast<const uint4 *>(row + ab));
+        uint4 hi = lo;
+        if (sh) hi = __ldg(reinterpret_cast<const uint4 *>(row + ab + 16));
+        const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+        const int q = sh >> 2, b = 8 * (sh & 3);
+        uint32_t t[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k)   // the words from q on, selected without local memory
+            t[k] = q == 0 ? w[k] : q == 1 ? w[k + 1] : q == 2 ? w[k + 2] : w[k + 3];
+        uint32_t o[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o[k] = __funnelshift_r(t[k], t[k + 1], b);   // bytes sh + 4k ..
+        *reinterpret_cast<uint4 *>(orow + u0) = make_uint4(o[0], o[1], o[2], o[3]);
         return;
     }
-    if (u0 + 16 <= W) {
+    if (aligned && u0 + 16 <= W) {
         uint32_t w[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -36,7 +53,7 @@ __global__ void k_warp(const uint8_t *__restrict__ tgt, const float *__restrict_
         *reinterpret_cast<uint4 *>(orow + u0) = make_uint4(w[0], w[1], w[2], w[3]);
         return;
     }
-    for (int u = u0; u < W; ++u) orow[u] = __ldg(row + min(max(u - si, 0), W - 1));
+    for (int u = u0; u < min(u0 + 16, W); ++u) orow[u] = __ldg(row + min(max(u - si, 0), W - 1));
 }
 
 int launch_warp(stereo_ctx *ctx, const uint8_t *tgt, const float *shift, uint8_t *out, cudaStream_t s)
@@ -53,8 +70,12 @@ int launch_warp(stereo_ctx *ctx, const uint8_t *tgt, const float *shift, uint8_t
 // the window statistics of the w x w block centred there:
 //     {S = sum I, bits of r = 1/sqrt(n * sum I^2 - S^2)}, r = 0 for a flat block.
 // These are the mu / sigma of eq. (c), kept as exact integer sums (§4.3 precomputes
-// mu and sigma in global memory as well).  Block: 32 x 8 positions.
-constexpr int kPrepX = 32, kPrepY = 8;
+// mu and sigma in global memory as well).  A block covers 32 x 32 positions: the images
+// are staged with the block's halo, the horizontal window sums (sum I, sum I^2, both
+// images) of every staged row are formed as running sums over groups of 4 columns, and
+// each thread then walks 4 consecutive rows of one column with running vertical sums.
+constexpr int kPrepX = 32, kPrepY = 8, kPrepRows = 32;   // threads x, y; positions per block in y
+constexpr int kPrepG = 4;                                 // columns per horizontal running-sum item
 
 __global__ void __launch_bounds__(kPrepX *kPrepY)
 k_prep(const uint8_t *__restrict__ ref, const uint8_t *__restrict__ tgt, int W, int H, int pitch,
@@ -62,54 +83,85 @@ k_prep(const uint8_t *__restrict__ ref, const uint8_t *__restrict__ tgt, int W, 
        uint8_t *__restrict__ ref_pad, uint8_t *__restrict__ tgt_pad,
        int2 *__restrict__ ref_stats, int2 *__restrict__ tgt_stats)
 {
-    constexpr int SX = kPrepX + 2 * kMaxRW, SY = kPrepY + 2 * kMaxRW;
+    constexpr int SX = kPrepX + 2 * kMaxRW, SY = kPrepRows + 2 * kMaxRW;
+    constexpr int NT = kPrepX * kPrepY;
     __shared__ uint8_t sr[SY][SX], st[SY][SX];
-    __shared__ int hs[2][SY][kPrepX], hq[2][SY][kPrepX];
-    const int x0 = blockIdx.x * kPrepX, y0 = blockIdx.y * kPrepY;
+    // rows padded to kPrepX + 1 words: the horizontal pass stores 4 rows x 8 column groups per
+    // warp, which an unpadded stride of 32 words would put 4 to a bank
+    __shared__ int hs[2][SY][kPrepX + 1], hq[2][SY][kPrepX + 1];
+    const int x0 = blockIdx.x * kPrepX, y0 = blockIdx.y * kPrepRows;
     const int tid = threadIdx.y * kPrepX + threadIdx.x;
-    const int sx = kPrepX + 2 * rw, sy = kPrepY + 2 * rw;
-    for (int i = tid; i < sx * sy; i += kPrepX * kPrepY) {
-        int ly = i / sx, lx = i % sx;
-        int ix = min(max(x0 - rw + lx - pad_left, 0), W - 1);
-        int iy = min(max(y0 - rw + ly - pad_top, 0), H - 1);
+    const int ws = 2 * rw + 1;
+    const int sx = kPrepX + 2 * rw, sy = kPrepRows + 2 * rw;
+    for (int i = tid; i < sx * sy; i += NT) {
+        const int ly = i / sx, lx = i - ly * sx;
+        const int ix = min(max(x0 - rw + lx - pad_left, 0), W - 1);
+        const int iy = min(max(y0 - rw + ly - pad_top, 0), H - 1);
         sr[ly][lx] = ref[(size_t)iy * pitch + ix];
         st[ly][lx] = tgt[(size_t)iy * pitch + ix];
     }
     __syncthreads();
-    // horizontal sums over 2rw+1 columns
-    for (int i = tid; i < sy * kPrepX; i += kPrepX * kPrepY) {
-        int ly = i / kPrepX, lx = i % kPrepX;
+    // horizontal sums over w columns: item = (staged row, group of kPrepG output columns),
+    // the window slid across the group
+    constexpr int NG = kPrepX / kPrepG;
+    for (int it = tid; it < sy * NG; it += NT) {
+        const int ly = it / NG, lx0 = (it - ly * NG) * kPrepG;
         int a = 0, aa = 0, b = 0, bb = 0;
-        for (int j = 0; j <= 2 * rw; ++j) {
-            int r = sr[ly][lx + j], t = st[ly][lx + j];
+        for (int j = 0; j < ws; ++j) {
+            const int r = sr[ly][lx0 + j], t = st[ly][lx0 + j];
             a += r;
             aa += r * r;
             b += t;
             bb += t * t;
         }
-        hs[0][ly][lx] = a;
-        hq[0][ly][lx] = aa;
-        hs[1][ly][lx] = b;
-        hq[1][ly][lx] = bb;
+#pragma unroll
+        for (int g = 0; g < kPrepG; ++g) {
+            hs[0][ly][lx0 + g] = a;
+            hq[0][ly][lx0 + g] = aa;
+            hs[1][ly][lx0 + g] = b;
+            hq[1][ly][lx0 + g] = bb;
+            if (g + 1 < kPrepG) {
+                const int ro = sr[ly][lx0 + g], ri = sr[ly][lx0 + g + ws];
+                const int to = st[ly][lx0 + g], ti = st[ly][lx0 + g + ws];
+                a += ri - ro;
+                aa += ri * ri - ro * ro;
+                b += ti - to;
+                bb += ti * ti - to * to;
+            }
+        }
     }
     __syncthreads();
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-    if (x >= pad_w || y >= pad_h) return;
-    const int n = (2 * rw + 1) * (2 * rw + 1);
+    // vertical sums: this thread's column, rows ry0 .. ry0 + 3 of the block
+    const int n = ws * ws;
+    const int lx = threadIdx.x, ry0 = threadIdx.y * (kPrepRows / kPrepY);
+    const int x = x0 + lx;
     int S[2] = {0, 0}, Q[2] = {0, 0};
-    for (int j = 0; j <= 2 * rw; ++j)
+    for (int j = 0; j < ws; ++j)
+#pragma unroll
         for (int k = 0; k < 2; ++k) {
-            S[k] += hs[k][threadIdx.y + j][threadIdx.x];
-            Q[k] += hq[k][threadIdx.y + j][threadIdx.x];
+            S[k] += hs[k][ry0 + j][lx];
+            Q[k] += hq[k][ry0 + j][lx];
         }
     int2 *dst[2] = {ref_stats, tgt_stats};
-    for (int k = 0; k < 2; ++k) {
-        int A = n * Q[k] - S[k] * S[k];   // n^2 sigma^2, exact (< 2^31 for w <= 11)
-        float r = A > 0 ? 1.0f / sqrtf((float)A) : 0.0f;
-        dst[k][(size_t)y * pad_w + x] = make_int2(S[k], __float_as_int(r));
+#pragma unroll
+    for (int i = 0; i < kPrepRows / kPrepY; ++i) {
+        const int ly = ry0 + i, y = y0 + ly;
+        if (i > 0)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                S[k] += hs[k][ly + ws - 1][lx] - hs[k][ly - 1][lx];
+                Q[k] += hq[k][ly + ws - 1][lx] - hq[k][ly - 1][lx];
+            }
+        if (x >= pad_w || y >= pad_h) continue;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int A = n * Q[k] - S[k] * S[k];   // n^2 sigma^2, exact (< 2^31 for w <= 11)
+            const float r = A > 0 ? 1.0f / sqrtf((float)A) : 0.0f;
+            dst[k][(size_t)y * pad_w + x] = make_int2(S[k], __float_as_int(r));
+        }
+        ref_pad[(size_t)y * pad_pitch + x] = sr[ly + rw][lx + rw];
+        tgt_pad[(size_t)y * pad_pitch + x] = st[ly + rw][lx + rw];
     }
-    ref_pad[(size_t)y * pad_pitch + x] = sr[threadIdx.y + rw][threadIdx.x + rw];
-    tgt_pad[(size_t)y * pad_pitch + x] = st[threadIdx.y + rw][threadIdx.x + rw];
 }
 
 int launch_prep(stereo_ctx *ctx, const uint8_t *ref, const uint8_t *tgtw, cudaStream_t s)
@@ -117,7 +169,7 @@ int launch_prep(stereo_ctx *ctx, const uint8_t *ref, const uint8_t *tgtw, cudaSt
     const Geometry &g = ctx->g;
     if (((uintptr_t)ref | (uintptr_t)tgtw) % 16)
         return set_error(STEREO_EINVAL, "images must be 16-byte aligned");
-    dim3 block(kPrepX, kPrepY), grid((g.pad_w + kPrepX - 1) / kPrepX, (g.pad_h + kPrepY - 1) / kPrepY);
+    dim3 block(kPrepX, kPrepY), grid((g.pad_w + kPrepX - 1) / kPrepX, (g.pad_h + kPrepRows - 1) / kPrepRows);
     k_prep<<<grid, block, 0, s>>>(ref, tgtw, g.W, g.H, g.pitch, g.rw, g.pad_left, g.pad_top, g.pad_w,
                                   g.pad_h, g.pad_pitch, ctx->ref_pad, ctx->tgt_pad, ctx->ref_stats,
                                   ctx->tgt_stats);
@@ -126,24 +178,38 @@ int launch_prep(stereo_ctx *ctx, const uint8_t *ref, const uint8_t *tgtw, cudaSt
 
 // Per image row v: the integer shift s_i(v) = floor(s(v) + 0.5) of §3.1, and the largest and
 // smallest s_i over rows v-m..v+m (the validity test of the fused epilogue).  FP64 here keeps
-// the rounding exact for any float s, once per row instead of once per pixel.
-__global__ void k_row_tables(const float *__restrict__ shift, int H, int m, int4 *__restrict__ tab)
+// the rounding exact for any float s.  A block of kRowTab rows first rounds its rows and an m-row
+// halo on each side once (an FP64 operation costs about as much as 64 FP32 ones on GB300),
+// then takes the window extremes from shared memory.
+constexpr int kRowTab = 128, kRowTabHalo = 16;   // m = rw + bilateral radius <= 12
+
+__global__ void __launch_bounds__(kRowTab) k_row_tables(const float *__restrict__ shift, int H, int m,
+                                                        int4 *__restrict__ tab)
 {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ int si[kRowTab + 2 * kRowTabHalo];
+    const int v0 = blockIdx.x * kRowTab;
+    for (int i = threadIdx.x; i < kRowTab + 2 * m; i += kRowTab) {
+        const int y = v0 - m + i;
+        si[i] = (y >= 0 && y < H) ? (int)floor((double)__ldg(shift + y) + 0.5) : 0;
+    }
+    __syncthreads();
+    const int v = v0 + threadIdx.x;
     if (v >= H) return;
     int hi = -(1 << 30), lo = 1 << 30;
-    for (int y = max(v - m, 0); y <= min(v + m, H - 1); ++y) {
-        const int s = (int)floor((double)shift[y] + 0.5);
+    const int ylo = max(v - m, 0), yhi = min(v + m, H - 1);
+    for (int y = ylo; y <= yhi; ++y) {
+        const int s = si[y - v0 + m];
         hi = max(hi, s);
         lo = min(lo, s);
     }
-    tab[v] = make_int4((int)floor((double)shift[v] + 0.5), hi, lo, 0);
+    tab[v] = make_int4(si[threadIdx.x + m], hi, lo, 0);
 }
 
 int launch_row_tables(stereo_ctx *ctx, const float *shift, cudaStream_t s)
 {
     const Geometry &g = ctx->g;
-    k_row_tables<<<(g.H + 127) / 128, 128, 0, s>>>(shift, g.H, g.m, ctx->row_tab);
+    if (g.m > kRowTabHalo) return set_error(STEREO_EINVAL, "k_row_tables: halo %d above %d", g.m, kRowTabHalo);
+    k_row_tables<<<(g.H + kRowTab - 1) / kRowTab, kRowTab, 0, s>>>(shift, g.H, g.m, ctx->row_tab);
     return cuda_error(cudaGetLastError(), "k_row_tables launch");
 }
 

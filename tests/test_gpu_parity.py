@@ -38,14 +38,17 @@ def run_fused(ref, tgtw, shift, D, win, bil, s0, s1, pitch_extra=0):
 
 
 # ------------------------------------------------------------------------------ warp
-@pytest.mark.parametrize("W,H", [(37, 5), (64, 9), (100, 17), (333, 11), (1, 3)])
-def test_warp_bit_exact(W, H):
+# widths equal to the pitch (320, 1920) put the second aligned source word of the last
+# interior segment at the end of the row; 40 rows of random shifts cover every byte offset
+@pytest.mark.parametrize("W,H,extra", [(37, 5, 16), (64, 9, 16), (100, 17, 16), (333, 11, 16), (1, 3, 16),
+                                         (320, 40, 0), (1920, 24, 0)])
+def test_warp_bit_exact(W, H, extra):
     rng = np.random.default_rng(W * 7 + H)
     tgt = rng.integers(0, 256, (H, W), dtype=np.uint8)
     shift = rng.uniform(-25, 25, H).astype(np.float32)
     shift[0] = 2.5
     shift[-1] = -2.5
-    pitch = pitch_of(W, 16)
+    pitch = pitch_of(W, extra)
     out = dev_img(np.zeros((H, W), np.uint8), pitch, fill=0xAB)
     with sg.Stereo(W, H, 8, win=3, bil=3, pitch=pitch) as st:
         st.warp_target(dev_img(tgt, pitch), dev_f32(shift), out)
