@@ -203,6 +203,35 @@ def test_dt_matches_oracle_on_a_shared_map(H, W, psi, psi_init):
     assert np.max(np.abs(out.cpu().numpy() - out_o)) < DT_TOL
 
 
+@pytest.mark.parametrize("H,W,psi,psi_init", [(120, 160, 0.05, 0.0), (540, 960, -0.08, 0.0),
+                                              (1080, 1920, 0.1, 0.3), (300, 200, 0.0, -0.2),
+                                              (240, 320, -0.6, 0.0)])
+def test_dt_reaches_the_plane_fit_closed_form(H, W, psi, psi_init):
+    """The minimum of eq. (E2) over (psi, alpha) has a closed form: alpha0 + alpha1 y(psi) spans
+    every affine function of (u, v), so the least-squares plane l ~ a + b u + c v over the
+    fitted pixels gives psi* = atan(-b / c), alpha1 = c / cos(psi*), alpha0 = a, and E_min(psi*)
+    is the plane's residual.  The device search lands within 1e-8 rad of psi*.  (The oracle,
+    which evaluates eq. (E_min2) on raw coordinates, stops up to about 5e-8 rad from psi* on
+    the 1080p map: its energy differences there are at its FP64 rounding floor.)"""
+    dmap = _plane_map(H, W, psi, 5.0, 0.12, 0.5, H + W).astype(np.float32)
+    rng = np.random.default_rng(1)
+    mask = (rng.random((H, W)) > 0.2).astype(np.uint8)
+    out = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    with sg.Stereo(W, H, 16, pitch=pitch_of(W)) as st:
+        res = st.disparity_transform(dev_f32(dmap), torch.from_numpy(mask).cuda(), psi_init, 0.0, out)
+    vv, uu = np.nonzero(mask)
+    A = np.stack([np.ones(len(uu)), uu.astype(np.float64), vv.astype(np.float64)], axis=1)
+    dv = dmap[vv, uu].astype(np.float64)
+    (a, b, c), *_ = np.linalg.lstsq(A, dv, rcond=None)
+    psi_star = math.atan(-b / c)
+    assert res.status == sg.STEREO_OK
+    assert abs(res.psi - psi_star) < 1e-8
+    assert res.alpha1 == pytest.approx(c / math.cos(psi_star), rel=1e-7)
+    assert res.alpha0 == pytest.approx(a, rel=1e-7, abs=1e-7)
+    resid = dv - A @ np.array([a, b, c])
+    assert res.e_min == pytest.approx(float(resid @ resid), rel=1e-7)
+
+
 def test_dt_device_result_iteration_cap_and_empty_mask():
     H, W = 64, 80
     dmap = _plane_map(H, W, 0.2, 3.0, 0.1, 0.3, 9).astype(np.float32)
