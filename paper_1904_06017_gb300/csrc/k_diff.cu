@@ -608,7 +608,7 @@ struct CbArgs {
 // columns); the d-independent terms of the reference gradient are summed over d per q and
 // box-summed once at the end.  Row strides are padded to odd lengths so that the running
 // sums of neighbouring rows hit distinct shared-memory banks.
-constexpr int kCbDC = 4;
+constexpr int kCbDC = 2;
 
 // Running box sums of one plane row: out[x] = sum_{j < WN} in[x + j], x < 32.
 template <int WN>
@@ -626,7 +626,7 @@ __device__ __forceinline__ void row_box(const float *in, float *out)
 }
 
 template <int RW>
-__global__ void __launch_bounds__(256) k_dcost_bwd(const CbArgs a)
+__global__ void __launch_bounds__(256, 3) k_dcost_bwd(const CbArgs a)
 {
     constexpr int QW = 32 + 2 * RW, QH = 8 + 2 * RW, NQ = QW * QH, NS = (NQ + 255) / 256;
     constexpr int WN = 2 * RW + 1, DC = kCbDC, NP = 4 * DC;   // planes: 4 terms x DC disparities
