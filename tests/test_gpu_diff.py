@@ -101,6 +101,23 @@ def test_forward_and_adjoint_match_the_oracle(scene, case):
     check_grad(gt[0], gto, "dS/dtgt")
 
 
+def test_rounded_shift_at_the_rounding_ties(scene):
+    """§3.1's s_i = floor(s + 0.5) taken exactly for shifts next to the ties, where s + 0.5
+    rounded to float32 would round up (0.5 - 2^-25 + 0.5 is a tie that rounds to 1.0): the
+    rounded warp and the add-back of s_i follow the oracle's exact rounding."""
+    ref, tgt, _ = synth.crop_pair(scene, 500, 300, 48, 16)
+    # one shift per row: values next to the ties of floor(s + 0.5), and the ties themselves
+    shift = np.array([0.5 - 2.0 ** -25, -0.5 - 2.0 ** -24, 0.5, -0.5, 1.5 - 2.0 ** -23, -1.5,
+                      2.5, -2.5 + 2.0 ** -22, 0.25 + 2.0 ** -26, 1e-30, -1e-30, 0.0,
+                      4.5, -3.5 - 2.0 ** -22, 0.375, 7.5], dtype=np.float32)
+    # the point of the test: rounding s + 0.5 to float32 first gets the first row wrong
+    assert np.floor(shift[0] + np.float32(0.5)) == 1.0 and odiff.round_shift(shift)[0] == 0
+    refd, tgtd = ref.astype(np.float64), tgt.astype(np.float64)
+    l, *_ = gpu_forward([refd], [tgtd], [shift], 16)
+    lo, *_ = odiff.disparity_vjp(refd, tgtd, shift, 16, WIN, BIL, S0, S1, T, np.zeros((16, 48)))
+    assert np.abs(l[0] - lo).max() <= L_TOL
+
+
 def test_energy_forward_and_adjoint_match_the_oracle():
     rng = np.random.default_rng(9)
     B, H, W = 3, 37, 53

@@ -48,6 +48,8 @@ def test_warp_bit_exact(W, H, extra):
     shift = rng.uniform(-25, 25, H).astype(np.float32)
     shift[0] = 2.5
     shift[-1] = -2.5
+    if H > 3:   # next to the ties, where s + 0.5 rounded to float32 would round up
+        shift[1], shift[2] = 0.5 - 2.0 ** -25, -0.5 - 2.0 ** -24
     pitch = pitch_of(W, extra)
     out = dev_img(np.zeros((H, W), np.uint8), pitch, fill=0xAB)
     with sg.Stereo(W, H, 8, win=3, bil=3, pitch=pitch) as st:
