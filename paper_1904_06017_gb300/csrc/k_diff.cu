@@ -27,6 +27,7 @@
 #include <string.h>
 
 #include "internal.cuh"
+#include "row_shift.cuh"
 #include "stereo_diff.h"
 
 namespace sgb {
@@ -60,20 +61,9 @@ __device__ __forceinline__ float ex2_fast(float x)
 
 __device__ __forceinline__ float lane(const float2 &v, int k) { return (k & 1) ? v.y : v.x; }
 
-// §3.1 integer row shift floor(s + 0.5), as the value added back to the disparity, exact for
-// every float s.  s + 0.5 rounded to float can round up to the next integer (s = 0.5 - 2^-25
-// gives 1.0 where the exact value floors to 0), so with f = floor(s) the test is s >= f + 0.5,
-// and f + 0.5 is a float for |s| < 2^22.  For 2^22 <= |s| < 2^23, s + 0.5 is exact (the
-// spacing of s is 0.5); from 2^23 on, s is an integer.
-__device__ __forceinline__ float row_shift_value(float s)
-{
-    const float as = fabsf(s);
-    if (as < 4194304.f) {
-        const float f = floorf(s);
-        return s >= f + 0.5f ? f + 1.f : f;
-    }
-    return as < 8388608.f ? floorf(s + 0.5f) : s;
-}
+// §3.1 integer row shift floor(s + 0.5) (exact for every float s), as the value added back to
+// the disparity.
+__device__ __forceinline__ float row_shift_value(float s) { return round_half_up(s); }
 
 // The same shift as a column offset, limited to +-2W: every column then clamps to the same
 // edge as it would with the exact value.

@@ -2,6 +2,7 @@
 // builds replicate-padded copies and per-position window statistics for the fused
 // kernel, and an FP32 FMA throughput probe.
 #include "internal.cuh"
+#include "row_shift.cuh"
 
 namespace sgb {
 
@@ -16,7 +17,7 @@ __global__ void k_warp(const uint8_t *__restrict__ tgt, const float *__restrict_
     const int v = blockIdx.y;
     const int u0 = (blockIdx.x * blockDim.x + threadIdx.x) * 16;
     if (v >= H || u0 >= W) return;
-    const int si = (int)floor((double)shift[v] + 0.5);
+    const int si = (int)round_half_up(shift[v]);
     const uint8_t *row = tgt + (size_t)v * pitch;
     uint8_t *orow = out + (size_t)v * pitch;
     const int a = u0 - si;
@@ -177,10 +178,9 @@ int launch_prep(stereo_ctx *ctx, const uint8_t *ref, const uint8_t *tgtw, cudaSt
 }
 
 // Per image row v: the integer shift s_i(v) = floor(s(v) + 0.5) of §3.1, and the largest and
-// smallest s_i over rows v-m..v+m (the validity test of the fused epilogue).  FP64 here keeps
-// the rounding exact for any float s.  A block of kRowTab rows first rounds its rows and an m-row
-// halo on each side once (an FP64 operation costs about as much as 64 FP32 ones on GB300),
-// then takes the window extremes from shared memory.
+// smallest s_i over rows v-m..v+m (the validity test of the fused epilogue).  A block of
+// kRowTab rows first rounds its rows and an m-row halo on each side once, then takes the window
+// extremes from shared memory.
 constexpr int kRowTab = 128, kRowTabHalo = 16;   // m = rw + bilateral radius <= 12
 
 __global__ void __launch_bounds__(kRowTab) k_row_tables(const float *__restrict__ shift, int H, int m,
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kRowTab) k_row_tables(const float *__restrict_
     const int v0 = blockIdx.x * kRowTab;
     for (int i = threadIdx.x; i < kRowTab + 2 * m; i += kRowTab) {
         const int y = v0 - m + i;
-        si[i] = (y >= 0 && y < H) ? (int)floor((double)__ldg(shift + y) + 0.5) : 0;
+        si[i] = (y >= 0 && y < H) ? (int)round_half_up(__ldg(shift + y)) : 0;
     }
     __syncthreads();
     const int v = v0 + threadIdx.x;
