@@ -9,9 +9,15 @@
 #pragma once
 #include <math.h>
 
+#if defined(__CUDACC__)
+#define SGB_RS_HD __host__ __device__ __forceinline__
+#else
+#define SGB_RS_HD inline
+#endif
+
 namespace sgb {
 
-__device__ __forceinline__ float round_half_up(float s)
+SGB_RS_HD float round_half_up(float s)
 {
     const float as = fabsf(s);
     if (as < 4194304.f) {
