@@ -345,7 +345,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // exp2(kx + ky - (sI_p - sI_q)^2) with sI = kappa I; an out-of-image neighbour has
 // sI = kFar and a zero value, so its weight and every product with it are exactly 0.
 template <int MODE, int RB>
-__global__ void __launch_bounds__(agg_threads(MODE)) k_dagg(const AggArgs a)
+__global__ void __launch_bounds__(agg_threads(MODE), MODE == AGG_FWD ? 3 : MODE == AGG_GC ? 2 : 1) k_dagg(const AggArgs a)
 {
     constexpr int DC = kAggDC, NQ = DC / 4, NR = kAggRows + 2 * RB;
     constexpr bool DB = agg_dbuf(MODE);
