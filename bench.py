@@ -58,7 +58,7 @@ def dist_env():
 
 
 def measured_peaks():
-    """The generated peaks of the GB300s (empty when the file is absent)."""
+    """The measured GB300 peak rates in MEASURED_PEAKS.json (empty when the file is absent)."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f)
