@@ -234,6 +234,31 @@ def test_dt_reaches_the_plane_fit_closed_form(H, W, psi, psi_init):
     assert res.e_min == pytest.approx(float(resid @ resid), rel=1e-7)
 
 
+@pytest.mark.parametrize("H,W,offset", [(23, 37, 0), (47, 61, 1), (11, 13, 0), (31, 33, 3)])
+def test_dt_ragged_and_unaligned_maps(H, W, offset):
+    """Maps whose pixel count is not a multiple of the 32-pixel load pieces, and maps (and masks)
+    that start off a 16-byte boundary, take the per-pixel reads of the moments kernel: the same
+    fit as the oracle's."""
+    dmap = _plane_map(H, W, 0.07, 4.0, 0.15, 0.3, H * W + offset, dent=False).astype(np.float32)
+    rng = np.random.default_rng(H + W)
+    mask = (rng.random((H, W)) > 0.1).astype(np.uint8)
+    N = H * W
+    dbuf = torch.zeros(N + offset, dtype=torch.float32, device="cuda")
+    mbuf = torch.zeros(N + offset, dtype=torch.uint8, device="cuda")
+    dbuf[offset:] = torch.from_numpy(dmap.ravel()).cuda()
+    mbuf[offset:] = torch.from_numpy(mask.ravel()).cuda()
+    d_in, m_in = dbuf[offset:].view(H, W), mbuf[offset:].view(H, W)
+    out = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    with sg.Stereo(W, H, 2, pitch=pitch_of(W)) as st:
+        res = st.disparity_transform(d_in, m_in, 0.0, 0.5, out)
+    out_o, r_o = dt.disparity_transform(dmap.astype(np.float64), mask.astype(bool), delta_t=0.5)
+    assert res.status == sg.STEREO_OK and res.n == int(mask.sum())
+    assert abs(res.psi - r_o["psi"]) < math.pi / 1.8e6
+    assert res.alpha1 == pytest.approx(r_o["alpha1"], rel=1e-5)
+    assert res.alpha0 == pytest.approx(r_o["alpha0"], rel=1e-5, abs=1e-4)
+    assert np.max(np.abs(out.cpu().numpy() - out_o)) < DT_TOL
+
+
 def test_dt_device_result_iteration_cap_and_empty_mask():
     H, W = 64, 80
     dmap = _plane_map(H, W, 0.2, 3.0, 0.1, 0.3, 9).astype(np.float32)
