@@ -70,3 +70,25 @@ def test_reference_rows_fit_the_budget():
     s = synth.make_scene(256, 64, 16, 5, warp=True)
     assert 1 <= bench.reference_rows(s, 1000, budget_s=0.01) <= 2
     assert bench.reference_rows(s, 1, budget_s=1e6) == 16
+
+
+def test_reference_arm_prints_the_contract_line():
+    """Rank 0 of `bench.py --impl reference` times the oracle on bands of the benchmark pair and
+    prints one JSON line in the same metric, unit and direction as the GPU arm, with the
+    oracle's run described under cpu_baseline and an end-to-end figure equal to its value."""
+    import json
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 1
+    assert d["value"] > 0 and d["ms_per_step"] > 0 and d["vs_baseline"] is None
+    assert d["config"]["workload"].startswith("road-stereo 1920x1080 D=128")
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
