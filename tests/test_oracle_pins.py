@@ -324,3 +324,96 @@ def test_error_metrics_definitions():
     assert metrics.error_pixel_percent(disp, gt, 2) == pytest.approx(5.0)
     assert metrics.error_pixel_percent(disp, gt, 1) == pytest.approx(10.0)
     assert metrics.rms_error(disp, gt) == pytest.approx(math.sqrt(13 / 20))
+
+
+# ------------------------------------------------ geometric validity (readings of §3.2, §3.3)
+
+def _valid_by_enumeration(W, H, D, rw, rb, shift_int):
+    """Every read behind pixel (u, v), listed one by one: for each neighbour q of the k x k
+    window (in the image or not), each offset j of the w x w block and each d in [0, D), the
+    reference read at q + j, the warped-target read at q + j - [d, 0], and the original-target
+    read behind the warp, at that column minus the integer shift of its row.  The pixel is
+    valid exactly when none of those coordinates lies outside the image (none needs a clamp).
+    The shift table is passed as integers, so no rounding enters this check."""
+    valid = np.zeros((H, W), np.uint8)
+    offs = range(-(rw + rb), rw + rb + 1)
+    # all (neighbour offset, block offset) pairs along one axis, listed explicitly
+    pairs = [(a, b) for a in range(-rb, rb + 1) for b in range(-rw, rw + 1)]
+    assert sorted({a + b for a, b in pairs}) == list(offs)
+    for v in range(H):
+        for u in range(W):
+            ok = True
+            for qy, jy in pairs:
+                y = v + qy + jy
+                for qx, jx in pairs:
+                    x = u + qx + jx
+                    if not (0 <= x < W and 0 <= y < H):          # reference read
+                        ok = False
+                        break
+                    for d in range(D):
+                        xt = x - d
+                        if not (0 <= xt < W):                     # warped-target read
+                            ok = False
+                            break
+                        xo = xt - int(shift_int[y])
+                        if not (0 <= xo < W):                     # original target behind the warp
+                            ok = False
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            valid[v, u] = ok
+    return valid
+
+
+@pytest.mark.parametrize("W,H,D,rw,rb,seed", [
+    (23, 13, 3, 1, 1, 0),
+    (20, 11, 1, 0, 0, 1),     # D = 1, w = k = 1: only the shift can invalidate a pixel
+    (26, 15, 4, 2, 1, 2),
+    (24, 12, 2, 0, 2, 3),     # w = 1
+    (22, 14, 5, 1, 0, 4),     # k = 1
+    (30, 17, 6, 1, 2, 5),
+])
+def test_valid_mask_equals_enumeration_of_every_read(W, H, D, rw, rb, seed):
+    rng = np.random.default_rng(seed)
+    # negative, zero and large shifts, and half-integers whose rounding goes up
+    base = rng.integers(-6, 7, size=H).astype(np.float64)
+    base[rng.integers(0, H)] = 0.0
+    base[rng.integers(0, H)] = W // 2           # large enough to empty a whole band
+    half = rng.random(H) < 0.3
+    s = np.where(half, base - 0.5, base)        # k - 0.5 rounds to k (halves go up)
+    shift_int = base.astype(np.int64)
+    got = oracle.valid_mask(W, H, D, 2 * rw + 1, 2 * rb + 1, s.astype(np.float32))
+    want = _valid_by_enumeration(W, H, D, rw, rb, shift_int)
+    assert np.array_equal(got, want), np.argwhere(got != want)[:8]
+
+
+def test_valid_mask_constant_shift_band():
+    # a constant shift s moves the valid band of every interior row by max(0, s) on the left
+    # and by min(0, s) on the right; the band is empty once it no longer fits
+    W, H, D, rw, rb = 40, 9, 5, 1, 1
+    m = rw + rb
+    for s in (-7, -1, 0, 3, 30):
+        got = oracle.valid_mask(W, H, D, 2 * rw + 1, 2 * rb + 1, np.full(H, s, np.float32))
+        lo, hi = m + D - 1 + max(0, s), W - 1 - m + min(0, s)
+        want = np.zeros((H, W), np.uint8)
+        if lo <= hi:
+            want[m:H - m, lo:hi + 1] = 1
+        assert np.array_equal(got, want), s
+
+
+# ------------------------------------------------------------ eq. (sigma_d), §4.4.2
+
+def test_sigma_d_hand_computed():
+    # s = (1, 2, 3, 4, 5, 7): mean 11/3, squared deviations sum to 70/3, and eq. (sigma_d)
+    # divides by m = 6: sigma_d = sqrt(35/9) = sqrt(35)/3 (a 1/(m-1) form would give sqrt(70/15))
+    s = np.array([[1.0, 2.0, 3.0], [4.0, 5.0, 7.0]])
+    assert metrics.sigma_d(s) == pytest.approx(math.sqrt(35.0) / 3.0, rel=1e-14)
+    # the mask selects the elements that enter: (2, 4, 7) -> mean 13/3, deviations
+    # (-7/3, -1/3, 8/3), squares sum to 114/9, divided by 3 -> sqrt(38)/3
+    mask = np.array([[0, 1, 0], [1, 0, 1]], bool)
+    assert metrics.sigma_d(s, mask) == pytest.approx(math.sqrt(38.0) / 3.0, rel=1e-14)
+    # a constant offset does not change it; a scale multiplies it
+    assert metrics.sigma_d(s + 100.0) == pytest.approx(math.sqrt(35.0) / 3.0, rel=1e-12)
+    assert metrics.sigma_d(2.5 * s) == pytest.approx(2.5 * math.sqrt(35.0) / 3.0, rel=1e-14)
