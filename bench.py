@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-diff", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     return ap.parse_args()
 
@@ -74,15 +75,19 @@ def kernel_sha():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background, with the
+    sampler's timestamps, so that the samples of any interval (the timed steps) can be told
+    from the rest.  Started before the warm-up so that a short timed region still has samples."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.marks = {}
 
     def start(self):
         try:
@@ -94,7 +99,30 @@ class ClockSampler:
         except (OSError, FileNotFoundError):
             self.proc = None
 
-    def stop(self):
+    def mark(self, name):
+        """Wall-clock time of an event (local time, as nvidia-smi's timestamps)."""
+        self.marks[name] = time.time()
+
+    @staticmethod
+    def _when(ts):
+        import datetime
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(ts, fmt).timestamp()
+            except ValueError:
+                pass
+        return None
+
+    def _summary(self, rows):
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        reasons = sorted({self.REASONS[i] for r in rows for i in range(4) if r[6 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+    def stop(self, t0=None, t1=None):
+        """Summary of the samples between marks t0 and t1 (all samples if unset), plus the
+        summary of every sample taken under load (from the first mark on)."""
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -105,17 +133,22 @@ class ClockSampler:
         rows = []
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 9:
+            if len(parts) >= 10:
                 rows.append(parts)
         os.unlink(self.path)
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+        when = [self._when(r[0]) for r in rows]
+        lo, hi = self.marks.get(t0), self.marks.get(t1)
+        timed = [r for r, w in zip(rows, when) if w is not None and lo is not None and hi is not None
+                 and lo - 0.1 <= w <= hi + 0.1]
+        first = min(self.marks.values()) if self.marks else None
+        load = [r for r, w in zip(rows, when) if w is not None and first is not None and w >= first]
+        out = self._summary(timed if timed else load if load else rows)
+        out["window"] = "timed steps" if timed else "whole GPU phase of the bench"
+        out["under_load"] = self._summary(load if load else rows)
+        out["under_load"]["window"] = "warm-up, timed steps, end-to-end and storage-variant legs"
+        return out
 
 
 def max_over_ranks(x, world, device="cpu"):
@@ -240,6 +273,7 @@ def bench_batch(args, dev, stream, flush):
         pairs.append(dict(ref=img(s.ref), tgt=img(s.tgt), shift=torch.from_numpy(s.shift).to(dev),
                           tgt_warped=torch.empty((H, pitch), dtype=torch.uint8, device=dev),
                           disp=torch.empty((H, W), dtype=torch.float32, device=dev),
+                          wta=torch.empty((H, W), dtype=torch.int32, device=dev),
                           valid=torch.empty((H, W), dtype=torch.uint8, device=dev),
                           disp_out=torch.empty((H, W), dtype=torch.float32, device=dev),
                           res=torch.zeros(64, dtype=torch.uint8, device=dev), max_disp=D))
@@ -247,7 +281,7 @@ def bench_batch(args, dev, stream, flush):
     out = {"pairs": len(scenes), "sizes": sorted({"%dx%d" % (s.width, s.height) for s in scenes}),
            "search_ranges": sorted({s.params["D"] for s in scenes}), "win": cfg["win"], "bil": cfg["bil"]}
     steps = max(3, min(args.steps, 20))
-    disp32 = None
+    disp32 = wta32 = None
     for name, dtype in (("f32", sg.STEREO_F32), ("f16", sg.STEREO_F16)):
         b = sg.StereoBatch(pairs, win=cfg["win"], bil=cfg["bil"], sigma0=cfg["sigma0"], sigma1=cfg["sigma1"],
                            cost_dtype=dtype)
@@ -263,18 +297,96 @@ def bench_batch(args, dev, stream, flush):
         b.check_device_status()
         ms = sum(a.elapsed_time(c) for a, c in ev) / steps
         disp = [q["disp"].cpu().numpy() for q in pairs]
+        wta = [q["wta"].cpu().numpy() for q in pairs]
+        valid = [q["valid"].cpu().numpy().astype(bool) for q in pairs]
         rec = {"ms_per_batch": ms, "pairs_per_s": len(scenes) * 1e3 / ms,
                "gpix_disp_per_s": units / ms / 1e6, "graph_runs": steps, "tiles": b.config()}
         if disp32 is None:
-            disp32 = disp
+            disp32, wta32 = disp, wta
         else:
+            npx = sum(a.size for a in disp32)
             moved = sum(int(np.count_nonzero(np.abs(a - c) > 0.5)) for a, c in zip(disp32, disp))
-            rec["disp_diff_gt_half_px_vs_f32"] = moved / sum(a.size for a in disp32)
+            rec["disp_diff_gt_half_px_vs_f32"] = moved / npx
+            # the integer WTA disparity d*: the fraction of pixels whose d* differs from the
+            # batched FP32 form's (the pass line is 0.1 %), over all pixels and over valid ones
+            rec["wta_disagree_vs_f32"] = sum(int(np.count_nonzero(a != c)) for a, c in zip(wta32, wta)) / npx
+            nv = sum(int(m.sum()) for m in valid)
+            rec["wta_disagree_vs_f32_valid"] = (sum(int(np.count_nonzero((a != c) & m))
+                                                    for a, c, m in zip(wta32, wta, valid)) / max(nv, 1))
+            rec["wta_disagree_pass"] = rec["wta_disagree_vs_f32"] <= 1e-3
         out[name] = rec
         b.close()
     del pairs
     torch.cuda.empty_cache()
     return out
+
+
+def bench_precision(args, dev, stream, flush, peak):
+    """The precision workload: one 1920 x 1080 pair, D = 192, w = 9, k = 13, with the cost
+    volume stored as FP32, FP16 and BF16 (FP32 accumulators in every form).  One step = warp
+    -> fused cost/aggregation/WTA -> disparity transformation, L2 flushed before each step.
+    Reports each form's step time, throughput, the fused kernel's share of the FP32 roofline
+    (the same algorithmic work in every form) and its integer-WTA disagreement with FP32."""
+    import numpy as np
+    import torch
+    import paper_1904_06017_gb300 as sg
+    import synth
+    s = synth.make_config_scene("precision")
+    p = s.params
+    H, W, D, win, bil = s.height, s.width, p["D"], p["win"], p["bil"]
+    pitch = (W + 15) // 16 * 16
+
+    def img(a):
+        t = torch.zeros((H, pitch), dtype=torch.uint8)
+        t[:, :W] = torch.from_numpy(a)
+        return t.to(dev)
+
+    ref, tgt, shift = img(s.ref), img(s.tgt), torch.from_numpy(s.shift).to(dev)
+    tw = torch.empty_like(tgt)
+    disp = torch.empty((H, W), dtype=torch.float32, device=dev)
+    valid = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    out = torch.empty_like(disp)
+    res = torch.zeros(64, dtype=torch.uint8, device=dev)
+    flops_per_unit = 2.0 * bil * bil + 11.0 + 2.0 * bil * bil / D + 1.0
+    flops = flops_per_unit * W * H * D
+    n = max(3, min(args.steps, 20))
+    rec = {"workload": "1920x1080 D=192 w=9 k=13 sigma0=3 sigma1=10", "flops_per_pixel_disparity": flops_per_unit}
+    wta32 = None
+    for name, dtype in (("f32", sg.STEREO_F32), ("f16", sg.STEREO_F16), ("bf16", sg.STEREO_BF16)):
+        sv = sg.Stereo(W, H, D, win=win, bil=bil, sigma0=p["sigma0"], sigma1=p["sigma1"], pitch=pitch,
+                       cost_dtype=dtype)
+        wta = torch.empty((H, W), dtype=torch.int32, device=dev)
+        sv.warp_target(tgt, shift, tw)
+        sv.cost_aggregate_wta(ref, tw, shift, disp, wta, valid)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        sg.stereo_profile_enable(sv.ctx, True)
+        for i in range(n):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            sv.warp_target(tgt, shift, tw)
+            sv.cost_aggregate_wta(ref, tw, shift, disp, None, valid)
+            sv.disparity_transform(disp, valid, 0.0, 0.0, out, res=res)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        nf, fms = sg.stereo_profile_read(sv.ctx)
+        sg.stereo_profile_enable(sv.ctx, False)
+        sv.check_device_status()
+        sv.close()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / n
+        fused = fms / max(nf, 1)
+        w = wta.cpu().numpy()
+        vm = valid.cpu().numpy().astype(bool)
+        if wta32 is None:
+            wta32 = w
+        r = {"ms_per_step": ms, "gpix_disp_per_s": W * H * D / ms / 1e6, "pairs_per_s": 1e3 / ms,
+             "fused_ms": fused, "fused_tflops": flops / (fused * 1e-3) / 1e12,
+             "fused_frac_of_fp32_roofline": flops / (fused * 1e-3) / 1e12 / peak, "steps": n}
+        if name != "f32":
+            r["wta_disagree_vs_f32"] = float(np.mean(w != wta32))
+            r["wta_disagree_vs_f32_valid"] = float(np.mean((w != wta32)[vm])) if vm.any() else None
+        rec[name] = r
+    return rec
 
 
 def bench_diff(args, dev, stream, flush):
@@ -327,7 +439,28 @@ def bench_diff(args, dev, stream, flush):
     torch.cuda.synchronize()
     fwd_ms = sum(a.elapsed_time(b) for a, b in e_f) / n
     step_ms = sum(a.elapsed_time(b) for a, b in e_s) / n
-    mask = torch.ones((B, H, W), dtype=torch.uint8, device=dev)
+    # the fit mask: the library's geometric validity of each pair (no read behind any d
+    # clamped), from the plain fused path on the same pair
+    import paper_1904_06017_gb300 as sg
+    pitch = (W + 15) // 16 * 16
+    mask = torch.empty((B, H, W), dtype=torch.uint8, device=dev)
+    search_psi = []
+    with sg.Stereo(W, H, D, win=kw["win"], bil=kw["bil"], sigma0=kw["sigma0"], sigma1=kw["sigma1"],
+                   pitch=pitch) as st:
+        for b, sc in enumerate(scenes):
+            def img(a):
+                t = torch.zeros((H, pitch), dtype=torch.uint8)
+                t[:, :W] = torch.from_numpy(a)
+                return t.to(dev)
+            rb, tb = img(sc.ref), img(sc.tgt)
+            tw = torch.empty_like(tb)
+            dtmp = torch.empty((H, W), dtype=torch.float32, device=dev)
+            st.warp_target(tb, shift[b], tw)
+            st.cost_aggregate_wta(rb, tw, shift[b], dtmp, None, mask[b])
+            # the paper's roll search (the A7 kernel) on the same soft-argmin map and mask
+            r = st.disparity_transform(l[b].detach().contiguous(), mask[b], 0.0, 0.0, dtmp)
+            search_psi.append(r.psi)
+        st.check_device_status()
     sgd.refine_roll(l.detach(), mask, 0.0, 50)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -336,6 +469,16 @@ def bench_diff(args, dev, stream, flush):
     e1.record(stream)
     torch.cuda.synchronize()
     psi = traj[:, -1, 0].cpu().numpy()
+    # closed form on the same map and mask: the least-squares plane l = a + b u + c v gives
+    # psi* = atan(-b / c) in (-pi/2, pi/2] (alpha0 + alpha1 y(psi) spans every plane)
+    lh, mh = l.detach().double().cpu().numpy(), mask.cpu().numpy().astype(bool)
+    vv, uu = np.mgrid[0:H, 0:W]
+    plane_psi = []
+    for b in range(B):
+        m = mh[b]
+        A = np.stack([np.ones(int(m.sum())), uu[m], vv[m]], 1).astype(np.float64)
+        coef = np.linalg.lstsq(A, lh[b][m], rcond=None)[0]
+        plane_psi.append(math.atan(-coef[1] / coef[2]))
     units = B * W * H * D
     k2 = cfg["bil"] ** 2
     return {"pairs": B, "size": "%dx%d" % (W, H), "max_disp": D, "temperature": cfg["temperature"],
@@ -345,8 +488,15 @@ def bench_diff(args, dev, stream, flush):
             "aggregation_flops_per_step": 2.0 * k2 * units * (1 + 2 + 2),
             "aggregation_tflops_effective": 2.0 * k2 * units * 5 / (step_ms * 1e-3) / 1e12,
             "refine_roll_50_steps_ms": e0.elapsed_time(e1),
+            "fit_mask": "geometric validity from the library's fused path (%.1f %% of pixels)"
+                        % (100.0 * float(mh.mean())),
             "refined_psi_deg": [float(np.degrees(x)) for x in psi],
+            "search_psi_deg": [float(np.degrees(x)) for x in search_psi],
+            "plane_fit_psi_deg": [float(np.degrees(x)) for x in plane_psi],
+            "refined_minus_plane_fit_rad": [float(a - c) for a, c in zip(psi, plane_psi)],
+            "search_minus_plane_fit_rad": [float(a - c) for a, c in zip(search_psi, plane_psi)],
             "true_roll_deg": [float(np.degrees(s.roll)) for s in scenes],
+            "plane_fit_minus_true_roll_deg": [float(np.degrees(c - s.roll)) for c, s in zip(plane_psi, scenes)],
             "grad_finite": bool(torch.isfinite(ref.grad).all() and torch.isfinite(tgt.grad).all()),
             "steps": n}
 
@@ -403,23 +553,26 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)            # the sampler's first reading precedes the warm-up
+    clocks.mark("warmup")
     for _ in range(args.warmup):
         step()
     st.check_device_status()
 
     # ---- device-resident timing, L2 flushed before each step (outside the events)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(torch.cuda.current_device())
     sg.stereo_profile_enable(st.ctx, True)
     barrier()
-    clocks.start()
+    clocks.mark("timed_start")
     for i in range(args.steps):
         flush.fill_(i & 0xFF)
         ev[i][0].record(stream)
         step()
         ev[i][1].record(stream)
     barrier()
-    clk = clocks.stop()
+    clocks.mark("timed_end")
     n_fused, fused_ms = sg.stereo_profile_read(st.ctx)
     sg.stereo_profile_enable(st.ctx, False)
     st.check_device_status()
@@ -534,6 +687,8 @@ def run_ours(args):
           "kept_fraction": float(lr_ok.float().mean()),
           "kept_fraction_of_valid": float(lr_ok[vm].float().mean()) if bool(vm.any()) else None}
 
+    clk = clocks.stop("timed_start", "timed_end")
+
     if rank != 0:
         st.close()
         if world > 1:
@@ -590,6 +745,11 @@ def run_ours(args):
             line["batch"] = bench_batch(args, dev, stream, flush)
         except Exception as exc:   # the headline line above stands on its own
             line["batch"] = {"error": str(exc)[:300]}
+    if not args.no_precision:
+        try:
+            line["precision"] = bench_precision(args, dev, stream, flush, peak)
+        except Exception as exc:   # the headline line above stands on its own
+            line["precision"] = {"error": str(exc)[:300]}
     if not args.no_diff:
         try:
             line["differentiation"] = bench_diff(args, dev, stream, flush)

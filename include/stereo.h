@@ -203,6 +203,7 @@ typedef struct {
     stereo_dt_result *res_dev;                /* device result of the transformation (output) */
     double psi_init;                          /* roll search start */
     float delta_t;                            /* eq. (disparity_transformation) offset */
+    int32_t *wta_dev;                         /* [H][W] integer WTA disparity d* (optional output, or NULL) */
 } stereo_pair_desc;
 
 typedef struct {
@@ -258,7 +259,14 @@ int stereo_batch_destroy(stereo_batch *b);
  * to 1024 blocks and the final coefficients, 80 KiB + 64 B) is a fixed array inside the
  * library's device image, present on every device that loads the library until exit.
  *   - The first call on each device looks up that array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.  The address
+ *     is cached with the unique id of the context it was read in; a call in a new context
+ *     (after cudaDeviceReset, say) looks it up again, so that first call in the new context
+ *     also belongs before any capture.
+ *   - The first call into the library in a process (this one or any other) initialises the
+ *     library's CUDA runtime, which loads the library's device code: the driver takes device
+ *     memory for that image then (about 16 MiB), not this call.  A caller that cannot let
+ *     free memory move at all makes one call during start-up.
  *   - Every call shares the one array and leaves its last contents there; nothing in it
  *     needs to start at zero.  Calls whose kernels overlap on the GPU (other streams, other
  *     host threads) race on it: serialise them.
@@ -339,6 +347,15 @@ int stereo_warp_est_destroy(stereo_warp_est *e);
 /* Synchronise the stream, read and clear the context's device status word.
  * Returns STEREO_OK, or STEREO_ETIMEOUT when a kernel gave up a bounded wait. */
 int stereo_check_device_status(stereo_ctx *ctx, stereo_stream_t stream);
+
+/* Test hook of the failure path above (no counterpart in the paper).  With on != 0, later
+ * fused launches of this context (stereo_cost_aggregate_wta, _ex, stereo_lr_check) arm each
+ * tile's staging barrier but issue no copy, so every CTA's bounded wait expires after about
+ * a millisecond with nothing in flight; the CTA sets the status word and returns, the
+ * launch's outputs are invalid, and stereo_check_device_status reports STEREO_ETIMEOUT (and
+ * clears the word).  on = 0 restores normal launches; the context stays usable.  No fault,
+ * trap or hang is involved.  Returns STEREO_OK, or STEREO_EINVAL for a NULL context. */
+int stereo_debug_stall_staging(stereo_ctx *ctx, int32_t on);
 
 /* Timing of the fused kernel alone: when enabled (on != 0), every later
  * stereo_cost_aggregate_wta records CUDA events on its stream around the fused

@@ -21,7 +21,7 @@ __all__ = [
     "stereo_params_default", "stereo_create", "stereo_destroy", "stereo_row_shift_affine",
     "stereo_warp_target", "stereo_cost_aggregate_wta", "stereo_cost_aggregate_wta_ex", "stereo_disparity_transform",
     "stereo_cost_volume", "stereo_aggregate_volume", "stereo_wta_volume",
-    "stereo_check_device_status", "stereo_profile_enable", "stereo_profile_read",
+    "stereo_check_device_status", "stereo_debug_stall_staging", "stereo_profile_enable", "stereo_profile_read",
     "stereo_fp32_peak_probe", "stereo_last_error", "stereo_version", "Stereo",
     "stereo_disparity_transform_noalloc", "stereo_lr_check", "WarpEstimator", "stereo_pair_desc",
     "stereo_batch_params",
@@ -74,7 +74,7 @@ class stereo_pair_desc(ctypes.Structure):
                 ("shift_dev", ctypes.c_void_p), ("tgt_warped_dev", ctypes.c_void_p),
                 ("disp_dev", ctypes.c_void_p), ("valid_dev", ctypes.c_void_p),
                 ("disp_out_dev", ctypes.c_void_p), ("res_dev", ctypes.c_void_p),
-                ("psi_init", ctypes.c_double), ("delta_t", ctypes.c_float)]
+                ("psi_init", ctypes.c_double), ("delta_t", ctypes.c_float), ("wta_dev", ctypes.c_void_p)]
 
 
 class stereo_batch_params(ctypes.Structure):
@@ -111,6 +111,7 @@ def load_library():
         "stereo_aggregate_volume": [P, P, P, P, P],
         "stereo_wta_volume": [P, P, P, P, P, P, P],
         "stereo_check_device_status": [P, P],
+        "stereo_debug_stall_staging": [P, I32],
         "stereo_profile_enable": [P, I32],
         "stereo_profile_read": [P, P, P],
         "stereo_fp32_peak_probe": [I32, P, P],
@@ -284,6 +285,10 @@ def stereo_check_device_status(ctx, stream=None):
     _check(load_library().stereo_check_device_status(ctx, _stream(stream)))
 
 
+def stereo_debug_stall_staging(ctx, on=True):
+    _check(load_library().stereo_debug_stall_staging(ctx, 1 if on else 0))
+
+
 def stereo_profile_enable(ctx, on=True):
     _check(load_library().stereo_profile_enable(ctx, 1 if on else 0))
 
@@ -400,7 +405,8 @@ def stereo_batch_destroy(batch):
 class StereoBatch:
     """Owns one batch.  ``pairs`` is a list of dicts of CUDA tensors with keys ref, tgt,
     shift, tgt_warped, disp, valid, disp_out, res (uint8 tensor of >= 48 bytes) and ints
-    max_disp (and optionally psi_init, delta_t); images are [H][pitch] uint8 tensors."""
+    max_disp (and optionally psi_init, delta_t, and wta: an int32 [H][W] tensor that receives
+    the integer WTA disparity); images are [H][pitch] uint8 tensors."""
 
     def __init__(self, pairs, win=9, bil=11, sigma0=1.5, sigma1=5.5, cost_dtype=STEREO_F32,
                  tile_wc=0, tile_dc=0, **extra):
@@ -414,7 +420,8 @@ class StereoBatch:
             descs.append(stereo_pair_desc(W, H, pitch, int(q["max_disp"]), _ptr(q["ref"]), _ptr(q["tgt"]),
                                           _ptr(q["shift"]), _ptr(q["tgt_warped"]), _ptr(q["disp"]),
                                           _ptr(q["valid"]), _ptr(q["disp_out"]), _ptr(q["res"]),
-                                          float(q.get("psi_init", 0.0)), float(q.get("delta_t", 0.0))))
+                                          float(q.get("psi_init", 0.0)), float(q.get("delta_t", 0.0)),
+                                          _ptr(q.get("wta"))))
         self.pairs = pairs      # keep the tensors alive
         self.batch = stereo_batch_create(self.params, descs)
 

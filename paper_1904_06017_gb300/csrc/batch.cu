@@ -112,7 +112,7 @@ static int build(stereo_batch *b, int wc, int dc)
     std::vector<Item> items;
     for (int i = 0; i < n; ++i) {
         const stereo_pair_desc &d = b->pairs[i];
-        fill_pair_desc(b->ctx[i], d.disp_dev, nullptr, d.valid_dev, hp[i]);
+        fill_pair_desc(b->ctx[i], d.disp_dev, d.wta_dev, d.valid_dev, hp[i]);
         const Geometry &g = b->ctx[i]->g;
         for (int ty = 0; ty < g.nty; ++ty)
             for (int tx = 0; tx < g.ntx; ++tx) items.push_back({g.Dp, i, tx | (ty << 16)});
@@ -278,6 +278,17 @@ static void cache_store(const char *path, const std::string &key, int wc, int dc
     rename(tmp.c_str(), path);
 }
 
+// Reads and clears the device status word of every pair of the batch (synchronising the
+// capture stream first); true when none was set.
+static bool statuses_clear(stereo_batch *b)
+{
+    if (cudaStreamSynchronize(b->cap) != cudaSuccess) return false;
+    bool clear = true;
+    for (stereo_ctx *c : b->ctx)
+        if (stereo_check_device_status(c, nullptr) != STEREO_OK) clear = false;
+    return clear;
+}
+
 // Time the persistent fused launch of every candidate (tile shape, chunk size) on this
 // batch; keep the fastest.
 static int autotune(stereo_batch *b, int *wc_out, int *dc_out, int *source)
@@ -312,6 +323,10 @@ static int autotune(stereo_batch *b, int *wc_out, int *dc_out, int *source)
             best = std::min(best, ms);
         }
         if (rc) continue;
+        // a candidate whose bounded staging wait gave up returns early and would look fastest:
+        // read and clear every pair's status word, and drop the candidate if any was set (so
+        // it is neither chosen nor cached, and its status does not reach the first real run)
+        if (!statuses_clear(b)) continue;
         if (best < best_ms) {
             best_ms = best;
             best_wc = c[0];

@@ -23,10 +23,48 @@ constexpr size_t kNoAllocMoments = (size_t)kDtMaxBlocks * 10;
 static __device__ __align__(256) double g_dt_scratch[kNoAllocMoments + 8];
 static_assert(sizeof(stereo_dt_result) <= 6 * sizeof(double), "result slot too small");
 
-// Device address of g_dt_scratch per device, looked up once per device on first use.
+// Device address of g_dt_scratch, cached per device together with the unique id of the
+// context it was looked up in.  A context that is destroyed and re-created (cudaDeviceReset,
+// a reset of the primary context) reloads the library's module at a new address and gets a
+// new id (ids are never reused within a process), so a changed id forces a new lookup
+// instead of handing the kernels a stale address.  The two driver calls that read the id
+// are fetched through the runtime, so the library keeps no link-time dependency on libcuda.
 constexpr int kMaxDevices = 64;
+struct ScratchSlot {
+    unsigned long long ctx_id;   // 0: not looked up yet
+    void *ptr;
+};
 static std::mutex g_scratch_mu;
-static void *g_scratch_ptr[kMaxDevices];
+static ScratchSlot g_scratch[kMaxDevices];
+
+typedef int (*CtxGetCurrentFn)(void **ctx);
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
+
+// The current context's unique id, or 0 when it cannot be read (then every call looks the
+// address up again, which is always correct).
+static unsigned long long current_context_id()
+{
+    static std::once_flag once;
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+        cudaGetLastError();
+    });
+    if (!get_current || !get_id) return 0;
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
 
 static int scratch_for_current_device(void **out)
 {
@@ -35,15 +73,20 @@ static int scratch_for_current_device(void **out)
     if (rc) return rc;
     if (dev < 0 || dev >= kMaxDevices)
         return set_error(STEREO_ENOTSUP, "stereo_disparity_transform_noalloc: device %d beyond %d", dev, kMaxDevices);
+    // the id is read only once a lookup has run: cudaGetSymbolAddress makes the device's
+    // primary context current on the first call, so before it there may be no context to read
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
+    ScratchSlot &slot = g_scratch[dev];
+    unsigned long long id = slot.ctx_id ? current_context_id() : 0;
+    if (!slot.ctx_id || id == 0 || id != slot.ctx_id) {
         void *p = nullptr;
         rc = cuda_error(cudaGetSymbolAddress(&p, g_dt_scratch),
                         "stereo_disparity_transform_noalloc: cudaGetSymbolAddress");
         if (rc) return rc;
-        g_scratch_ptr[dev] = p;
+        slot.ptr = p;
+        slot.ctx_id = current_context_id();   // 0 when unreadable: look up again next call
     }
-    *out = g_scratch_ptr[dev];
+    *out = slot.ptr;
     return STEREO_OK;
 }
 

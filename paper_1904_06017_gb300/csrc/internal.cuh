@@ -84,6 +84,7 @@ struct stereo_ctx {
     float *dt_coef;                // 3 FP32 coefficients of the final per-pixel map
     stereo_dt_result *res_dev;     // device-side result when the caller passes none
     int *status_dev;               // device status word (bounded waits)
+    int stall_test;                // test hook of stereo_debug_stall_staging
     // LR-consistency check (stereo_create only; batch contexts leave them null)
     uint8_t *lr_ref, *lr_tgt;      // mirrored warped target and mirrored reference [H][pitch]
     int32_t *lr_wta;               // target-view WTA of the mirrored pair [H][W]

@@ -21,6 +21,7 @@ struct FusedArgs {
     uint8_t *valid;
     float *best2;       // optional [H][W][2]: normalised E at d* and the smallest E over d != d*
     int *status;
+    int stall_test;     // test hook: arm the staging barrier but issue no copy (the wait expires)
     int W, H, D, Dp, rw, m, n;
     int pad_left, pad_top, pad_w;
     int ref_e, tgt_e, ref_box_w, tgt_box_w, box_h, ref_box_x;
@@ -128,19 +129,29 @@ __device__ __forceinline__ const PairDesc *claim_tile(const PairDesc &single, co
 // Stages the reference tile and the warped-target strip of the tile at (x0, y0) into sref /
 // stgt with TMA; the mbarrier completes once per tile (phase iter & 1).  The wait is bounded
 // (about a second of clock cycles): false, with the status word set, when the copies did not
-// land.  The caller's barrier before this call orders the previous tile's shared-memory
-// accesses before the copies that overwrite the same bytes.
+// land.  That limit is a fail-safe that should never fire: when it does, the CTA returns and
+// its copies may still be in flight into its shared memory, and the launch's outputs are
+// invalid (the host reads the status word with stereo_check_device_status, which reports
+// STEREO_ETIMEOUT).  With the test hook stall_test set, thread 0 arms the barrier's
+// transaction count but issues no copy, so nothing is in flight when the wait expires (after
+// about a millisecond): the failure path then runs on purpose, without any fault.  The
+// caller's barrier before this call orders the previous tile's shared-memory accesses before
+// the copies that overwrite the same bytes.
 __device__ __forceinline__ bool stage_images(const PairDesc *pd, const FusedArgs &a, uint8_t *sref, uint8_t *stgt,
                                              uint64_t *bar, int *flag, int x0, int y0, int iter, int tid)
 {
     if (tid == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(bar, (uint32_t)(a.box_h * (a.ref_box_w + a.tgt_box_w)));
-        tma_load_3d(sref, &pd->tmap_ref, 0, (x0 + a.ref_box_x) / 16, y0, bar);
-        tma_load_3d(stgt, &pd->tmap_tgt, 0, x0 / 16, y0, bar);
+        const bool stall = a.stall_test != 0;
+        if (!stall) {
+            tma_load_3d(sref, &pd->tmap_ref, 0, (x0 + a.ref_box_x) / 16, y0, bar);
+            tma_load_3d(stgt, &pd->tmap_tgt, 0, x0 / 16, y0, bar);
+        }
+        const long long limit = stall ? (1ll << 21) : (1ll << 31);
         const long long t0 = clock64();
         bool ok = false;
-        while (!(ok = mbar_try_wait(bar, (uint32_t)(iter & 1))) && clock64() - t0 < (1ll << 31)) {
+        while (!(ok = mbar_try_wait(bar, (uint32_t)(iter & 1))) && clock64() - t0 < limit) {
         }
         *flag = ok ? 1 : 0;
         if (!ok) atomicOr(a.status, 1);

@@ -78,6 +78,7 @@ void fill_pair_desc(const stereo_ctx *ctx, float *disp, int32_t *wta, uint8_t *v
     a.valid = valid;
     a.best2 = best2;
     a.status = ctx->status_dev;
+    a.stall_test = ctx->stall_test;
     a.W = g.W;
     a.H = g.H;
     a.D = g.D;

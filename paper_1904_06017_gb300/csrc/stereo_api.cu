@@ -387,6 +387,13 @@ int stereo_check_device_status(stereo_ctx *ctx, stereo_stream_t stream)
     return STEREO_OK;
 }
 
+int stereo_debug_stall_staging(stereo_ctx *ctx, int32_t on)
+{
+    if (!ctx) return set_error(STEREO_EINVAL, "stereo_debug_stall_staging: null pointer");
+    ctx->stall_test = on ? 1 : 0;
+    return STEREO_OK;
+}
+
 int stereo_profile_enable(stereo_ctx *ctx, int32_t on)
 {
     if (!ctx) return set_error(STEREO_EINVAL, "stereo_profile_enable: null pointer");

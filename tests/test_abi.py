@@ -66,8 +66,10 @@ def test_struct_layout_matches_header(tmp_path):
 #include <stdio.h>
 #include "stereo.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(stereo_params), offsetof(stereo_params, lambda0),
-         offsetof(stereo_params, max_iters), sizeof(stereo_dt_result), offsetof(stereo_dt_result, n));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(stereo_params), offsetof(stereo_params, lambda0),
+         offsetof(stereo_params, max_iters), sizeof(stereo_dt_result), offsetof(stereo_dt_result, n),
+         sizeof(stereo_pair_desc), offsetof(stereo_pair_desc, psi_init), offsetof(stereo_pair_desc, delta_t),
+         offsetof(stereo_pair_desc, wta_dev));
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -76,7 +78,9 @@ int main(void) {
                                            check=True).stdout.split()]
     assert vals == [ctypes.sizeof(sg.stereo_params), sg.stereo_params.lambda0.offset,
                     sg.stereo_params.max_iters.offset, ctypes.sizeof(sg.stereo_dt_result),
-                    sg.stereo_dt_result.n.offset]
+                    sg.stereo_dt_result.n.offset, ctypes.sizeof(sg.stereo_pair_desc),
+                    sg.stereo_pair_desc.psi_init.offset, sg.stereo_pair_desc.delta_t.offset,
+                    sg.stereo_pair_desc.wta_dev.offset]
 
 
 def test_defaults_are_the_paper_constants(lib):
