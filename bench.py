@@ -34,7 +34,9 @@ SM_MAX_MHZ = 2070.0
 # DRAM traffic of one fused-kernel launch on this workload, from the ncu capture summarised
 # in profiles/ (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the kernel
 # source with this SHA-256 prefix.
-FUSED_TRAFFIC = {"sha256": "06f8b332a9877f95", "bytes": 39964160}
+FUSED_TRAFFIC = {"sha256": "a376bd7179bb2957", "bytes": 40092160}
+FUSED_SOURCES = ("internal.cuh", "k_fused_common.cuh", "k_cost.cuh", "k_fused_tc.cuh", "k_fused_sc.cuh",
+                 "k_fused_sc.cu")
 
 
 def parse():
@@ -69,7 +71,7 @@ def measured_peaks():
 
 def kernel_sha():
     h = hashlib.sha256()
-    for f in ("internal.cuh", "k_fused_common.cuh", "k_cost.cuh", "k_fused.cuh", "k_fused_f32.cu"):
+    for f in FUSED_SOURCES:
         h.update(open(os.path.join(ROOT, "paper_1904_06017_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -352,9 +354,11 @@ def bench_precision(args, dev, stream, flush, peak):
     n = max(3, min(args.steps, 20))
     rec = {"workload": "1920x1080 D=192 w=9 k=13 sigma0=3 sigma1=10", "flops_per_pixel_disparity": flops_per_unit}
     wta32 = None
-    for name, dtype in (("f32", sg.STEREO_F32), ("f16", sg.STEREO_F16), ("bf16", sg.STEREO_BF16)):
+    for name, dtype, form in (("f32", sg.STEREO_F32, sg.STEREO_FUSED_AUTO),
+                              ("f32_simt", sg.STEREO_F32, sg.STEREO_FUSED_SIMT),
+                              ("f16", sg.STEREO_F16, sg.STEREO_FUSED_AUTO), ("bf16", sg.STEREO_BF16, sg.STEREO_FUSED_AUTO)):
         sv = sg.Stereo(W, H, D, win=win, bil=bil, sigma0=p["sigma0"], sigma1=p["sigma1"], pitch=pitch,
-                       cost_dtype=dtype)
+                       cost_dtype=dtype, fused_form=form)
         wta = torch.empty((H, W), dtype=torch.int32, device=dev)
         sv.warp_target(tgt, shift, tw)
         sv.cost_aggregate_wta(ref, tw, shift, disp, wta, valid)
@@ -706,7 +710,9 @@ def run_ours(args):
     traffic = FUSED_TRAFFIC["bytes"] if FUSED_TRAFFIC["sha256"] == kernel_sha() else None
     probe_s, probe_p = sg.stereo_fp32_peak_probe(2)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": "k_fused (cost + bilateral aggregation + WTA + sub-pixel)",
+            "traffic": traffic,
+            "kernel": "k_fused_sc (cost + bilateral aggregation + WTA + sub-pixel: tensor-core screening with a "
+                      "certified bound, FP32 refinement; outputs bit for bit those of the SIMT FP32 kernel)",
             "flops_per_launch": agg_flops, "flops_per_pixel_disparity": flops_per_unit,
             "avg_launch_ms": fused_avg_ms, "launches": n_fused,
             "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal, derived)",
@@ -727,7 +733,8 @@ def run_ours(args):
             "frac": t_tf / peaks["bf16_tflops"] if peaks.get("bf16_tflops") else None,
             "peak_basis": "measured dense bf16 (same rate for fp16), MEASURED_PEAKS.json",
             "note": "the form is bound by weight generation and the integer cost phase, not the tensor pipe"}
-    variants["kernel"] = {"f32": "k_fused (FP32 weights and accumulators)",
+    variants["kernel"] = {"f32": "k_fused_sc (screened FP32 form; the default)",
+                          "f32_simt": "k_fused (the SIMT FP32 form: FP32 weights and accumulators on the CUDA cores)",
                           "f16": "k_fused_tc (tensor-core aggregation, FP32 accumulators)",
                           "bf16": "k_fused_tc (tensor-core aggregation, FP32 accumulators)"}
 

@@ -67,7 +67,24 @@ typedef struct {
     double lambda0;          /* initial rate of eq. (e_min_gd); paper: 10 (§4.4.2) */
     double delta_psi;        /* stop when |psi_k+1 - psi_k| < delta_psi; paper: pi/1.8e6 */
     int32_t max_iters;       /* cap on the roll iterations (default 100) */
+    int32_t fused_form;      /* which kernel runs cost + aggregation + WTA (not in the paper):
+                                STEREO_FUSED_AUTO (0, default), STEREO_FUSED_SIMT or
+                                STEREO_FUSED_TENSOR; see below */
 } stereo_params;
+
+/* stereo_params.fused_form.  Every form computes eq. (c), eq. (fbs), the WTA and eq. (subpixel).
+ *   STEREO_FUSED_SIMT    the aggregation in FP32 (or FP16 / BF16 storage with FP32 weights) on
+ *                        the CUDA cores, 64 x 36 tiles, 12 disparities per chunk.
+ *   STEREO_FUSED_TENSOR  FP32 storage: the screened form -- the aggregation screened on the
+ *                        tensor cores with a certified error bound, the certified candidates
+ *                        refined with the SIMT form's FP32 arithmetic; its outputs equal the SIMT
+ *                        form's bit for bit (bil <= 11).  FP16 / BF16 storage: the tensor-core
+ *                        aggregation of the 16-bit costs (bil <= 13, sigma1 <= 150).
+ *   STEREO_FUSED_AUTO    TENSOR where it applies, else SIMT.
+ * stereo_create returns STEREO_ENOTSUP when TENSOR is asked for and does not apply. */
+#define STEREO_FUSED_AUTO 0
+#define STEREO_FUSED_SIMT 1
+#define STEREO_FUSED_TENSOR 2
 
 /* Result of the disparity transformation (§3.3).  alpha0 is in raw pixel
  * coordinates, so the fitted road is alpha0 + alpha1 * (v cos psi - u sin psi). */
@@ -217,8 +234,10 @@ typedef struct {
                                   warps while consumer warps aggregate (FP32 storage, tile_dc 12,
                                   bil <= 11); 16: 64x36 tiles with the aggregation on the tensor cores
                                   (FP16 / BF16 storage, tile_dc 16, bil <= 13, sigma1 <= 150);
-                                  0 = autotune */
-    int32_t tile_dc;           /* disparities per chunk (12 or 4; 16 with tile_wc 16); 0 = autotune */
+                                  32: the screened FP32 form on 32x36 tiles (FP32 storage, tile_dc
+                                  32, bil <= 11; see stereo_params.fused_form); 0 = autotune */
+    int32_t tile_dc;           /* disparities per chunk (12 or 4; 16 with tile_wc 16; 32 with
+                                  tile_wc 32); 0 = autotune */
 } stereo_batch_params;
 
 typedef struct stereo_batch stereo_batch;

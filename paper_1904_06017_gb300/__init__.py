@@ -29,6 +29,7 @@ __all__ = [
     "stereo_batch_check_device_status", "stereo_batch_destroy", "StereoBatch",
     "STEREO_OK", "STEREO_EINVAL", "STEREO_ENOMEM", "STEREO_ECUDA", "STEREO_ETIMEOUT",
     "STEREO_ENOCONV", "STEREO_ENOTSUP", "STEREO_F32", "STEREO_F16", "STEREO_BF16",
+    "STEREO_FUSED_AUTO", "STEREO_FUSED_SIMT", "STEREO_FUSED_TENSOR",
 ]
 
 STEREO_OK = 0
@@ -39,6 +40,7 @@ STEREO_ETIMEOUT = -4
 STEREO_ENOCONV = -5
 STEREO_ENOTSUP = -6
 STEREO_F32, STEREO_F16, STEREO_BF16 = 0, 1, 2
+STEREO_FUSED_AUTO, STEREO_FUSED_SIMT, STEREO_FUSED_TENSOR = 0, 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_lib", "libstereo_gb300.so")
@@ -56,7 +58,7 @@ class stereo_params(ctypes.Structure):
                 ("max_disp", ctypes.c_int32), ("win", ctypes.c_int32), ("bil", ctypes.c_int32),
                 ("sigma0", ctypes.c_float), ("sigma1", ctypes.c_float),
                 ("cost_dtype", ctypes.c_int32), ("lambda0", ctypes.c_double),
-                ("delta_psi", ctypes.c_double), ("max_iters", ctypes.c_int32)]
+                ("delta_psi", ctypes.c_double), ("max_iters", ctypes.c_int32), ("fused_form", ctypes.c_int32)]
 
 
 class stereo_dt_result(ctypes.Structure):

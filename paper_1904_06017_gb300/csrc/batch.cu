@@ -152,7 +152,7 @@ static int enqueue_pre_pair(stereo_batch *b, size_t i, cudaStream_t s)
     const stereo_pair_desc &d = b->pairs[i];
     int rc = launch_warp(b->ctx[i], d.tgt_dev, d.shift_dev, d.tgt_warped_dev, s);
     if (!rc) rc = launch_prep(b->ctx[i], d.ref_dev, d.tgt_warped_dev, s);
-    if (!rc) rc = launch_row_tables(b->ctx[i], d.shift_dev, s);
+    if (!rc) rc = launch_row_tables(b->ctx[i], d.shift_dev, d.tgt_warped_dev, s);
     return rc;
 }
 
@@ -300,7 +300,7 @@ static int autotune(stereo_batch *b, int *wc_out, int *dc_out, int *source)
         *source = 1;
         return STEREO_OK;
     }
-    const int cand[][2] = {{kTcWC, 16}, {kWsWC, 12}, {2, 12}, {1, 12}, {4, 12}, {2, 4}};
+    const int cand[][2] = {{kScWC, 32}, {kTcWC, 16}, {kWsWC, 12}, {2, 12}, {1, 12}, {4, 12}, {2, 4}};
     double best_ms = 1e30;
     int best_wc = 0, best_dc = 0;
     cudaEvent_t e0, e1;
@@ -373,9 +373,12 @@ int stereo_batch_create(const stereo_batch_params *p, int32_t n, const stereo_pa
     *out = nullptr;
     if (n < 1 || n > 4096) return set_error(STEREO_EINVAL, "stereo_batch_create: n = %d outside 1..4096", n);
     if ((p->tile_wc && p->tile_wc != 1 && p->tile_wc != 2 && p->tile_wc != 4 && p->tile_wc != kWsWC &&
-         p->tile_wc != kTcWC) ||
-        (p->tile_dc && p->tile_dc != 4 && p->tile_dc != 12 && p->tile_dc != 16))
-        return set_error(STEREO_EINVAL, "stereo_batch_create: tile_wc must be 0, 1, 2, 4, 8 or 16 and tile_dc 0, 4, 12 or 16");
+         p->tile_wc != kTcWC && p->tile_wc != kScWC) ||
+        (p->tile_dc && p->tile_dc != 4 && p->tile_dc != 12 && p->tile_dc != 16 && p->tile_dc != 32))
+        return set_error(STEREO_EINVAL,
+                         "stereo_batch_create: tile_wc must be 0, 1, 2, 4, 8, 16 or 32 and tile_dc 0, 4, 12, 16 or 32");
+    if (p->tile_wc == kScWC && (p->cost_dtype != STEREO_F32 || p->bil / 2 > kScMaxRB))
+        return set_error(STEREO_ENOTSUP, "stereo_batch_create: tile_wc 32 needs FP32 storage and bil <= 11");
     if (p->tile_wc == kTcWC && !tc_supported(p->cost_dtype, p->bil, p->sigma1))
         return set_error(STEREO_ENOTSUP, "stereo_batch_create: tile_wc 16 needs FP16 / BF16 storage, bil <= 13 and sigma1 <= 150");
     for (int i = 0; i < n; ++i) {

@@ -34,10 +34,18 @@ constexpr int kWsMaxRB = 5;         // the two cost buffers fit shared memory up
 constexpr int kTcWC = 16;
 constexpr int kTcMaxRB = 6;
 constexpr float kTcMaxSigma1 = 150.f;   // -s^2 stays a normal FP16 number
-__host__ __device__ constexpr int tile_x(int wc) { return wc == kWsWC || wc == kTcWC ? 64 : 32 * wc; }
+// The screened FP32 form (tile code kScWC): 32 x 36 tiles, kWarps warps, tensor-core screening
+// over 32 disparities per chunk and an exact FP32 refinement of the certified candidates
+// (k_fused_sc.cuh); bil <= 11.
+constexpr int kScWC = 32;
+constexpr int kScMaxRB = 5;
+__host__ __device__ constexpr int tile_x(int wc)
+{
+    return wc == kWsWC || wc == kTcWC ? 64 : wc == kScWC ? 32 : 32 * wc;
+}
 __host__ __device__ constexpr int tile_y(int wc)
 {
-    return wc == kWsWC ? kWsPY * (kWsConsWarps / 2) : wc == kTcWC ? 36 : kPY * (kWarps / wc);
+    return wc == kWsWC ? kWsPY * (kWsConsWarps / 2) : wc == kTcWC || wc == kScWC ? 36 : kPY * (kWarps / wc);
 }
 // Whether the tensor-core form can run these parameters.
 inline bool tc_supported(int cost_dtype, int bil, float sigma1)
@@ -76,7 +84,8 @@ struct stereo_ctx {
     int device;
     uint8_t *ref_pad, *tgt_pad;    // replicate-padded copies (pad_pitch x pad_h)
     int2 *ref_stats, *tgt_stats;   // per padded position: {sum, bits of 1/sqrt(n*sumsq - sum^2)}
-    int4 *row_tab;                 // per image row: {s_i(v), max and min of s_i over rows v-m..v+m, 0}
+    int4 *row_tab;                 // per image row: {s_i(v), max and min of s_i over rows v-m..v+m,
+                                   //   min over those rows of the target's column-0 run length}
     CUtensorMap tmap_ref, tmap_tgt;
     float kspatial[(2 * sgb::kMaxRB + 1) * (2 * sgb::kMaxRB + 1)];  // -log2(e) |dq|^2 / sigma0^2
     float iscale;                  // sqrt(log2(e)) / sigma1
@@ -104,7 +113,7 @@ int cuda_error(cudaError_t e, const char *what);
 int launch_warp(stereo_ctx *ctx, const uint8_t *tgt, const float *shift, uint8_t *out,
                 cudaStream_t s);
 int launch_prep(stereo_ctx *ctx, const uint8_t *ref, const uint8_t *tgtw, cudaStream_t s);
-int launch_row_tables(stereo_ctx *ctx, const float *shift, cudaStream_t s);
+int launch_row_tables(stereo_ctx *ctx, const float *shift, const uint8_t *tgtw, cudaStream_t s);
 int launch_fused(stereo_ctx *ctx, const float *shift, float *disp, int32_t *wta, uint8_t *valid,
                  cudaStream_t s, float *best2 = nullptr);
 size_t fused_smem_bytes(const Geometry &g);

@@ -9,6 +9,15 @@
 
 namespace sgb {
 
+// One cost rounded to the storage type.
+template <typename T> __device__ __forceinline__ T cost_from_float(float c);
+template <> __device__ __forceinline__ float cost_from_float<float>(float c) { return c; }
+template <> __device__ __forceinline__ __half cost_from_float<__half>(float c) { return __float2half_rn(c); }
+template <> __device__ __forceinline__ __nv_bfloat16 cost_from_float<__nv_bfloat16>(float c)
+{
+    return __float2bfloat16_rn(c);
+}
+
 // Calls f(std::integral_constant<int, i>) for i = 0 .. N-1 (compile-time loop).
 template <typename F, int... I>
 __device__ __forceinline__ void static_for_impl(F &&f, std::integer_sequence<int, I...>)
@@ -38,8 +47,22 @@ __device__ __forceinline__ void group_sync()
     else asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NT) : "memory");
 }
 
+// SWZ: the DC disparities of a position are stored as DC / 8 16-byte units whose index is XORed
+// with a function of the column (the tensor-core aggregations' ldmatrix layouts): for DC = 16
+// unit ^ bit 2 of the column, for DC = 32 unit ^ bits 1..2 of the column (sc_unit below).
+// CSH: the costs are stored multiplied by 2^CSH (exactly: the power of two is folded into the
+// reciprocal and the constant of eq. (c), so the scaled value is the same rounding of the same
+// exact product).  PLW > 0: planar storage, one plane per disparity, rows of PLW entries and
+// planes PSZ entries apart (cbuf[d * PSZ + y * PLW + x]), for per-pixel gathers whose lanes need
+// different disparities.
+template <int DC>
+__host__ __device__ constexpr int swz_unit(int unit, int x)
+{
+    return DC == 16 ? unit ^ ((x >> 2) & 1) : unit ^ ((x >> 1) & 3);
+}
+
 template <int RB, int DC, int RW, typename T, int TX, int TY, int NT = kThreads, int BAR = 0,
-          int KBAND = kBand, bool SWZ = false>
+          int KBAND = kBand, bool SWZ = false, int CSH = 0, int PLW = 0, int PSZ = 0>
 __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sref, const uint8_t *stgt,
                                            T *cbuf, int *vband, int2 *sstr, int2 *sstt,
                                            int x0, int y0, int d0, int tid)
@@ -201,6 +224,7 @@ __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sr
             for (int j = 0; j < kSeg; ++j) rs[j] = (j < nout) ? rsr[xs + j] : make_int2(0, 0);
 #pragma unroll
             for (int j = 0; j < kSeg + 3; ++j) ts[j] = (j < nout + 3) ? tsr[xs + j - 3] : make_int2(0, 0);
+            constexpr float CS = (float)(1 << CSH);
             float4 out[kSeg];
             int4 S = make_int4(0, 0, 0, 0);
 #pragma unroll
@@ -212,12 +236,12 @@ __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sr
             }
 #pragma unroll
             for (int j = 0; j < kSeg; ++j) {
-                const float ir = __int_as_float(rs[j].y);
+                const float ir = __int_as_float(rs[j].y) * CS;
                 const int2 t0 = ts[j + 3], t1 = ts[j + 2], t2 = ts[j + 1], t3 = ts[j];
-                out[j].x = fmaf(-(float)(a.n * S.x - rs[j].x * t0.x), ir * __int_as_float(t0.y), 1.0f);
-                out[j].y = fmaf(-(float)(a.n * S.y - rs[j].x * t1.x), ir * __int_as_float(t1.y), 1.0f);
-                out[j].z = fmaf(-(float)(a.n * S.z - rs[j].x * t2.x), ir * __int_as_float(t2.y), 1.0f);
-                out[j].w = fmaf(-(float)(a.n * S.w - rs[j].x * t3.x), ir * __int_as_float(t3.y), 1.0f);
+                out[j].x = fmaf(-(float)(a.n * S.x - rs[j].x * t0.x), ir * __int_as_float(t0.y), CS);
+                out[j].y = fmaf(-(float)(a.n * S.y - rs[j].x * t1.x), ir * __int_as_float(t1.y), CS);
+                out[j].z = fmaf(-(float)(a.n * S.z - rs[j].x * t2.x), ir * __int_as_float(t2.y), CS);
+                out[j].w = fmaf(-(float)(a.n * S.w - rs[j].x * t3.x), ir * __int_as_float(t3.y), CS);
                 if (j + 1 < kSeg) {
                     S.x += v[j + WS].x - v[j].x;
                     S.y += v[j + WS].y - v[j].y;
@@ -226,15 +250,26 @@ __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sr
                 }
             }
             if constexpr (SWZ) {
-                // 16 disparities per position as two 16-byte halves, the half index XORed with
-                // bit 2 of the column (the tensor-core aggregation's ldmatrix layout)
-                static_assert(DC == 16, "the swizzled layout holds 16 disparities per position");
+                // DC / 8 16-byte units per position, the unit index swizzled by the column
+                static_assert(DC == 16 || DC == 32, "swizzled layouts hold 16 or 32 disparities per position");
                 T *co = cbuf + (size_t)yq * crow + 4 * (dq & 1);
 #pragma unroll
                 for (int j = 0; j < kSeg; ++j) {
                     const int x = xs + j;
-                    if (j < nout) CostStore<T>::store4(co + (size_t)x * DC + ((((dq >> 1) ^ (x >> 2)) & 1) << 3), out[j]);
+                    if (j < nout) CostStore<T>::store4(co + (size_t)x * DC + (swz_unit<DC>(dq >> 1, x) << 3), out[j]);
                 }
+            } else if constexpr (PLW > 0) {
+                static_assert(PSZ >= QH * PLW, "planes must not overlap");
+                T *co = cbuf + (size_t)(4 * dq) * PSZ + (size_t)yq * PLW;
+#pragma unroll
+                for (int j = 0; j < kSeg; ++j)
+                    if (j < nout) {
+                        const int x = xs + j;
+                        co[x] = cost_from_float<T>(out[j].x);
+                        co[PSZ + x] = cost_from_float<T>(out[j].y);
+                        co[2 * PSZ + x] = cost_from_float<T>(out[j].z);
+                        co[3 * PSZ + x] = cost_from_float<T>(out[j].w);
+                    }
             } else {
                 T *co = cbuf + (size_t)yq * crow + 4 * dq;
 #pragma unroll
@@ -269,13 +304,6 @@ __device__ __forceinline__ uint32_t u8pair_h2(const uint8_t *p)
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-template <typename T> __device__ __forceinline__ T cost_from_float(float c);
-template <> __device__ __forceinline__ float cost_from_float<float>(float c) { return c; }
-template <> __device__ __forceinline__ __half cost_from_float<__half>(float c) { return __float2half_rn(c); }
-template <> __device__ __forceinline__ __nv_bfloat16 cost_from_float<__nv_bfloat16>(float c)
-{
-    return __float2bfloat16_rn(c);
-}
 
 // The costs of one chunk of DC <= 16 disparities at the tile plus its bilateral halo (QH x QW
 // positions), eq. (c), with the cross term S = sum_block I_ref(q) I_tar(q - d) on the tensor

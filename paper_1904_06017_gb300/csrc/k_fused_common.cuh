@@ -254,6 +254,8 @@ FusedKernel pick_fused_f16(int rb, int dc, int wc);    // k_fused_f16.cu: WC = 2
 FusedKernel pick_fused_bf16(int rb, int dc, int wc);   // k_fused_bf16.cu: WC = 2, DC = 12
 FusedKernel pick_fused_ws(int rb, int dc);             // k_fused_ws.cu: warp-specialised, FP32, DC = 12
 FusedKernel pick_fused_tc(int cost_dtype, int rb);     // k_fused_tc_{f16,bf16}.cu: tensor-core aggregation, DC = 16
+FusedKernel pick_fused_sc(int rb);                     // k_fused_sc.cu: screened FP32 form, tile code kScWC
+FusedKernel pick_fused_sc_b2(int rb);                  // k_fused_sc_b2.cu: the same with the best2 output
 FusedKernel pick_fused(int cost_dtype, int rb, int dc, int wc);
 // The instantiation with the best2 output (FP32 storage at WC = 2 with DC = 12, and the
 // tensor-core form); nullptr where there is none.  k_fused_b2_f32.cu, k_fused_tc_{f16,bf16}_b2.cu.

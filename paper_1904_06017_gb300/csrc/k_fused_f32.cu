@@ -3,7 +3,7 @@
 #include <string.h>
 
 #include "k_fused.cuh"
-#include "k_fused_tc.cuh"
+#include "k_fused_sc.cuh"
 
 namespace sgb {
 
@@ -19,6 +19,7 @@ FusedKernel pick_fused(int cost_dtype, int rb, int dc, int wc)
 {
     if (wc == kWsWC) return cost_dtype == STEREO_F32 && rb <= kWsMaxRB ? pick_fused_ws(rb, dc) : nullptr;
     if (wc == kTcWC) return dc == kTcDC && rb <= kTcMaxRB ? pick_fused_tc(cost_dtype, rb) : nullptr;
+    if (wc == kScWC) return cost_dtype == STEREO_F32 && dc == kScDC ? pick_fused_sc(rb) : nullptr;
     switch (cost_dtype) {
     case STEREO_F32: return pick_fused_f32(rb, dc, wc);
     case STEREO_F16: return pick_fused_f16(rb, dc, wc);
@@ -30,6 +31,7 @@ FusedKernel pick_fused(int cost_dtype, int rb, int dc, int wc)
 size_t fused_smem_bytes(const Geometry &g)
 {
     if (g.wc == kTcWC) return tc_layout(g.rb, g.m, g.ref_box_w, g.tgt_box_w, g.box_h, g.esize).total;
+    if (g.wc == kScWC) return sc_layout(g.rb, g.m, g.ref_box_w, g.tgt_box_w, g.box_h).total;
     // the warp-specialised form keeps the two-pass cost phase (vband, staged statistics); the
     // others compute costs on the tensor cores and need neither
     const bool ws = g.wc == kWsWC;
@@ -107,8 +109,8 @@ int launch_fused(stereo_ctx *ctx, const float *shift, float *disp, int32_t *wta,
     const Geometry &g = ctx->g;
     FusedKernel k = best2 ? pick_fused_b2(ctx->p.cost_dtype, g.rb, g.dc, g.wc) : pick(ctx);
     if (!k)
-        return set_error(STEREO_ENOTSUP, best2 ? "the best2 output needs FP32 storage with 12 disparities per chunk or "
-                                                 "the tensor-core form (FP16 / BF16 with bil <= 13)"
+        return set_error(STEREO_ENOTSUP, best2 ? "the best2 output needs FP32 storage (the screened form or 12 "
+                                                 "disparities per chunk) or the tensor-core form (FP16 / BF16 with bil <= 13)"
                                                : "no fused kernel for bil=%d",
                          ctx->p.bil);
     PairDesc d;

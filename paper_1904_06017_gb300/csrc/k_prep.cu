@@ -177,39 +177,53 @@ int launch_prep(stereo_ctx *ctx, const uint8_t *ref, const uint8_t *tgtw, cudaSt
     return cuda_error(cudaGetLastError(), "k_prep launch");
 }
 
-// Per image row v: the integer shift s_i(v) = floor(s(v) + 0.5) of §3.1, and the largest and
-// smallest s_i over rows v-m..v+m (the validity test of the fused epilogue).  A block of
-// kRowTab rows first rounds its rows and an m-row halo on each side once, then takes the window
-// extremes from shared memory.
+// Per image row v: the integer shift s_i(v) = floor(s(v) + 0.5) of §3.1, the largest and
+// smallest s_i over rows v-m..v+m (the validity test of the fused epilogue), and the smallest
+// over those rows of L(y), the length of the run of target row y that equals its column 0 (at
+// least 1; W when the whole row is one value).  The replicate padding extends that run to the
+// left, so a read of row y at any column below L(y) returns the value of column 0: the
+// screened fused form uses this to find the disparities beyond which every cost behind a
+// pixel no longer changes.  A block of kRowTab rows first rounds its rows and an m-row halo
+// on each side once (and measures their runs), then takes the window extremes from shared
+// memory.
 constexpr int kRowTab = 128, kRowTabHalo = 16;   // m = rw + bilateral radius <= 12
 
-__global__ void __launch_bounds__(kRowTab) k_row_tables(const float *__restrict__ shift, int H, int m,
-                                                        int4 *__restrict__ tab)
+__global__ void __launch_bounds__(kRowTab) k_row_tables(const float *__restrict__ shift, const uint8_t *__restrict__ tgt,
+                                                        int pitch, int W, int H, int m, int4 *__restrict__ tab)
 {
     __shared__ int si[kRowTab + 2 * kRowTabHalo];
+    __shared__ int li[kRowTab + 2 * kRowTabHalo];
     const int v0 = blockIdx.x * kRowTab;
     for (int i = threadIdx.x; i < kRowTab + 2 * m; i += kRowTab) {
         const int y = v0 - m + i;
+        int run = 1;
+        if (y >= 0 && y < H) {
+            const uint8_t *row = tgt + (size_t)y * pitch;
+            const uint8_t c0 = __ldg(row);
+            while (run < W && __ldg(row + run) == c0) ++run;
+        }
         si[i] = (y >= 0 && y < H) ? (int)round_half_up(__ldg(shift + y)) : 0;
+        li[i] = run;
     }
     __syncthreads();
     const int v = v0 + threadIdx.x;
     if (v >= H) return;
-    int hi = -(1 << 30), lo = 1 << 30;
+    int hi = -(1 << 30), lo = 1 << 30, lmin = 1 << 30;
     const int ylo = max(v - m, 0), yhi = min(v + m, H - 1);
     for (int y = ylo; y <= yhi; ++y) {
         const int s = si[y - v0 + m];
         hi = max(hi, s);
         lo = min(lo, s);
+        lmin = min(lmin, li[y - v0 + m]);
     }
-    tab[v] = make_int4(si[threadIdx.x + m], hi, lo, 0);
+    tab[v] = make_int4(si[threadIdx.x + m], hi, lo, lmin);
 }
 
-int launch_row_tables(stereo_ctx *ctx, const float *shift, cudaStream_t s)
+int launch_row_tables(stereo_ctx *ctx, const float *shift, const uint8_t *tgtw, cudaStream_t s)
 {
     const Geometry &g = ctx->g;
     if (g.m > kRowTabHalo) return set_error(STEREO_EINVAL, "k_row_tables: halo %d above %d", g.m, kRowTabHalo);
-    k_row_tables<<<(g.H + kRowTab - 1) / kRowTab, kRowTab, 0, s>>>(shift, g.H, g.m, ctx->row_tab);
+    k_row_tables<<<(g.H + kRowTab - 1) / kRowTab, kRowTab, 0, s>>>(shift, tgtw, g.pitch, g.W, g.H, g.m, ctx->row_tab);
     return cuda_error(cudaGetLastError(), "k_row_tables launch");
 }
 

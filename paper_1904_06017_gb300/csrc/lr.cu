@@ -64,7 +64,7 @@ extern "C" int stereo_lr_check(stereo_ctx *ctx, const uint8_t *ref, const uint8_
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "stereo_lr_check: mirror");
     int rc = launch_prep(ctx, ctx->lr_ref, ctx->lr_tgt, s);
-    if (!rc) rc = launch_row_tables(ctx, shift, s);
+    if (!rc) rc = launch_row_tables(ctx, shift, ctx->lr_tgt, s);
     if (!rc) rc = launch_fused(ctx, shift, ctx->lr_disp, ctx->lr_wta, nullptr, s);
     if (rc) return rc;
     k_lr_check<<<grid, 256, 0, s>>>(wta_ref, ctx->lr_wta, wta_tgt, lr_ok, W, delta_r);

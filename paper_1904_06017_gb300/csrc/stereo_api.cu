@@ -47,7 +47,9 @@ int compute_geometry(const stereo_params &p, int dc, int wc, Geometry &g)
     g.tx = tile_x(wc);
     g.ty = tile_y(wc);
     g.esize = p.cost_dtype == STEREO_F32 ? 4 : 2;
-    g.Dp = round_up(g.D, dc);
+    // the screened form's FP32 refinement computes 16 disparities from any start d <= D - 1,
+    // so its target strip holds 16 disparities beyond the last screening chunk
+    g.Dp = wc == kScWC ? round_up(g.D, dc) + 16 : round_up(g.D, dc);
     g.ntx = (g.W + g.tx - 1) / g.tx;
     g.nty = (g.H + g.ty - 1) / g.ty;
     g.pad_left = round_up(g.m + g.Dp - 1, 16);
@@ -196,6 +198,8 @@ int create_context(const stereo_params *p, int force_dc, int force_wc, stereo_ct
         return set_error(STEREO_EINVAL, "stereo_create: sigma0, sigma1 must be positive and finite");
     if (p->cost_dtype != STEREO_F32 && p->cost_dtype != STEREO_F16 && p->cost_dtype != STEREO_BF16)
         return set_error(STEREO_EINVAL, "stereo_create: unknown cost_dtype %d", p->cost_dtype);
+    if (p->fused_form < STEREO_FUSED_AUTO || p->fused_form > STEREO_FUSED_TENSOR)
+        return set_error(STEREO_EINVAL, "stereo_create: fused_form %d outside 0..2", p->fused_form);
     if (!(p->lambda0 > 0.0) || !(p->delta_psi > 0.0) || p->max_iters < 1 || p->max_iters > 100000)
         return set_error(STEREO_EINVAL, "stereo_create: lambda0, delta_psi must be > 0 and max_iters in 1..100000");
 
@@ -207,13 +211,22 @@ int create_context(const stereo_params *p, int force_dc, int force_wc, stereo_ct
         free_ctx(c);
         return cuda_error(cudaErrorNoDevice, "stereo_create: no CUDA device");
     }
-    // FP16 / BF16 storage: the tensor-core form (16 disparities per chunk) where it applies;
-    // otherwise 12 disparities per chunk when the fused kernel's shared memory allows it, else 4
+    // The fused form (stereo_params.fused_form): FP16 / BF16 storage takes the tensor-core form
+    // (16 disparities per chunk) where it applies, FP32 storage the screened form (32 per
+    // chunk); otherwise the SIMT form with 12 disparities per chunk when its shared memory
+    // allows it, else 4
     const int smem_max = max_smem_optin() - kFusedStaticSmem;
-    const bool tc = !force_wc && !force_dc && tc_supported(p->cost_dtype, p->bil, p->sigma1);
-    const int wc = force_wc ? force_wc : tc ? kTcWC : kDefaultWC;
-    compute_geometry(*p, force_dc ? force_dc : tc ? 16 : 12, wc, c->g);
-    if (tc && (int)c->g.smem_bytes > smem_max) compute_geometry(*p, 12, kDefaultWC, c->g);
+    const bool want_tensor = p->fused_form != STEREO_FUSED_SIMT;
+    const bool tc = !force_wc && !force_dc && want_tensor && tc_supported(p->cost_dtype, p->bil, p->sigma1);
+    const bool sc = !force_wc && !force_dc && want_tensor && p->cost_dtype == STEREO_F32 && p->bil / 2 <= kScMaxRB;
+    if (p->fused_form == STEREO_FUSED_TENSOR && !force_wc && !tc && !sc) {
+        free_ctx(c);
+        return set_error(STEREO_ENOTSUP, "stereo_create: no tensor-core form for cost_dtype %d, bil %d, sigma1 %g",
+                         p->cost_dtype, p->bil, (double)p->sigma1);
+    }
+    const int wc = force_wc ? force_wc : tc ? kTcWC : sc ? kScWC : kDefaultWC;
+    compute_geometry(*p, force_dc ? force_dc : tc ? 16 : sc ? 32 : 12, wc, c->g);
+    if ((tc || sc) && (int)c->g.smem_bytes > smem_max) compute_geometry(*p, 12, kDefaultWC, c->g);
     if (!force_dc && c->g.wc != kTcWC && (int)c->g.smem_bytes > smem_max) compute_geometry(*p, 4, c->g.wc, c->g);
     if ((int)c->g.smem_bytes > smem_max) {
         free_ctx(c);
@@ -306,7 +319,7 @@ int stereo_cost_aggregate_wta_ex(stereo_ctx *ctx, const uint8_t *ref, const uint
         return set_error(STEREO_EINVAL, "stereo_cost_aggregate_wta: null pointer");
     cudaStream_t s = (cudaStream_t)stream;
     int rc = launch_prep(ctx, ref, tgtw, s);
-    if (!rc) rc = launch_row_tables(ctx, shift, s);
+    if (!rc) rc = launch_row_tables(ctx, shift, tgtw, s);
     if (rc) return rc;
     int slot = -1;
     if (ctx->prof_on && ctx->prof_n < kProfSlots) {

@@ -177,7 +177,7 @@ extern "C" int stereo_warp_est_run(stereo_warp_est *e, const uint8_t *ref, const
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return cuda_error(err, who);
     int rc = launch_prep(e->cc, e->ref_c, e->tgt_c, s);
-    if (!rc) rc = launch_row_tables(e->cc, e->zero_shift, s);
+    if (!rc) rc = launch_row_tables(e->cc, e->zero_shift, e->tgt_c, s);
     if (!rc) rc = launch_fused(e->cc, e->zero_shift, e->disp_c, nullptr, e->valid_c, s);
     if (rc) return rc;
     k_fit_partials<<<kFitBlocks, 256, 0, s>>>(e->disp_c, e->valid_c, e->Wc, e->Hc, e->F, e->part);
