@@ -354,11 +354,9 @@ def bench_precision(args, dev, stream, flush, peak):
     n = max(3, min(args.steps, 20))
     rec = {"workload": "1920x1080 D=192 w=9 k=13 sigma0=3 sigma1=10", "flops_per_pixel_disparity": flops_per_unit}
     wta32 = None
-    for name, dtype, form in (("f32", sg.STEREO_F32, sg.STEREO_FUSED_AUTO),
-                              ("f32_simt", sg.STEREO_F32, sg.STEREO_FUSED_SIMT),
-                              ("f16", sg.STEREO_F16, sg.STEREO_FUSED_AUTO), ("bf16", sg.STEREO_BF16, sg.STEREO_FUSED_AUTO)):
+    for name, dtype in (("f32", sg.STEREO_F32), ("f16", sg.STEREO_F16), ("bf16", sg.STEREO_BF16)):
         sv = sg.Stereo(W, H, D, win=win, bil=bil, sigma0=p["sigma0"], sigma1=p["sigma1"], pitch=pitch,
-                       cost_dtype=dtype, fused_form=form)
+                       cost_dtype=dtype)
         wta = torch.empty((H, W), dtype=torch.int32, device=dev)
         sv.warp_target(tgt, shift, tw)
         sv.cost_aggregate_wta(ref, tw, shift, disp, wta, valid)
@@ -645,9 +643,11 @@ def run_ours(args):
     variants = {}
     wta_ref = None
     nvar = max(3, min(args.steps, 50))
-    for name, dtype in (("f32", sg.STEREO_F32), ("f16", sg.STEREO_F16), ("bf16", sg.STEREO_BF16)):
+    for name, dtype, form in (("f32", sg.STEREO_F32, sg.STEREO_FUSED_AUTO),
+                              ("f32_simt", sg.STEREO_F32, sg.STEREO_FUSED_SIMT),
+                              ("f16", sg.STEREO_F16, sg.STEREO_FUSED_AUTO), ("bf16", sg.STEREO_BF16, sg.STEREO_FUSED_AUTO)):
         sv = sg.Stereo(W, H, D, win=win, bil=bil, sigma0=p["sigma0"], sigma1=p["sigma1"], pitch=pitch,
-                       cost_dtype=dtype)
+                       cost_dtype=dtype, fused_form=form)
         wta_v = torch.empty((H, W), dtype=torch.int32, device=dev)
         sv.warp_target(tgt, shift, tw)
         sv.cost_aggregate_wta(ref, tw, shift, disp, wta_v, valid)

@@ -54,7 +54,7 @@ __device__ __forceinline__ void group_sync()
 // reciprocal and the constant of eq. (c), so the scaled value is the same rounding of the same
 // exact product).  PLW > 0: planar storage, one plane per disparity, rows of PLW entries and
 // planes PSZ entries apart (cbuf[d * PSZ + y * PLW + x]), for per-pixel gathers whose lanes need
-// different disparities.
+// different disparities.  KSEG: cost columns per work item of the horizontal pass.
 template <int DC>
 __host__ __device__ constexpr int swz_unit(int unit, int x)
 {
@@ -62,12 +62,12 @@ __host__ __device__ constexpr int swz_unit(int unit, int x)
 }
 
 template <int RB, int DC, int RW, typename T, int TX, int TY, int NT = kThreads, int BAR = 0,
-          int KBAND = kBand, bool SWZ = false, int CSH = 0, int PLW = 0, int PSZ = 0>
+          int KBAND = kBand, bool SWZ = false, int CSH = 0, int PLW = 0, int PSZ = 0, int KSEG = kSeg>
 __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sref, const uint8_t *stgt,
                                            T *cbuf, int *vband, int2 *sstr, int2 *sstt,
                                            int x0, int y0, int d0, int tid)
 {
-    constexpr int kThreads = NT, kBand = KBAND;      // the threads and band of this instantiation
+    constexpr int kThreads = NT, kBand = KBAND, kSeg = KSEG;   // the threads, band and segment of this instantiation
     constexpr int WS = 2 * RW + 1;                    // block size w
     constexpr int QH = TY + 2 * RB, QW = TX + 2 * RB;
     constexpr int CW = TX + 2 * (RW + RB);            // product columns

@@ -34,6 +34,7 @@ namespace sgb {
 constexpr int kScDC = 32;       // disparities per screening chunk
 constexpr int kScDCR = 8;       // disparities per FP32 refinement chunk
 constexpr int kScBand = 6;      // cost rows per band of the screening chunk's cost phase
+constexpr int kScSeg = 6;       // cost columns per horizontal work item (6 rows x 7 segments x 8 quads = 336 items)
 constexpr int kScQWI = 44;      // row length of the staged FP32 intensities (>= QW, >= 28 + 16)
 // Refinement planes: rows of kScRPW entries (8 mod 32) and planes a multiple of 32 entries
 // apart, so that the warp's 8 x 4 pixels read 32 distinct banks whatever disparity each needs
@@ -46,7 +47,8 @@ constexpr float kScAbs = 64.f;  // in the scaled units of E16 (2^20 x E32)
 // (1 + eps) / (1 - eps), rounded up
 constexpr float kScRho = (1.0f + kScEps) / (1.0f - kScEps) + 1e-6f;
 
-constexpr int kScRefOff = 16384;   // bytes into escr: past the refinement's window sums (<= 10 KB)
+constexpr int kScRefOff = 16384;     // bytes into escr: past the refinement's window sums (<= 10 KB)
+constexpr int kScRangeOff = 32768;   // bytes into escr: the per-pixel candidate ranges (int2 [36][32])
 
 __device__ __forceinline__ float sc_thr(float m) { return fmaf(m + kScAbs, kScRho, kScAbs); }
 
@@ -56,14 +58,15 @@ __device__ __forceinline__ float sc_thr(float m) { return fmaf(m + kScAbs, kScRh
 //          column); refinement: 8 FP32 planes of [QH][kScRPW], sc_psz(QH) entries apart -- the
 //          same bytes
 //   escr   the cost phase's vertical window sums ([band][CW][32] i32); the same bytes hold the
-//          per-warp E blocks of the aggregation ([warp][2][16 pixels][32] f32, 16-byte units
-//          swizzled by the pixel); during the refinement, from kScRefOff on: the intensities
-//          again as [QH][kScRPW] f32, and the spatial exponents as [2 RB + 1][12] f32
+//          per-warp E blocks of the aggregation ([warp][16 pixels][32] f32, 16-byte units
+//          swizzled by the pixel); after the screening, from kScRefOff on: the intensities
+//          again as [QH][kScRPW] f32 and the spatial exponents as [2 RB + 1][12] f32, and from
+//          kScRangeOff on the candidate range of every pixel of the tile ([TY][TX] int2)
 //   sstr, sstt  window statistics of one band
 //   sI     [QH][kScQWI] f32  the reference intensities times sqrt(log2 e) / sigma1 of the cost
 //          positions (1e18 outside the image, as in k_fused)
-//   skxy   [4 + 2 RB][32][8] f32  -(K[dx][dy] + 12) of this lane's eight A-fragment weights per
-//          window row (1e30 outside the window)
+//   skxy   the row terms of the spatial exponent, (nKy(j), nKy(j - 2)) for j = -1 .. 3 + 2 RB
+//          (float2; the region keeps its earlier, larger size)
 struct ScLayout {
     size_t sref, stgt, cbuf, escr, sstr, sstt, sI, skxy, total;
 };
@@ -113,11 +116,11 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
     constexpr int NKS = 4 + 2 * RB;              // k-steps: the window rows of a patch
     constexpr int NPX = TX / 4, NPY = TY / 4;    // patches of the tile
     constexpr int NPW = NPX * NPY / kWarps;      // patches per warp
-    constexpr int NPP = NPW / 2;                 // handled two at a time; also pixels per lane
     static_assert(RB <= kScMaxRB && NKS <= 16 && QW + 2 <= QWI, "a window row spans at most 16 columns");
     static_assert((NPX * NPY) % kWarps == 0 && NPW % 2 == 0, "patches must split evenly over the warps");
     static_assert(kScBand * (TX + 2 * (RB + kMaxRW)) * kScDCR * 4 <= kScRefOff, "refinement window sums");
-    static_assert(kScRefOff + (QH * kScRPW + KB * 12) * 4 <= kWarps * 2 * 16 * kScDC * 4, "refinement tables");
+    static_assert(kScRefOff + (QH * kScRPW + KB * 12) * 4 <= kScRangeOff, "refinement tables");
+    static_assert(kScRangeOff + TY * TX * 8 <= kWarps * 2 * 16 * kScDC * 4, "candidate ranges");
     constexpr int RPW = kScRPW, PSZ = sc_psz(QH);
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(16) FusedArgs s_args;
@@ -147,7 +150,6 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
         int2 *sstr = reinterpret_cast<int2 *>(smem + L.sstr);
         int2 *sstt = reinterpret_cast<int2 *>(smem + L.sstt);
         float *sI = reinterpret_cast<float *>(smem + L.sI);
-        float4 *skxy = reinterpret_cast<float4 *>(smem + L.skxy);
         const int x0 = tx * TX, y0 = ty * TY;
         if (tid == 0) {
             s_rlo = 0x7fffffff;
@@ -167,155 +169,178 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
                 v = (float)sref[(yq + rw) * RP + a.ref_e + xq + rw] * a.iscale;
             sI[i] = v;
         }
-        // -(K + 12) per (window row r, lane) in the A-fragment layout: pixels m0 = (mx, my),
-        // m1 = (mx, my + 2); columns 2 t4 + {0, 1} (first float4) and 2 t4 + {8, 9} (second)
-        for (int e = tid; e < NKS * 32; e += kThreads) {
-            const int r = e >> 5, ln = e & 31, lg = ln >> 2, lt = ln & 3, lmx = lg & 3, lmy = lg >> 2;
-            auto nk = [&](int col, int my) {
-                const int dx = col - lmx, dy = r - my;
-                return (dx >= 0 && dx <= 2 * RB && dy >= 0 && dy <= 2 * RB) ? -(a.K[dx * KB + dy] + (float)kScWSh)
-                                                                             : 1e30f;
-            };
-            skxy[2 * e] = make_float4(nk(2 * lt, lmy), nk(2 * lt + 1, lmy), nk(2 * lt, lmy + 2), nk(2 * lt + 1, lmy + 2));
-            skxy[2 * e + 1] =
-                make_float4(nk(2 * lt + 8, lmy), nk(2 * lt + 9, lmy), nk(2 * lt + 8, lmy + 2), nk(2 * lt + 9, lmy + 2));
-        }
+        // spatial exponents, separable: -(K[dx][dy] + 12) = nKx(dx) + nKy(dy) with
+        // nKx(i) = -(K[i][RB] + 12) and nKy(j) = -K[RB][j] (1e30 outside the window: weight 0).
+        // The row terms as a table over j = r - my (the lane's first pixel row): (nKy(j), nKy(j - 2))
+        float2 *sky = reinterpret_cast<float2 *>(smem + L.skxy);
+        auto nky = [&](int j) { return (j >= 0 && j <= 2 * RB) ? -a.K[RB * KB + j] : 1e30f; };
+        for (int j = tid; j < NKS + 2; j += kThreads) sky[j] = make_float2(nky(j - 1), nky(j - 3));
+        // this lane's column terms: columns 2 t4 + {0, 1} and 2 t4 + {8, 9} of a window row
+        auto nkx = [&](int col) {
+            const int i = col - mx;
+            return (i >= 0 && i <= 2 * RB) ? -(a.K[i * KB + RB] + (float)kScWSh) : 1e30f;
+        };
+        const float2 nkx_lo = make_float2(nkx(2 * t4), nkx(2 * t4 + 1));
+        const float2 nkx_hi = make_float2(nkx(2 * t4 + 8), nkx(2 * t4 + 9));
         __syncthreads();
 
-        // screening state of the lane's pixel in each patch pair (patch 2 pp + (lane >> 4),
-        // pixel lane & 15): the running minimum of E16 and the candidate range
-        float emin[NPP];
-        int dlo[NPP], dhi[NPP];
+        // Screening work: vertical segments of three patches (8 patch columns x 3 segments of 3
+        // patch rows), two per warp.  The patches of a segment share their window rows: each
+        // row's costs (ldmatrix) and intensities are read once for every patch that uses it.
+        constexpr int NSEGR = NPY / 3;                // segments per patch column
+        constexpr int NR3 = 8 + NKS;                  // window rows of a segment
+        static_assert(NPY % 3 == 0 && NPX * NSEGR == 2 * kWarps, "two segments of three patches per warp");
+        // screening state of this lane's pixel m = lane & 15 of patch i of segment si (both half
+        // warps hold the same state): the running minimum of E16 and the candidate range
+        float emin[2][3];
+        int dlo[2][3], dhi[2][3];
 #pragma unroll
-        for (int i = 0; i < NPP; ++i) {
-            emin[i] = __int_as_float(0x7f800000);
-            dlo[i] = dhi[i] = 0;
-        }
-        float *scr = escr + warp * (2 * 16 * DC);
+        for (int si = 0; si < 2; ++si)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                emin[si][i] = __int_as_float(0x7f800000);
+                dlo[si][i] = dhi[si][i] = 0;
+            }
+        float *scr = escr + warp * (16 * DC);         // one 16 x 32 E block per warp
+        const int hb = lane >> 4, m = lane & 15;
 
         for (int d0 = 0; d0 < (B2 ? 0 : a.D); d0 += DC) {
             // ---- costs of the chunk, 32 disparities, times 2^8, FP16, swizzled
             switch (rw) {
-            case 1: cost_chunk<RB, DC, 1, __half, TX, TY, kThreads, 0, kScBand, true, kScCSh>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
-            case 2: cost_chunk<RB, DC, 2, __half, TX, TY, kThreads, 0, kScBand, true, kScCSh>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
-            case 3: cost_chunk<RB, DC, 3, __half, TX, TY, kThreads, 0, kScBand, true, kScCSh>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
-            case 4: cost_chunk<RB, DC, 4, __half, TX, TY, kThreads, 0, kScBand, true, kScCSh>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
-            default: cost_chunk<RB, DC, 5, __half, TX, TY, kThreads, 0, kScBand, true, kScCSh>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
+            case 1: cost_chunk<RB, DC, 1, __half, TX, TY, kThreads, 0, kScBand, true, kScCSh, 0, 0, kScSeg>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
+            case 2: cost_chunk<RB, DC, 2, __half, TX, TY, kThreads, 0, kScBand, true, kScCSh, 0, 0, kScSeg>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
+            case 3: cost_chunk<RB, DC, 3, __half, TX, TY, kThreads, 0, kScBand, true, kScCSh, 0, 0, kScSeg>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
+            case 4: cost_chunk<RB, DC, 4, __half, TX, TY, kThreads, 0, kScBand, true, kScCSh, 0, 0, kScSeg>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
+            default: cost_chunk<RB, DC, 5, __half, TX, TY, kThreads, 0, kScBand, true, kScCSh, 0, 0, kScSeg>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
             }
-            // ---- screening aggregation, two patches at a time
+            const int dn = min(DC, a.D - d0);
 #pragma unroll 1
-            for (int pp = 0; pp < NPP; ++pp) {
-                float2 nip[2][2];
-                uint32_t brow[2][2];
-                const float *irow[2];
-                float acc[2][4][4];
+            for (int si = 0; si < 2; ++si) {
+                const int sg = warp + kWarps * si;
+                const int px0 = (sg % NPX) * 4, pys = (sg / NPX) * 12;
+                float2 nip[3][2];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int P = warp * NPW + 2 * pp + h;
-                    const int px0 = (P % NPX) * 4, py0 = (P / NPX) * 4;
-                    const float ip0 = sI[(py0 + RB + my0) * QWI + px0 + RB + mx];
-                    const float ip1 = sI[(py0 + RB + my0 + 2) * QWI + px0 + RB + mx];
-                    nip[h][0] = make_float2(-ip0, -ip0);
-                    nip[h][1] = make_float2(-ip1, -ip1);
-                    // ldmatrix rows: lanes 8i..8i+7 name matrix i = (k half, unit): k slots
-                    // 0..7 / 8..15 of the window row, 8-disparity units 2j + (lane >> 4)
-                    const int kk = ((lane >> 3) & 1) * 8 + (lane & 7);
-                    const int xq = min(px0 + kk, QW - 1);   // padding slots (zero weight) read a valid cost
-                    const uint32_t pos = smem_addr(cb16 + ((size_t)py0 * QW + xq) * DC);
+                for (int i = 0; i < 3; ++i) {
+                    const float ip0 = sI[(pys + 4 * i + RB + my0) * QWI + px0 + RB + mx];
+                    const float ip1 = sI[(pys + 4 * i + RB + my0 + 2) * QWI + px0 + RB + mx];
+                    nip[i][0] = make_float2(-ip0, -ip0);
+                    nip[i][1] = make_float2(-ip1, -ip1);
+                }
+                // ldmatrix rows: lanes 8i..8i+7 name matrix i = (k half, unit): k slots 0..7 /
+                // 8..15 of the window row, 8-disparity units 2j + (lane >> 4)
+                const int kk = ((lane >> 3) & 1) * 8 + (lane & 7);
+                const int xq = min(px0 + kk, QW - 1);   // padding slots (zero weight) read a valid cost
+                const uint32_t pos = smem_addr(cb16 + ((size_t)pys * QW + xq) * DC);
+                uint32_t brow[2];
 #pragma unroll
-                    for (int j = 0; j < 2; ++j) brow[h][j] = pos + (uint32_t)(swz_unit<DC>(2 * j + (lane >> 4), xq) << 4);
-                    irow[h] = sI + py0 * QWI + px0 + 2 * t4;
+                for (int j = 0; j < 2; ++j) brow[j] = pos + (uint32_t)(swz_unit<DC>(2 * j + (lane >> 4), xq) << 4);
+                const float *irow = sI + pys * QWI + px0 + 2 * t4;
+                float acc[3][4][4];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
 #pragma unroll
                     for (int nb = 0; nb < 4; ++nb)
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) acc[h][nb][k] = 0.f;
-                }
+                        for (int k = 0; k < 4; ++k) acc[i][nb][k] = 0.f;
 #pragma unroll
-                for (int r = 0; r < NKS; ++r) {
-                    const float4 klo = skxy[2 * (r * 32 + lane)], khi = skxy[2 * (r * 32 + lane) + 1];
+                for (int ra = 0; ra < NR3; ++ra) {
+                    const float2 qlo = *reinterpret_cast<const float2 *>(irow + ra * QWI);
+                    const float2 qhi = *reinterpret_cast<const float2 *>(irow + ra * QWI + 8);
+                    uint32_t b[2][4];
+                    const uint32_t roff = (uint32_t)(ra * QW * DC * (int)sizeof(__half));
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const float2 qlo = *reinterpret_cast<const float2 *>(irow[h] + r * QWI);
-                        const float2 qhi = *reinterpret_cast<const float2 *>(irow[h] + r * QWI + 8);
+                    for (int j = 0; j < 2; ++j) ldsm_x4_t(brow[j] + roff, b[j][0], b[j][1], b[j][2], b[j][3]);
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        const int r = ra - 4 * i;             // this patch's window row
+                        if (r < 0 || r >= NKS) continue;
+                        const float2 ky = sky[r - my0 + 1];   // (nKy(r - my0), nKy(r - my0 - 2))
                         // t = I_q - I_p; e' = t^2 - (K + 12); w16 = RN16(2^-e')
-                        const float2 ta = __fadd2_rn(qlo, nip[h][0]), tb = __fadd2_rn(qlo, nip[h][1]);
-                        const float2 tc = __fadd2_rn(qhi, nip[h][0]), td = __fadd2_rn(qhi, nip[h][1]);
-                        const float2 ea = __ffma2_rn(ta, ta, make_float2(klo.x, klo.y));
-                        const float2 eb = __ffma2_rn(tb, tb, make_float2(klo.z, klo.w));
-                        const float2 ec = __ffma2_rn(tc, tc, make_float2(khi.x, khi.y));
-                        const float2 ed = __ffma2_rn(td, td, make_float2(khi.z, khi.w));
+                        const float2 ta = __fadd2_rn(qlo, nip[i][0]), tb = __fadd2_rn(qlo, nip[i][1]);
+                        const float2 tc = __fadd2_rn(qhi, nip[i][0]), td = __fadd2_rn(qhi, nip[i][1]);
+                        const float2 ea = __fadd2_rn(__ffma2_rn(ta, ta, nkx_lo), make_float2(ky.x, ky.x));
+                        const float2 eb = __fadd2_rn(__ffma2_rn(tb, tb, nkx_lo), make_float2(ky.y, ky.y));
+                        const float2 ec = __fadd2_rn(__ffma2_rn(tc, tc, nkx_hi), make_float2(ky.x, ky.x));
+                        const float2 ed = __fadd2_rn(__ffma2_rn(td, td, nkx_hi), make_float2(ky.y, ky.y));
                         uint32_t af[4];
                         af[0] = h2_rn(ex2_approx(-ea.x), ex2_approx(-ea.y));
                         af[1] = h2_rn(ex2_approx(-eb.x), ex2_approx(-eb.y));
                         af[2] = h2_rn(ex2_approx(-ec.x), ex2_approx(-ec.y));
                         af[3] = h2_rn(ex2_approx(-ed.x), ex2_approx(-ed.y));
-                        const uint32_t roff = (uint32_t)(r * QW * DC * (int)sizeof(__half));
 #pragma unroll
                         for (int j = 0; j < 2; ++j) {
-                            uint32_t b0, b1, b2, b3;
-                            ldsm_x4_t(brow[h][j] + roff, b0, b1, b2, b3);
-                            X::mma(acc[h][2 * j], af, b0, b1);
-                            X::mma(acc[h][2 * j + 1], af, b2, b3);
+                            X::mma(acc[i][2 * j], af, b[j][0], b[j][1]);
+                            X::mma(acc[i][2 * j + 1], af, b[j][2], b[j][3]);
                         }
                     }
                 }
-                // the two 16 x 32 E blocks through the warp's scratch, one pixel per lane
+                // each patch's 16 x 32 E block through the warp's scratch; lanes 0-15 take
+                // disparities 0..15 of pixel lane & 15, lanes 16-31 disparities 16..31
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    float *sb = scr + h * 16 * DC;
+                for (int i = 0; i < 3; ++i) {
 #pragma unroll
                     for (int nb = 0; nb < 4; ++nb) {
                         const int u = 2 * nb + (t4 >> 1), o = 2 * (t4 & 1);
-                        *reinterpret_cast<float2 *>(sb + g * DC + (sc_eunit(u, g) << 2) + o) =
-                            make_float2(acc[h][nb][0], acc[h][nb][1]);
-                        *reinterpret_cast<float2 *>(sb + (g + 8) * DC + (sc_eunit(u, g + 8) << 2) + o) =
-                            make_float2(acc[h][nb][2], acc[h][nb][3]);
+                        *reinterpret_cast<float2 *>(scr + g * DC + (sc_eunit(u, g) << 2) + o) =
+                            make_float2(acc[i][nb][0], acc[i][nb][1]);
+                        *reinterpret_cast<float2 *>(scr + (g + 8) * DC + (sc_eunit(u, g + 8) << 2) + o) =
+                            make_float2(acc[i][nb][2], acc[i][nb][3]);
                     }
-                }
-                __syncwarp();
-                {
-                    const int m = lane & 15;
-                    const float *er = scr + (lane >> 4) * 16 * DC + m * DC;
-                    float e[DC];
+                    __syncwarp();
+                    float e[16];
 #pragma unroll
-                    for (int u = 0; u < DC / 4; ++u) {
-                        const float4 v = *reinterpret_cast<const float4 *>(er + (sc_eunit(u, m) << 2));
-                        e[4 * u] = v.x;
-                        e[4 * u + 1] = v.y;
-                        e[4 * u + 2] = v.z;
-                        e[4 * u + 3] = v.w;
+                    for (int uu = 0; uu < 4; ++uu) {
+                        const float4 v = *reinterpret_cast<const float4 *>(scr + m * DC + (sc_eunit(4 * hb + uu, m) << 2));
+                        e[4 * uu] = v.x;
+                        e[4 * uu + 1] = v.y;
+                        e[4 * uu + 2] = v.z;
+                        e[4 * uu + 3] = v.w;
                     }
-                    const int dn = min(DC, a.D - d0);
+                    __syncwarp();
                     float cm = __int_as_float(0x7f800000);
 #pragma unroll
-                    for (int dd = 0; dd < DC; ++dd) {
-                        if (dd >= dn) e[dd] = __int_as_float(0x7f800000);
+                    for (int dd = 0; dd < 16; ++dd) {
+                        if (16 * hb + dd >= dn) e[dd] = __int_as_float(0x7f800000);
                         cm = fminf(cm, e[dd]);
                     }
-                    // the pair's state, selected with static indices (no local memory)
-                    float em = emin[0];
-#pragma unroll
-                    for (int i = 1; i < NPP; ++i)
-                        if (i == pp) em = emin[i];
+                    cm = fminf(cm, __shfl_xor_sync(0xffffffffu, cm, 16));
+                    // the pixel's state, selected with static indices (no local memory)
+                    float em = emin[0][i];
+                    if (si == 1) em = emin[1][i];
                     const float nm = fminf(em, cm);
                     const float tn = sc_thr(nm);
-                    uint32_t mask = 0;
+                    uint32_t mh = 0;
 #pragma unroll
-                    for (int dd = 0; dd < DC; ++dd) mask |= (e[dd] <= tn) ? (1u << dd) : 0u;
+                    for (int dd = 0; dd < 16; ++dd) mh |= (e[dd] <= tn) ? (1u << dd) : 0u;
+                    const uint32_t mo = __shfl_xor_sync(0xffffffffu, mh, 16);
+                    const uint32_t mask = hb ? (mo | (mh << 16)) : (mh | (mo << 16));
                     const bool reset = mask && tn < em;   // the earlier range cannot hold d*
                     const int lo = d0 + __ffs(mask) - 1, hi = d0 + 31 - __clz(mask);
 #pragma unroll
-                    for (int i = 0; i < NPP; ++i)
-                        if (i == pp) {
-                            if (reset) dlo[i] = lo;
-                            if (mask) dhi[i] = hi;
-                            emin[i] = nm;
+                    for (int k = 0; k < 2; ++k)
+                        if (k == si) {
+                            if (reset) dlo[k][i] = lo;
+                            if (mask) dhi[k][i] = hi;
+                            emin[k][i] = nm;
                         }
                 }
-                __syncwarp();
             }
             __syncthreads();
         }
+
+        // the candidate ranges, per pixel of the tile, for the refinement's own pixel layout
+        int2 *srange = reinterpret_cast<int2 *>(smem + L.escr + kScRangeOff);   // [TY][TX]
+        if (!B2 && hb == 0) {
+#pragma unroll
+            for (int si = 0; si < 2; ++si)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const int sg = warp + kWarps * si;
+                    const int px = (sg % NPX) * 4 + (m & 3), py = (sg / NPX) * 12 + 4 * i + (m >> 2);
+                    srange[py * TX + px] = make_int2(dlo[si][i], dhi[si][i]);
+                }
+        }
+        __syncthreads();
 
         // ---- the tile's refinement range: [dlo - 1, dhi + 1] of every pixel inside the image,
         // clipped at df + 1, df = max(0, u + m - L + 1), where L is the shortest run of target
@@ -326,23 +351,28 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
         // E(p, df) exactly (the same terms in the same order).  The lowest d wins ties, so
         // d* <= df and d* + 1 stays inside the clipped range, and E(df) stands for the whole
         // tail in the smallest E over d != d*: the cut changes none of the outputs.
-        int rlo[NPP], rhi[NPP];
+        // From here on each thread owns a column of RPY pixels (column lane, rows RPY warp ..),
+        // as the SIMT kernel's aggregation does: its loads serve every pixel of the column.
+        constexpr int RPY = TY / kWarps;              // 3
+        static_assert(TX == 32 && TY % kWarps == 0, "one warp per strip of RPY rows");
+        const int px = lane, py0 = warp * RPY;
+        int rlo[RPY], rhi[RPY];
         {
             int ulo = 0x7fffffff, uhi = -1;
 #pragma unroll
-            for (int pp = 0; pp < NPP; ++pp) {
-                const int P = warp * NPW + 2 * pp + (lane >> 4), m = lane & 15;
-                const int u = x0 + (P % NPX) * 4 + (m & 3), v = y0 + (P / NPX) * 4 + (m >> 2);
+            for (int i = 0; i < RPY; ++i) {
+                const int u = x0 + px, v = y0 + py0 + i;
                 const int lmin = (v < a.H) ? __ldg(&a.row_tab[v].w) : 1;
                 const int cap = min(a.D - 1, max(0, u + a.m - lmin + 1) + 1);
-                rlo[pp] = B2 ? 0 : max(dlo[pp] - 1, 0);
-                rhi[pp] = min(B2 ? a.D - 1 : dhi[pp] + 1, cap);
+                const int2 rg = B2 ? make_int2(0, 0) : srange[(py0 + i) * TX + px];
+                rlo[i] = B2 ? 0 : max(rg.x - 1, 0);
+                rhi[i] = min(B2 ? a.D - 1 : rg.y + 1, cap);
                 if (u < a.W && v < a.H) {
-                    ulo = min(ulo, rlo[pp]);
-                    uhi = max(uhi, rhi[pp]);
+                    ulo = min(ulo, rlo[i]);
+                    uhi = max(uhi, rhi[i]);
                 } else {
-                    rlo[pp] = 1;   // nothing to refine
-                    rhi[pp] = 0;
+                    rlo[i] = 1;   // nothing to refine
+                    rhi[i] = 0;
                 }
             }
             ulo = __reduce_min_sync(0xffffffffu, ulo);
@@ -358,10 +388,10 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
         // ---- refinement: k_fused's FP32 arithmetic and running WTA over the candidates, in
         // chunks of DCR disparities from the tile's lowest candidate.  The FP32 costs come from
         // the two-pass cost phase (the same integers and the same rounding as k_fused's costs).
-        float best[NPP], bm1[NPP], bp1[NPP], prev[NPP], sec[B2 ? NPP : 1];
-        int bd[NPP];
+        float best[RPY], bm1[RPY], bp1[RPY], prev[RPY], sec[B2 ? RPY : 1];
+        int bd[RPY];
 #pragma unroll
-        for (int i = 0; i < NPP; ++i) {
+        for (int i = 0; i < RPY; ++i) {
             best[i] = __int_as_float(0x7f800000);
             bm1[i] = bp1[i] = prev[i] = best[i];
             if constexpr (B2) sec[i] = best[i];
@@ -377,87 +407,120 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
             const int dx = i / 12, dy = i - dx * 12;
             sKr[i] = dy < KB ? a.K[dx * KB + dy] : 0.f;
         }
-        // (the first refinement chunk's cost phase synchronises before these are read)
-        for (int cb = ulo_t; cb <= uhi_t; cb += DCR) {
-            switch (rw) {
-            case 1: cost_chunk<RB, DCR, 1, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
-            case 2: cost_chunk<RB, DCR, 2, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
-            case 3: cost_chunk<RB, DCR, 3, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
-            case 4: cost_chunk<RB, DCR, 4, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
-            default: cost_chunk<RB, DCR, 5, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+        float ip[RPY];
+        int tlo = 0x7fffffff, thi = -1;   // the union of this thread's ranges
+#pragma unroll
+        for (int i = 0; i < RPY; ++i) {
+            ip[i] = sI[(py0 + i + RB) * QWI + px + RB];
+            if (rlo[i] <= rhi[i]) {
+                tlo = min(tlo, rlo[i]);
+                thi = max(thi, rhi[i]);
             }
-#pragma unroll
-            for (int pp = 0; pp < NPP; ++pp) {
-                const int lo = max(rlo[pp], cb), hi = min(rhi[pp], cb + DCR - 1);
-                const int P = warp * NPW + 2 * pp + (lane >> 4), m = lane & 15;
-                const int px = (P % NPX) * 4 + (m & 3), py = (P / NPX) * 4 + (m >> 2);
-                const float ip = sIr[(py + RB) * RPW + px + RB];
-                const float *ib = sIr + py * RPW + px;
-                const float *cq = cb32 + py * RPW + px;   // plane 0; plane o at + o PSZ
-                // three disparities per pass: d = g0, g0 + 1, g0 + 2 (those above hi discarded)
+        }
+        // (the first refinement chunk's cost phase synchronises before the tables are read)
+        // refinement chunks of DCR disparities; a tile whose candidates span at most 4 takes one
+        // chunk of 4 (half the walkers and items of the two-pass phase)
+        const int dcr = (uhi_t - ulo_t < 4) ? 4 : DCR;
+        for (int cb = ulo_t; cb <= uhi_t; cb += dcr) {
+            if (dcr == 4) {
+                switch (rw) {
+                case 1: cost_chunk<RB, 4, 1, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+                case 2: cost_chunk<RB, 4, 2, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+                case 3: cost_chunk<RB, 4, 3, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+                case 4: cost_chunk<RB, 4, 4, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+                default: cost_chunk<RB, 4, 5, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+                }
+            } else {
+                switch (rw) {
+                case 1: cost_chunk<RB, DCR, 1, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+                case 2: cost_chunk<RB, DCR, 2, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+                case 3: cost_chunk<RB, DCR, 3, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+                case 4: cost_chunk<RB, DCR, 4, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+                default: cost_chunk<RB, DCR, 5, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+                }
+            }
+            const int lo = max(tlo, cb), hi = min(thi, cb + dcr - 1);
+            // four disparities per pass, d = dw .. dw + 3 (reads past the chunk clamped; their
+            // sums are discarded)
 #pragma unroll 1
-                for (int g0 = lo; g0 <= hi; g0 += 3) {
-                    const int o0 = (g0 - cb) * PSZ, o1 = min(g0 - cb + 1, DCR - 1) * PSZ,
-                              o2 = min(g0 - cb + 2, DCR - 1) * PSZ;
-                    float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+            for (int dw = lo; dw <= hi; dw += 4) {
+                int o[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) o[j] = min(dw + j - cb, dcr - 1) * PSZ;
+                float e[RPY][4];
+#pragma unroll
+                for (int i = 0; i < RPY; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) e[i][j] = 0.f;
+                const float *ib = sIr + py0 * RPW + px;
+                const float *cq = cb32 + py0 * RPW + px;
 #pragma unroll 1
-                    for (int dx = 0; dx < KB; ++dx) {
-                        float kr[12];
+                for (int dx = 0; dx < KB; ++dx) {
+                    float kr[12];
 #pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            const float4 q = *reinterpret_cast<const float4 *>(sKr + dx * 12 + 4 * k);
-                            kr[4 * k] = q.x;
-                            kr[4 * k + 1] = q.y;
-                            kr[4 * k + 2] = q.z;
-                            kr[4 * k + 3] = q.w;
-                        }
-#pragma unroll
-                        for (int dy = 0; dy < KB; ++dy) {
-                            const float t = ib[dy * RPW + dx] - ip;
-                            const float w = ex2_approx(fmaf(-t, t, kr[dy]));
-                            const float *c = cq + dy * RPW + dx;
-                            e0 = fmaf(w, c[o0], e0);
-                            e1 = fmaf(w, c[o1], e1);
-                            e2 = fmaf(w, c[o2], e2);
-                        }
+                    for (int k = 0; k < 3; ++k) {
+                        const float4 q = *reinterpret_cast<const float4 *>(sKr + dx * 12 + 4 * k);
+                        kr[4 * k] = q.x;
+                        kr[4 * k + 1] = q.y;
+                        kr[4 * k + 2] = q.z;
+                        kr[4 * k + 3] = q.w;
                     }
-                    const float ev[3] = {e0, e1, e2};
+                    // neighbour rows of the column, in increasing order: for every pixel the
+                    // window rows come in k_fused's order (row inner, column outer)
 #pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        const int d = g0 + j;
-                        if (d > hi) break;
-                        const float v = ev[j];
-                        if (v < best[pp]) {
-                            if constexpr (B2) sec[pp] = best[pp];
-                            best[pp] = v;
-                            bd[pp] = d;
-                            bm1[pp] = prev[pp];
-                        } else {
-                            if constexpr (B2) sec[pp] = fminf(sec[pp], v);
-                            if (d == bd[pp] + 1) bp1[pp] = v;
+                    for (int r = 0; r < RPY + 2 * RB; ++r) {
+                        const float iq = ib[r * RPW + dx];
+                        float c[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) c[j] = cq[r * RPW + dx + o[j]];
+#pragma unroll
+                        for (int i = 0; i < RPY; ++i) {
+                            const int dy = r - i;
+                            if (dy < 0 || dy > 2 * RB) continue;
+                            const float t = iq - ip[i];
+                            const float w = ex2_approx(fmaf(-t, t, kr[dy]));
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) e[i][j] = fmaf(w, c[j], e[i][j]);
                         }
-                        prev[pp] = v;
                     }
                 }
+#pragma unroll
+                for (int i = 0; i < RPY; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int d = dw + j;
+                        if (d < rlo[i] || d > rhi[i] || d > hi) continue;
+                        const float v = e[i][j];
+                        if (v < best[i]) {
+                            if constexpr (B2) sec[i] = best[i];
+                            best[i] = v;
+                            bd[i] = d;
+                            bm1[i] = prev[i];
+                        } else {
+                            if constexpr (B2) sec[i] = fminf(sec[i], v);
+                            if (d == bd[i] + 1) bp1[i] = v;
+                        }
+                        prev[i] = v;
+                    }
             }
             __syncthreads();
         }
+
         // ---- epilogue: eq. (subpixel), add back s_i(v), validity from the row table (k_fused's)
 #pragma unroll
-        for (int pp = 0; pp < NPP; ++pp) {
-            const int P = warp * NPW + 2 * pp + (lane >> 4), m = lane & 15;
-            const int px = (P % NPX) * 4 + (m & 3), py = (P / NPX) * 4 + (m >> 2);
+        for (int i = 0; i < RPY; ++i) {
+            const int py = py0 + i;
             const int u = x0 + px, v = y0 + py;
             if (u >= a.W || v >= a.H) continue;
-            const int4 rt = __ldg(a.row_tab + v);   // {s_i(v), max s_i, min s_i over v +- m}
+            const int4 rt = __ldg(a.row_tab + v);   // {s_i(v), max s_i, min s_i over v +- m, run}
             float delta = 0.f;
-            if (bd[pp] > 0 && bd[pp] < a.D - 1) {
-                const float den = 2.f * bm1[pp] + 2.f * bp1[pp] - 4.f * best[pp];
-                if (den > 0.f) delta = (bm1[pp] - bp1[pp]) / den;
+            if (bd[i] > 0 && bd[i] < a.D - 1) {
+                const float den = 2.f * bm1[i] + 2.f * bp1[i] - 4.f * best[i];
+                if (den > 0.f) delta = (bm1[i] - bp1[i]) / den;
             }
             const size_t o = (size_t)v * a.W + u;
-            a.disp[o] = (float)bd[pp] + delta + (float)rt.x;
-            if (a.wta) a.wta[o] = bd[pp];
+            a.disp[o] = (float)bd[i] + delta + (float)rt.x;
+            if (a.wta) a.wta[o] = bd[i];
             if (a.valid) {
                 const int ulo = a.m + a.D - 1 + max(0, rt.y);
                 const int uhi = a.W - 1 - a.m + min(0, rt.z);
@@ -465,15 +528,15 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
             }
             if constexpr (B2) {
                 // the skipped normaliser sum_q w(p,q), as k_fused sums it
-                const float ip = sI[(py + RB) * QWI + px + RB];
+                const float ipp = sI[(py + RB) * QWI + px + RB];
                 float ws = 0.f;
                 for (int dx = 0; dx < KB; ++dx)
                     for (int dy = 0; dy < KB; ++dy) {
-                        const float t = sI[(py + dy) * QWI + px + dx] - ip;
+                        const float t = sI[(py + dy) * QWI + px + dx] - ipp;
                         ws += ex2_approx(fmaf(-t, t, a.K[dx * KB + dy]));
                     }
-                a.best2[2 * o] = best[pp] / ws;
-                a.best2[2 * o + 1] = sec[pp] / ws;
+                a.best2[2 * o] = best[i] / ws;
+                a.best2[2 * o + 1] = sec[i] / ws;
             }
         }
     }  // tile loop

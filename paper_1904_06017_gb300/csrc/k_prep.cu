@@ -196,14 +196,27 @@ __global__ void __launch_bounds__(kRowTab) k_row_tables(const float *__restrict_
     const int v0 = blockIdx.x * kRowTab;
     for (int i = threadIdx.x; i < kRowTab + 2 * m; i += kRowTab) {
         const int y = v0 - m + i;
+        si[i] = (y >= 0 && y < H) ? (int)round_half_up(__ldg(shift + y)) : 0;
+    }
+    // the column-0 runs, one warp per row: 32 columns per step, the first other value by ballot
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = wid; i < kRowTab + 2 * m; i += kRowTab / 32) {
+        const int y = v0 - m + i;
         int run = 1;
         if (y >= 0 && y < H) {
             const uint8_t *row = tgt + (size_t)y * pitch;
             const uint8_t c0 = __ldg(row);
-            while (run < W && __ldg(row + run) == c0) ++run;
+            run = W;
+            for (int c = 0; c < W; c += 32) {
+                const bool other = c + lane < W && __ldg(row + c + lane) != c0;
+                const unsigned b = __ballot_sync(0xffffffffu, other);
+                if (b) {
+                    run = c + __ffs(b) - 1;
+                    break;
+                }
+            }
         }
-        si[i] = (y >= 0 && y < H) ? (int)round_half_up(__ldg(shift + y)) : 0;
-        li[i] = run;
+        if (lane == 0) li[i] = run;
     }
     __syncthreads();
     const int v = v0 + threadIdx.x;
