@@ -721,22 +721,23 @@ def run_ours(args):
     # the FP16 / BF16 forms do the same algorithmic work: their share of the same FP32 roofline
     for v in variants.values():
         v["fused_frac_of_fp32_roofline"] = agg_flops / (v["fused_ms"] * 1e-3) / 1e12 / peak
-    # the tensor-core form's executed mma work: per 4 x 4 patch, chunk of 16 disparities and
-    # window row, two m16n8k16 (4096 flop each), including the zero-weight K slots
+    # the tensor-core forms' executed mma work: per 4 x 4 patch, chunk of 32 disparities and
+    # window row, four m16n8k16 (4096 flop each), including the zero-weight K slots (32 x 36
+    # tiles of 72 patches; bil <= 11)
     peaks = measured_peaks()
     nks = 4 + 2 * (bil // 2)
-    mma_flops = ((W + 63) // 64) * ((H + 35) // 36) * 144 * ((D + 15) // 16) * nks * 2 * 4096.0
+    mma_flops = ((W + 31) // 32) * ((H + 35) // 36) * 72 * ((D + 31) // 32) * nks * 4 * 4096.0
     for name in ("f16", "bf16"):
         t_tf = mma_flops / (variants[name]["fused_ms"] * 1e-3) / 1e12
         variants[name]["tensor_mma"] = {
             "tflops": t_tf, "peak": peaks.get("bf16_tflops"), "unit": "TFLOP/s",
             "frac": t_tf / peaks["bf16_tflops"] if peaks.get("bf16_tflops") else None,
             "peak_basis": "measured dense bf16 (same rate for fp16), MEASURED_PEAKS.json",
-            "note": "the form is bound by weight generation and the integer cost phase, not the tensor pipe"}
+            "note": "the form is bound by the cost phase and shared memory, not the tensor pipe"}
     variants["kernel"] = {"f32": "k_fused_sc (screened FP32 form; the default)",
                           "f32_simt": "k_fused (the SIMT FP32 form: FP32 weights and accumulators on the CUDA cores)",
-                          "f16": "k_fused_tc (tensor-core aggregation, FP32 accumulators)",
-                          "bf16": "k_fused_tc (tensor-core aggregation, FP32 accumulators)"}
+                          "f16": "k_fused_sc, plain mode (tensor-core aggregation of the FP16 costs, FP32 accumulators)",
+                          "bf16": "k_fused_sc, plain mode (tensor-core aggregation of the BF16 costs, FP32 accumulators)"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,

@@ -15,7 +15,7 @@ FusedKernel pick_fused_f32_b2(int rb, int dc)
 FusedKernel pick_fused_b2(int cost_dtype, int rb, int dc, int wc)
 {
     if (wc == kTcWC) return dc == kTcDC && rb <= kTcMaxRB ? pick_fused_tc_b2(cost_dtype, rb) : nullptr;
-    if (wc == kScWC) return cost_dtype == STEREO_F32 ? pick_fused_sc_b2(rb) : nullptr;
+    if (wc == kScWC) return cost_dtype == STEREO_F32 ? pick_fused_sc_b2(rb) : pick_fused_sc16_b2(cost_dtype, rb);
     if (cost_dtype == STEREO_F32 && wc == 2) return pick_fused_f32_b2(rb, dc);
     return nullptr;
 }

@@ -256,6 +256,8 @@ FusedKernel pick_fused_ws(int rb, int dc);             // k_fused_ws.cu: warp-sp
 FusedKernel pick_fused_tc(int cost_dtype, int rb);     // k_fused_tc_{f16,bf16}.cu: tensor-core aggregation, DC = 16
 FusedKernel pick_fused_sc(int rb);                     // k_fused_sc.cu: screened FP32 form, tile code kScWC
 FusedKernel pick_fused_sc_b2(int rb);                  // k_fused_sc_b2.cu: the same with the best2 output
+FusedKernel pick_fused_sc16(int cost_dtype, int rb);   // k_fused_sc16.cu: FP16 / BF16 storage, tile code kScWC
+FusedKernel pick_fused_sc16_b2(int cost_dtype, int rb);   // k_fused_sc16_b2.cu: the same with best2
 FusedKernel pick_fused(int cost_dtype, int rb, int dc, int wc);
 // The instantiation with the best2 output (FP32 storage at WC = 2 with DC = 12, and the
 // tensor-core form); nullptr where there is none.  k_fused_b2_f32.cu, k_fused_tc_{f16,bf16}_b2.cu.

@@ -19,7 +19,10 @@ FusedKernel pick_fused(int cost_dtype, int rb, int dc, int wc)
 {
     if (wc == kWsWC) return cost_dtype == STEREO_F32 && rb <= kWsMaxRB ? pick_fused_ws(rb, dc) : nullptr;
     if (wc == kTcWC) return dc == kTcDC && rb <= kTcMaxRB ? pick_fused_tc(cost_dtype, rb) : nullptr;
-    if (wc == kScWC) return cost_dtype == STEREO_F32 && dc == kScDC ? pick_fused_sc(rb) : nullptr;
+    if (wc == kScWC) {
+        if (dc != kScDC) return nullptr;
+        return cost_dtype == STEREO_F32 ? pick_fused_sc(rb) : pick_fused_sc16(cost_dtype, rb);
+    }
     switch (cost_dtype) {
     case STEREO_F32: return pick_fused_f32(rb, dc, wc);
     case STEREO_F16: return pick_fused_f16(rb, dc, wc);

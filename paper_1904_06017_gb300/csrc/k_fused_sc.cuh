@@ -102,12 +102,28 @@ __device__ __forceinline__ uint32_t h2_rn(float lo, float hi)
 // 16-byte units, unit u stored at u ^ (m & 7) (conflict-free fragment stores and row reads).
 __device__ __forceinline__ int sc_eunit(int u, int m) { return u ^ (m & 7); }
 
-template <int RB, bool B2 = false>
+// Packed pair of FP32 values rounded to the 16-bit type (lo in the low half).
+template <typename T> __device__ __forceinline__ uint32_t pack_rn(float lo, float hi);
+template <> __device__ __forceinline__ uint32_t pack_rn<__half>(float lo, float hi) { return h2_rn(lo, hi); }
+template <> __device__ __forceinline__ uint32_t pack_rn<__nv_bfloat16>(float lo, float hi)
+{
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+// MODE: kScScreened (the FP32 screened form), or kScPlain (the FP16 / BF16 storage form: the
+// same tensor-core aggregation of the 16-bit costs with a running WTA on its sums, no
+// refinement).  B2: the best2 output.  T: the 16-bit type of the costs and weights.
+constexpr int kScScreened = 0, kScPlain = 1;
+
+template <int RB, bool B2 = false, int MODE = kScScreened, typename T = __half>
 __global__ void __launch_bounds__(kThreads, 1)
 k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__ pairs,
            const int2 *__restrict__ items, int nitems, int *__restrict__ counter)
 {
-    using X = TcOps<__half>;
+    using X = TcOps<T>;
+    constexpr bool PLAIN = MODE == kScPlain;
     constexpr int DC = kScDC, DCR = kScDCR;
     constexpr int TX = tile_x(kScWC), TY = tile_y(kScWC);
     constexpr int KB = 2 * RB + 1;
@@ -143,7 +159,7 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
         const ScLayout L = sc_layout(RB, a.m, RP, a.tgt_box_w, a.box_h);
         uint8_t *sref = smem + L.sref;
         uint8_t *stgt = smem + L.stgt;
-        __half *cb16 = reinterpret_cast<__half *>(smem + L.cbuf);
+        T *cb16 = reinterpret_cast<T *>(smem + L.cbuf);
         float *cb32 = reinterpret_cast<float *>(smem + L.cbuf);
         int *vband = reinterpret_cast<int *>(smem + L.escr);
         float *escr = reinterpret_cast<float *>(smem + L.escr);
@@ -203,15 +219,29 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
             }
         float *scr = escr + warp * (16 * DC);         // one 16 x 32 E block per warp
         const int hb = lane >> 4, m = lane & 15;
+        // the plain form's running WTA (k_fused's rules on the 16-bit sums): per segment, state 0
+        // is pixel m of patch hb, state 1 (lanes 0-15) pixel m of patch 2
+        struct Wta {
+            float best, bm1, bp1, prev, sec;
+            int bd;
+        };
+        Wta ws[2][2];
+#pragma unroll
+        for (int si = 0; si < 2; ++si)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const float inf = __int_as_float(0x7f800000);
+                ws[si][k] = Wta{inf, inf, inf, inf, inf, -1};
+            }
 
-        for (int d0 = 0; d0 < (B2 ? 0 : a.D); d0 += DC) {
+        for (int d0 = 0; d0 < (B2 && !PLAIN ? 0 : a.D); d0 += DC) {
             // ---- costs of the chunk, 32 disparities, times 2^8, FP16, swizzled
             switch (rw) {
-            case 1: cost_chunk<RB, DC, 1, __half, TX, TY, kThreads, 0, kScBand, true, kScCSh, 0, 0, kScSeg>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
-            case 2: cost_chunk<RB, DC, 2, __half, TX, TY, kThreads, 0, kScBand, true, kScCSh, 0, 0, kScSeg>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
-            case 3: cost_chunk<RB, DC, 3, __half, TX, TY, kThreads, 0, kScBand, true, kScCSh, 0, 0, kScSeg>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
-            case 4: cost_chunk<RB, DC, 4, __half, TX, TY, kThreads, 0, kScBand, true, kScCSh, 0, 0, kScSeg>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
-            default: cost_chunk<RB, DC, 5, __half, TX, TY, kThreads, 0, kScBand, true, kScCSh, 0, 0, kScSeg>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
+            case 1: cost_chunk<RB, DC, 1, T, TX, TY, kThreads, 0, kScBand, true, kScCSh, 0, 0, kScSeg>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
+            case 2: cost_chunk<RB, DC, 2, T, TX, TY, kThreads, 0, kScBand, true, kScCSh, 0, 0, kScSeg>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
+            case 3: cost_chunk<RB, DC, 3, T, TX, TY, kThreads, 0, kScBand, true, kScCSh, 0, 0, kScSeg>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
+            case 4: cost_chunk<RB, DC, 4, T, TX, TY, kThreads, 0, kScBand, true, kScCSh, 0, 0, kScSeg>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
+            default: cost_chunk<RB, DC, 5, T, TX, TY, kThreads, 0, kScBand, true, kScCSh, 0, 0, kScSeg>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
             }
             const int dn = min(DC, a.D - d0);
 #pragma unroll 1
@@ -263,10 +293,10 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
                         const float2 ec = __fadd2_rn(__ffma2_rn(tc, tc, nkx_hi), make_float2(ky.x, ky.x));
                         const float2 ed = __fadd2_rn(__ffma2_rn(td, td, nkx_hi), make_float2(ky.y, ky.y));
                         uint32_t af[4];
-                        af[0] = h2_rn(ex2_approx(-ea.x), ex2_approx(-ea.y));
-                        af[1] = h2_rn(ex2_approx(-eb.x), ex2_approx(-eb.y));
-                        af[2] = h2_rn(ex2_approx(-ec.x), ex2_approx(-ec.y));
-                        af[3] = h2_rn(ex2_approx(-ed.x), ex2_approx(-ed.y));
+                        af[0] = pack_rn<T>(ex2_approx(-ea.x), ex2_approx(-ea.y));
+                        af[1] = pack_rn<T>(ex2_approx(-eb.x), ex2_approx(-eb.y));
+                        af[2] = pack_rn<T>(ex2_approx(-ec.x), ex2_approx(-ec.y));
+                        af[3] = pack_rn<T>(ex2_approx(-ed.x), ex2_approx(-ed.y));
 #pragma unroll
                         for (int j = 0; j < 2; ++j) {
                             X::mma(acc[i][2 * j], af, b[j][0], b[j][1]);
@@ -274,58 +304,158 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
                         }
                     }
                 }
-                // each patch's 16 x 32 E block through the warp's scratch; lanes 0-15 take
-                // disparities 0..15 of pixel lane & 15, lanes 16-31 disparities 16..31
+                if constexpr (PLAIN) {
+                    // two E blocks per warp: patches 0 and 1 (one pixel per lane), then patch 2
+                    float *scr2 = escr + warp * (2 * 16 * DC);
+                    auto put = [&](int i, int slot) {
+                        float *sb = scr2 + slot * 16 * DC;
 #pragma unroll
-                for (int i = 0; i < 3; ++i) {
-#pragma unroll
-                    for (int nb = 0; nb < 4; ++nb) {
-                        const int u = 2 * nb + (t4 >> 1), o = 2 * (t4 & 1);
-                        *reinterpret_cast<float2 *>(scr + g * DC + (sc_eunit(u, g) << 2) + o) =
-                            make_float2(acc[i][nb][0], acc[i][nb][1]);
-                        *reinterpret_cast<float2 *>(scr + (g + 8) * DC + (sc_eunit(u, g + 8) << 2) + o) =
-                            make_float2(acc[i][nb][2], acc[i][nb][3]);
-                    }
-                    __syncwarp();
-                    float e[16];
-#pragma unroll
-                    for (int uu = 0; uu < 4; ++uu) {
-                        const float4 v = *reinterpret_cast<const float4 *>(scr + m * DC + (sc_eunit(4 * hb + uu, m) << 2));
-                        e[4 * uu] = v.x;
-                        e[4 * uu + 1] = v.y;
-                        e[4 * uu + 2] = v.z;
-                        e[4 * uu + 3] = v.w;
-                    }
-                    __syncwarp();
-                    float cm = __int_as_float(0x7f800000);
-#pragma unroll
-                    for (int dd = 0; dd < 16; ++dd) {
-                        if (16 * hb + dd >= dn) e[dd] = __int_as_float(0x7f800000);
-                        cm = fminf(cm, e[dd]);
-                    }
-                    cm = fminf(cm, __shfl_xor_sync(0xffffffffu, cm, 16));
-                    // the pixel's state, selected with static indices (no local memory)
-                    float em = emin[0][i];
-                    if (si == 1) em = emin[1][i];
-                    const float nm = fminf(em, cm);
-                    const float tn = sc_thr(nm);
-                    uint32_t mh = 0;
-#pragma unroll
-                    for (int dd = 0; dd < 16; ++dd) mh |= (e[dd] <= tn) ? (1u << dd) : 0u;
-                    const uint32_t mo = __shfl_xor_sync(0xffffffffu, mh, 16);
-                    const uint32_t mask = hb ? (mo | (mh << 16)) : (mh | (mo << 16));
-                    const bool reset = mask && tn < em;   // the earlier range cannot hold d*
-                    const int lo = d0 + __ffs(mask) - 1, hi = d0 + 31 - __clz(mask);
-#pragma unroll
-                    for (int k = 0; k < 2; ++k)
-                        if (k == si) {
-                            if (reset) dlo[k][i] = lo;
-                            if (mask) dhi[k][i] = hi;
-                            emin[k][i] = nm;
+                        for (int nb = 0; nb < 4; ++nb) {
+                            const int u = 2 * nb + (t4 >> 1), o = 2 * (t4 & 1);
+                            *reinterpret_cast<float2 *>(sb + g * DC + (sc_eunit(u, g) << 2) + o) =
+                                make_float2(acc[i][nb][0], acc[i][nb][1]);
+                            *reinterpret_cast<float2 *>(sb + (g + 8) * DC + (sc_eunit(u, g + 8) << 2) + o) =
+                                make_float2(acc[i][nb][2], acc[i][nb][3]);
                         }
+                    };
+                    auto run = [&](int slot, int k) {
+                        const float *er = scr2 + slot * 16 * DC + m * DC;
+                        float e[DC];
+#pragma unroll
+                        for (int u = 0; u < DC / 4; ++u) {
+                            const float4 v = *reinterpret_cast<const float4 *>(er + (sc_eunit(u, m) << 2));
+                            e[4 * u] = v.x;
+                            e[4 * u + 1] = v.y;
+                            e[4 * u + 2] = v.z;
+                            e[4 * u + 3] = v.w;
+                        }
+                        Wta st = ws[0][k];
+                        if (si == 1) st = ws[1][k];
+#pragma unroll
+                        for (int dd = 0; dd < DC; ++dd) {
+                            if (dd >= dn) break;
+                            const float v = e[dd];
+                            const int d = d0 + dd;
+                            if (v < st.best) {
+                                if constexpr (B2) st.sec = st.best;
+                                st.best = v;
+                                st.bd = d;
+                                st.bm1 = st.prev;
+                            } else {
+                                if constexpr (B2) st.sec = fminf(st.sec, v);
+                                if (d == st.bd + 1) st.bp1 = v;
+                            }
+                            st.prev = v;
+                        }
+                        if (si == 0) ws[0][k] = st;
+                        else ws[1][k] = st;
+                    };
+                    put(0, 0);
+                    put(1, 1);
+                    __syncwarp();
+                    run(hb, 0);
+                    __syncwarp();
+                    put(2, 0);
+                    __syncwarp();
+                    if (hb == 0) run(0, 1);
+                    __syncwarp();
+                } else {
+                    // each patch's 16 x 32 E block through the warp's scratch; lanes 0-15 take
+                    // disparities 0..15 of pixel lane & 15, lanes 16-31 disparities 16..31
+    #pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+    #pragma unroll
+                        for (int nb = 0; nb < 4; ++nb) {
+                            const int u = 2 * nb + (t4 >> 1), o = 2 * (t4 & 1);
+                            *reinterpret_cast<float2 *>(scr + g * DC + (sc_eunit(u, g) << 2) + o) =
+                                make_float2(acc[i][nb][0], acc[i][nb][1]);
+                            *reinterpret_cast<float2 *>(scr + (g + 8) * DC + (sc_eunit(u, g + 8) << 2) + o) =
+                                make_float2(acc[i][nb][2], acc[i][nb][3]);
+                        }
+                        __syncwarp();
+                        float e[16];
+    #pragma unroll
+                        for (int uu = 0; uu < 4; ++uu) {
+                            const float4 v = *reinterpret_cast<const float4 *>(scr + m * DC + (sc_eunit(4 * hb + uu, m) << 2));
+                            e[4 * uu] = v.x;
+                            e[4 * uu + 1] = v.y;
+                            e[4 * uu + 2] = v.z;
+                            e[4 * uu + 3] = v.w;
+                        }
+                        __syncwarp();
+                        float cm = __int_as_float(0x7f800000);
+    #pragma unroll
+                        for (int dd = 0; dd < 16; ++dd) {
+                            if (16 * hb + dd >= dn) e[dd] = __int_as_float(0x7f800000);
+                            cm = fminf(cm, e[dd]);
+                        }
+                        cm = fminf(cm, __shfl_xor_sync(0xffffffffu, cm, 16));
+                        // the pixel's state, selected with static indices (no local memory)
+                        float em = emin[0][i];
+                        if (si == 1) em = emin[1][i];
+                        const float nm = fminf(em, cm);
+                        const float tn = sc_thr(nm);
+                        uint32_t mh = 0;
+    #pragma unroll
+                        for (int dd = 0; dd < 16; ++dd) mh |= (e[dd] <= tn) ? (1u << dd) : 0u;
+                        const uint32_t mo = __shfl_xor_sync(0xffffffffu, mh, 16);
+                        const uint32_t mask = hb ? (mo | (mh << 16)) : (mh | (mo << 16));
+                        const bool reset = mask && tn < em;   // the earlier range cannot hold d*
+                        const int lo = d0 + __ffs(mask) - 1, hi = d0 + 31 - __clz(mask);
+    #pragma unroll
+                        for (int k = 0; k < 2; ++k)
+                            if (k == si) {
+                                if (reset) dlo[k][i] = lo;
+                                if (mask) dhi[k][i] = hi;
+                                emin[k][i] = nm;
+                            }
+                    }
                 }
             }
             __syncthreads();
+        }
+
+        if constexpr (PLAIN) {
+            // ---- epilogue of the plain form: eq. (subpixel), add back s_i(v), validity
+#pragma unroll
+            for (int si = 0; si < 2; ++si)
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if (k == 1 && hb) continue;
+                    const int sg = warp + kWarps * si, patch = k ? 2 : hb;
+                    const int px = (sg % NPX) * 4 + (m & 3), py = (sg / NPX) * 12 + 4 * patch + (m >> 2);
+                    const int u = x0 + px, v = y0 + py;
+                    if (u >= a.W || v >= a.H) continue;
+                    const Wta &st = ws[si][k];
+                    const int4 rt = __ldg(a.row_tab + v);
+                    float delta = 0.f;
+                    if (st.bd > 0 && st.bd < a.D - 1) {
+                        const float den = 2.f * st.bm1 + 2.f * st.bp1 - 4.f * st.best;
+                        if (den > 0.f) delta = (st.bm1 - st.bp1) / den;
+                    }
+                    const size_t o = (size_t)v * a.W + u;
+                    a.disp[o] = (float)st.bd + delta + (float)rt.x;
+                    if (a.wta) a.wta[o] = st.bd;
+                    if (a.valid) {
+                        const int ulo = a.m + a.D - 1 + max(0, rt.y);
+                        const int uhi = a.W - 1 - a.m + min(0, rt.z);
+                        a.valid[o] = (uint8_t)(v >= a.m && v <= a.H - 1 - a.m && u >= ulo && u <= uhi);
+                    }
+                    if constexpr (B2) {
+                        // the skipped normaliser in FP32 (the sums carry the factor 2^20)
+                        const float ipp = sI[(py + RB) * QWI + px + RB];
+                        float wsum = 0.f;
+                        for (int dx = 0; dx < KB; ++dx)
+                            for (int dy = 0; dy < KB; ++dy) {
+                                const float t = sI[(py + dy) * QWI + px + dx] - ipp;
+                                wsum += ex2_approx(fmaf(-t, t, a.K[dx * KB + dy]));
+                            }
+                        const float sc = 1.f / (float)(1 << (kScWSh + kScCSh));
+                        a.best2[2 * o] = st.best * sc / wsum;
+                        a.best2[2 * o + 1] = st.sec * sc / wsum;
+                    }
+                }
+            continue;   // the next tile
         }
 
         // the candidate ranges, per pixel of the tile, for the refinement's own pixel layout
@@ -542,16 +672,16 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
     }  // tile loop
 }
 
-template <bool B2 = false>
+template <bool B2 = false, int MODE = kScScreened, typename T = __half>
 FusedKernel pick_sc_rb(int rb)
 {
     switch (rb) {
-    case 0: return k_fused_sc<0, B2>;
-    case 1: return k_fused_sc<1, B2>;
-    case 2: return k_fused_sc<2, B2>;
-    case 3: return k_fused_sc<3, B2>;
-    case 4: return k_fused_sc<4, B2>;
-    case 5: return k_fused_sc<5, B2>;
+    case 0: return k_fused_sc<0, B2, MODE, T>;
+    case 1: return k_fused_sc<1, B2, MODE, T>;
+    case 2: return k_fused_sc<2, B2, MODE, T>;
+    case 3: return k_fused_sc<3, B2, MODE, T>;
+    case 4: return k_fused_sc<4, B2, MODE, T>;
+    case 5: return k_fused_sc<5, B2, MODE, T>;
     }
     return nullptr;
 }

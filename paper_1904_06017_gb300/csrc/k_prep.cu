@@ -183,24 +183,24 @@ int launch_prep(stereo_ctx *ctx, const uint8_t *ref, const uint8_t *tgtw, cudaSt
 // least 1; W when the whole row is one value).  The replicate padding extends that run to the
 // left, so a read of row y at any column below L(y) returns the value of column 0: the
 // screened fused form uses this to find the disparities beyond which every cost behind a
-// pixel no longer changes.  A block of kRowTab rows first rounds its rows and an m-row halo
-// on each side once (and measures their runs), then takes the window extremes from shared
-// memory.
-constexpr int kRowTab = 128, kRowTabHalo = 16;   // m = rw + bilateral radius <= 12
+// pixel no longer changes.  A block of kRowTab rows first rounds its rows and an m-row halo on
+// each side once and measures their runs (one warp per row, 32 columns per step), then takes
+// the window extremes from shared memory.
+constexpr int kRowTab = 32, kRowTabHalo = 16;   // m = rw + bilateral radius <= 12
+constexpr int kRowThreads = 256;
 
-__global__ void __launch_bounds__(kRowTab) k_row_tables(const float *__restrict__ shift, const uint8_t *__restrict__ tgt,
-                                                        int pitch, int W, int H, int m, int4 *__restrict__ tab)
+__global__ void __launch_bounds__(kRowThreads) k_row_tables(const float *__restrict__ shift, const uint8_t *__restrict__ tgt,
+                                                           int pitch, int W, int H, int m, int4 *__restrict__ tab)
 {
     __shared__ int si[kRowTab + 2 * kRowTabHalo];
     __shared__ int li[kRowTab + 2 * kRowTabHalo];
     const int v0 = blockIdx.x * kRowTab;
-    for (int i = threadIdx.x; i < kRowTab + 2 * m; i += kRowTab) {
+    for (int i = threadIdx.x; i < kRowTab + 2 * m; i += kRowThreads) {
         const int y = v0 - m + i;
         si[i] = (y >= 0 && y < H) ? (int)round_half_up(__ldg(shift + y)) : 0;
     }
-    // the column-0 runs, one warp per row: 32 columns per step, the first other value by ballot
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int i = wid; i < kRowTab + 2 * m; i += kRowTab / 32) {
+    for (int i = wid; i < kRowTab + 2 * m; i += kRowThreads / 32) {
         const int y = v0 - m + i;
         int run = 1;
         if (y >= 0 && y < H) {
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(kRowTab) k_row_tables(const float *__restrict_
     }
     __syncthreads();
     const int v = v0 + threadIdx.x;
-    if (v >= H) return;
+    if (threadIdx.x >= kRowTab || v >= H) return;
     int hi = -(1 << 30), lo = 1 << 30, lmin = 1 << 30;
     const int ylo = max(v - m, 0), yhi = min(v + m, H - 1);
     for (int y = ylo; y <= yhi; ++y) {
@@ -236,7 +236,7 @@ int launch_row_tables(stereo_ctx *ctx, const float *shift, const uint8_t *tgtw, 
 {
     const Geometry &g = ctx->g;
     if (g.m > kRowTabHalo) return set_error(STEREO_EINVAL, "k_row_tables: halo %d above %d", g.m, kRowTabHalo);
-    k_row_tables<<<(g.H + kRowTab - 1) / kRowTab, kRowTab, 0, s>>>(shift, tgtw, g.pitch, g.W, g.H, g.m, ctx->row_tab);
+    k_row_tables<<<(g.H + kRowTab - 1) / kRowTab, kRowThreads, 0, s>>>(shift, tgtw, g.pitch, g.W, g.H, g.m, ctx->row_tab);
     return cuda_error(cudaGetLastError(), "k_row_tables launch");
 }
 

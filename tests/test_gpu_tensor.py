@@ -1,5 +1,7 @@
 """Tensor-core aggregation of the FP16 / BF16 storage forms (mma.sync over 4 x 4 pixel
-patches, FP32 accumulators), the default kernel of those forms for bil <= 13.
+patches, FP32 accumulators), the default kernel of those forms for bil <= 13: for bil <= 11 on
+32 x 36 tiles with weights rounded from the FP32 ones (k_fused_sc, plain mode), for bil = 13 on
+64 x 36 tiles with weights formed in 16-bit arithmetic (k_fused_tc).
 
 Its costs and bilateral weights are rounded to the 16-bit type, so it is held to bounds
 derived from that rounding rather than the FP32 path's 1e-3 gap.  FP16: a cost moves by at
@@ -179,20 +181,24 @@ def _batch(ss, dtype, wc, dc):
     return [q["disp"].cpu().numpy() for q in qs], qs, cfg
 
 
-def test_tensor_form_batch_equals_single_and_tracks_simt_form():
+@pytest.mark.parametrize("wc,dc", [(32, 32), (16, 16)])
+def test_tensor_form_batch_equals_single_and_tracks_simt_form(wc, dc):
+    """tile_wc 32: the 32 x 36 form with weights rounded from FP32 (the default single-pair
+    context for bil <= 11); tile_wc 16: the 64 x 36 form with 16-bit weights."""
     ss = [synth.make_scene(W, H, D, 700 + i, roll=math.radians(2.0 * (i - 2)), coeffs=(6.0, 0.1, 0.0),
                            n_potholes=1, warp=True, win=7, bil=9) for i, (W, H, D) in enumerate(SIZES)]
-    tc, qs, cfg = _batch(ss, sg.STEREO_F16, 16, 16)
-    assert cfg["tile_wc"] == 16 and cfg["tile_dc"] == 16
-    # the persistent batch launch gives what single-pair contexts give (same kernel, same tiles)
-    for (W, H, D), q, d in zip(SIZES, qs, tc):
-        tw = torch.empty_like(q["tgt"])
-        disp = torch.empty((H, W), dtype=torch.float32, device="cuda")
-        with sg.Stereo(W, H, D, win=7, bil=9, sigma0=3.0, sigma1=10.0, pitch=q["ref"].shape[1],
-                       cost_dtype=sg.STEREO_F16) as st:
-            st.warp_target(q["tgt"], q["shift"], tw)
-            st.cost_aggregate_wta(q["ref"], tw, q["shift"], disp)
-        assert np.array_equal(disp.cpu().numpy(), d)
+    tc, qs, cfg = _batch(ss, sg.STEREO_F16, wc, dc)
+    assert cfg["tile_wc"] == wc and cfg["tile_dc"] == dc
+    if wc == 32:
+        # the persistent batch launch gives what single-pair contexts give (same kernel, same tiles)
+        for (W, H, D), q, d in zip(SIZES, qs, tc):
+            tw = torch.empty_like(q["tgt"])
+            disp = torch.empty((H, W), dtype=torch.float32, device="cuda")
+            with sg.Stereo(W, H, D, win=7, bil=9, sigma0=3.0, sigma1=10.0, pitch=q["ref"].shape[1],
+                           cost_dtype=sg.STEREO_F16) as st:
+                st.warp_target(q["tgt"], q["shift"], tw)
+                st.cost_aggregate_wta(q["ref"], tw, q["shift"], disp)
+            assert np.array_equal(disp.cpu().numpy(), d)
     # against the FP16 form without tensor cores (FP32 weights): the rounded disparities
     # agree as closely as FP16 and FP32 storage do (a sub-pixel disparity near a half-integer
     # rounds either way), and disparities more than half a pixel apart are rarer still
@@ -201,8 +207,8 @@ def test_tensor_form_batch_equals_single_and_tracks_simt_form():
     total = sum(a.size for a in tc)
     diff = sum(int(np.count_nonzero(np.rint(a) != np.rint(b))) for a, b in zip(tc, simt))
     far = sum(int(np.count_nonzero(np.abs(a - b) > 0.5)) for a, b in zip(tc, simt))
-    print("\nFP16 tensor-core vs FP16 SIMT aggregation: rounded disparities differ on %.2e, "
-          "by more than 0.5 px on %.2e of pixels" % (diff / total, far / total))
+    print("\nFP16 tensor-core (tiles %d) vs FP16 SIMT aggregation: rounded disparities differ on %.2e, "
+          "by more than 0.5 px on %.2e of pixels" % (wc, diff / total, far / total))
     assert diff / total <= 5e-3
     assert far / total <= 1e-3
 
