@@ -5,6 +5,8 @@
 //   cost_chunk_mma  -- the cross term on the tensor cores (exact FP16 operands and FP32
 //                      accumulation), one warp per block of 8 cost columns.
 #pragma once
+#include <type_traits>
+
 #include "k_fused_common.cuh"
 
 namespace sgb {
@@ -54,7 +56,9 @@ __device__ __forceinline__ void group_sync()
 // reciprocal and the constant of eq. (c), so the scaled value is the same rounding of the same
 // exact product).  PLW > 0: planar storage, one plane per disparity, rows of PLW entries and
 // planes PSZ entries apart (cbuf[d * PSZ + y * PLW + x]), for per-pixel gathers whose lanes need
-// different disparities.  KSEG: cost columns per work item of the horizontal pass.
+// different disparities; with PAIR the planes hold disparity pairs (2k, 2k + 1) interleaved as
+// float2, cbuf[(k * PSZ + y * PLW + x) * 2 + (d & 1)], so that one 8-byte load gives both.
+// KSEG: cost columns per work item of the horizontal pass.
 template <int DC>
 __host__ __device__ constexpr int swz_unit(int unit, int x)
 {
@@ -62,7 +66,8 @@ __host__ __device__ constexpr int swz_unit(int unit, int x)
 }
 
 template <int RB, int DC, int RW, typename T, int TX, int TY, int NT = kThreads, int BAR = 0,
-          int KBAND = kBand, bool SWZ = false, int CSH = 0, int PLW = 0, int PSZ = 0, int KSEG = kSeg>
+          int KBAND = kBand, bool SWZ = false, int CSH = 0, int PLW = 0, int PSZ = 0, int KSEG = kSeg,
+          bool PAIR = false>
 __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sref, const uint8_t *stgt,
                                            T *cbuf, int *vband, int2 *sstr, int2 *sstt,
                                            int x0, int y0, int d0, int tid)
@@ -258,6 +263,17 @@ __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sr
                     const int x = xs + j;
                     if (j < nout) CostStore<T>::store4(co + (size_t)x * DC + (swz_unit<DC>(dq >> 1, x) << 3), out[j]);
                 }
+            } else if constexpr (PLW > 0 && PAIR) {
+                static_assert(PSZ >= QH * PLW, "planes must not overlap");
+                static_assert(std::is_same<T, float>::value, "pair planes hold FP32 costs");
+                float2 *co = reinterpret_cast<float2 *>(cbuf) + (size_t)(2 * dq) * PSZ + (size_t)yq * PLW;
+#pragma unroll
+                for (int j = 0; j < kSeg; ++j)
+                    if (j < nout) {
+                        const int x = xs + j;
+                        co[x] = make_float2(out[j].x, out[j].y);
+                        co[PSZ + x] = make_float2(out[j].z, out[j].w);
+                    }
             } else if constexpr (PLW > 0) {
                 static_assert(PSZ >= QH * PLW, "planes must not overlap");
                 T *co = cbuf + (size_t)(4 * dq) * PSZ + (size_t)yq * PLW;

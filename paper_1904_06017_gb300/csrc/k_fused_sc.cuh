@@ -36,9 +36,9 @@ constexpr int kScDCR = 8;       // disparities per FP32 refinement chunk
 constexpr int kScBand = 6;      // cost rows per band of the screening chunk's cost phase
 constexpr int kScSeg = 6;       // cost columns per horizontal work item (6 rows x 7 segments x 8 quads = 336 items)
 constexpr int kScQWI = 44;      // row length of the staged FP32 intensities (>= QW, >= 28 + 16)
-// Refinement planes: rows of kScRPW entries (8 mod 32) and planes a multiple of 32 entries
-// apart, so that the warp's 8 x 4 pixels read 32 distinct banks whatever disparity each needs
-constexpr int kScRPW = 72;
+// Refinement planes: rows of kScRPW entries and planes a multiple of 32 entries apart, so that
+// a warp's 32 pixels of one row read 32 distinct banks whatever disparity each needs
+constexpr int kScRPW = 44;
 __host__ __device__ constexpr int sc_psz(int qh) { return (qh * kScRPW + 31) / 32 * 32; }
 constexpr int kScWSh = 12;      // weights scaled by 2^12 before rounding to FP16
 constexpr int kScCSh = 8;       // costs scaled by 2^8
@@ -110,6 +110,219 @@ template <> __device__ __forceinline__ uint32_t pack_rn<__nv_bfloat16>(float lo,
     uint32_t r;
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
     return r;
+}
+
+// ---- refinement of one tile (k_fused's FP32 arithmetic over each pixel's certified candidates)
+//
+// The range of pixel (u, v) is [dlo - 1, dhi + 1] (range_of(py, px) gives {dlo, dhi}; with B2
+// every disparity), clipped at df + 1, df = max(0, u + m - L + 1), where L is the shortest run of
+// target values equal to their row's column 0 over the rows v - m .. v + m (row table, .w).  For
+// d >= df every target read behind the pixel falls at a column below L (or in the replicate
+// padding left of column 0) and returns its row's column-0 value, so each block, its statistics
+// and each cost c(q, d) are the same for all such d: E(p, d) = E(p, df) exactly (the same terms in
+// the same order).  The lowest d wins ties, so d* <= df and d* + 1 stays inside the clipped range,
+// and E(df) stands for the whole tail in the smallest E over d != d*: the cut changes none of the
+// outputs.
+//
+// Each thread owns a column of RPY pixels (column lane, rows RPY warp ..), as the SIMT kernel's
+// aggregation does: its loads serve every pixel of the column.  The tile's candidates are
+// refined in chunks of DCR disparities (4 when they span at most 4) from the tile's lowest one;
+// the FP32 costs come from the two-pass cost phase (the same integers and the same rounding as
+// k_fused's costs), stored as planes of [QH][kScRPW] entries sc_psz(QH) apart.
+//
+// On entry: the tile's images are staged; sIr ([QH][kScRPW], the scaled reference intensities
+// of the cost positions) and sKr ([KB][12], the spatial exponents K[dx][dy]) are written; *s_rlo
+// = INT_MAX and *s_rhi = -1; and range_of's data are visible to every thread.  The function
+// synchronises before it reads sIr and returns after the epilogue, without a final barrier.
+template <int RB, bool B2, int NT, int DCR, int RKSEG, typename RangeOf>
+__device__ __forceinline__ void sc_refine(const FusedArgs &a, const uint8_t *sref, const uint8_t *stgt, float *cb32,
+                                          int *vband, int2 *sstr, int2 *sstt, const float *sIr, const float *sKr,
+                                          int x0, int y0, int tid, int *s_rlo, int *s_rhi, RangeOf range_of)
+{
+    constexpr int TX = tile_x(kScWC), TY = tile_y(kScWC);
+    constexpr int KB = 2 * RB + 1, QH = TY + 2 * RB;
+    constexpr int RPW = kScRPW, PSZ = sc_psz(QH);
+    constexpr int NW = NT / 32, RPY = TY / NW;
+    static_assert(TX == 32 && TY % NW == 0, "one warp per strip of RPY rows");
+    static_assert(DCR == 4 || DCR == 8, "refinement chunks of 4 or 8 disparities");
+    const int lane = tid & 31, warp = tid >> 5;
+    const int px = lane, py0 = warp * RPY;
+    int rlo[RPY], rhi[RPY];
+    {
+        int ulo = 0x7fffffff, uhi = -1;
+#pragma unroll
+        for (int i = 0; i < RPY; ++i) {
+            const int u = x0 + px, v = y0 + py0 + i;
+            rlo[i] = 1;   // nothing to refine outside the image
+            rhi[i] = 0;
+            if (u < a.W && v < a.H) {
+                const int lmin = __ldg(&a.row_tab[v].w);
+                const int cap = min(a.D - 1, max(0, u + a.m - lmin + 1) + 1);
+                const int2 rg = B2 ? make_int2(0, 0) : range_of(py0 + i, px);
+                rlo[i] = B2 ? 0 : max(rg.x - 1, 0);
+                rhi[i] = min(B2 ? a.D - 1 : rg.y + 1, cap);
+                ulo = min(ulo, rlo[i]);
+                uhi = max(uhi, rhi[i]);
+            }
+        }
+        ulo = __reduce_min_sync(0xffffffffu, ulo);
+        uhi = __reduce_max_sync(0xffffffffu, uhi);
+        if (lane == 0 && uhi >= 0) {
+            atomicMin(s_rlo, ulo);
+            atomicMax(s_rhi, uhi);
+        }
+    }
+    __syncthreads();
+    const int ulo_t = *s_rlo, uhi_t = *s_rhi;
+    const int rw = a.rw;
+
+    float best[RPY], bm1[RPY], bp1[RPY], prev[RPY], sec[B2 ? RPY : 1];
+    int bd[RPY];
+    float ip[RPY];
+    int tlo = 0x7fffffff, thi = -1;   // the union of this thread's ranges
+#pragma unroll
+    for (int i = 0; i < RPY; ++i) {
+        best[i] = __int_as_float(0x7f800000);
+        bm1[i] = bp1[i] = prev[i] = best[i];
+        if constexpr (B2) sec[i] = best[i];
+        bd[i] = -1;
+        ip[i] = sIr[(py0 + i + RB) * RPW + px + RB];
+        if (rlo[i] <= rhi[i]) {
+            tlo = min(tlo, rlo[i]);
+            thi = max(thi, rhi[i]);
+        }
+    }
+    const int dcr = (DCR == 4 || uhi_t - ulo_t < 4) ? 4 : DCR;
+    const float2 *cb2 = reinterpret_cast<const float2 *>(cb32);
+    for (int cb = ulo_t; cb <= uhi_t; cb += dcr) {
+        if (DCR == 4 || dcr == 4) {
+            switch (rw) {
+            case 1: cost_chunk<RB, 4, 1, float, TX, TY, NT, 0, kScBand, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+            case 2: cost_chunk<RB, 4, 2, float, TX, TY, NT, 0, kScBand, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+            case 3: cost_chunk<RB, 4, 3, float, TX, TY, NT, 0, kScBand, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+            case 4: cost_chunk<RB, 4, 4, float, TX, TY, NT, 0, kScBand, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+            default: cost_chunk<RB, 4, 5, float, TX, TY, NT, 0, kScBand, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+            }
+        } else {
+            constexpr int D8 = DCR == 4 ? 4 : 8;
+            switch (rw) {
+            case 1: cost_chunk<RB, D8, 1, float, TX, TY, NT, 0, kScBand, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+            case 2: cost_chunk<RB, D8, 2, float, TX, TY, NT, 0, kScBand, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+            case 3: cost_chunk<RB, D8, 3, float, TX, TY, NT, 0, kScBand, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+            case 4: cost_chunk<RB, D8, 4, float, TX, TY, NT, 0, kScBand, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+            default: cost_chunk<RB, D8, 5, float, TX, TY, NT, 0, kScBand, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+            }
+        }
+        // One pass per thread and chunk: disparities dw .. dw + 2 NPP - 1 from the pair below
+        // the thread's lowest candidate in the chunk, NPP pairs (the warp's largest need; 2 or
+        // 4).  Pairs past the chunk read its last pair (their sums are discarded), and so do the
+        // threads with nothing to refine in the chunk.
+        const int lo = max(tlo, cb), hi = min(thi, cb + dcr - 1);
+        const int dw = lo <= hi ? cb + ((lo - cb) & ~1) : cb;
+        const int need = lo <= hi ? (hi - dw) / 2 + 1 : 0;
+        const int wneed = __reduce_max_sync(0xffffffffu, need);
+        auto pass = [&](auto npp_c) {
+            constexpr int NPP = decltype(npp_c)::value;
+            int o[NPP];
+#pragma unroll
+            for (int k = 0; k < NPP; ++k) o[k] = min((dw - cb) / 2 + k, dcr / 2 - 1) * PSZ;
+            float2 e[RPY][NPP];
+#pragma unroll
+            for (int i = 0; i < RPY; ++i)
+#pragma unroll
+                for (int k = 0; k < NPP; ++k) e[i][k] = make_float2(0.f, 0.f);
+            const float *ib = sIr + py0 * RPW + px;
+            const float2 *cq = cb2 + py0 * RPW + px;
+#pragma unroll 1
+            for (int dx = 0; dx < KB; ++dx) {
+                float kr[12];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float4 q = *reinterpret_cast<const float4 *>(sKr + dx * 12 + 4 * k);
+                    kr[4 * k] = q.x;
+                    kr[4 * k + 1] = q.y;
+                    kr[4 * k + 2] = q.z;
+                    kr[4 * k + 3] = q.w;
+                }
+                // neighbour rows of the column, in increasing order: for every pixel the window
+                // rows come in k_fused's order (row inner, column outer); each FMA of a pair is
+                // the scalar FMA of k_fused (same operands, one rounding)
+#pragma unroll
+                for (int r = 0; r < RPY + 2 * RB; ++r) {
+                    const float iq = ib[r * RPW + dx];
+                    float2 c[NPP];
+#pragma unroll
+                    for (int k = 0; k < NPP; ++k) c[k] = cq[r * RPW + dx + o[k]];
+#pragma unroll
+                    for (int i = 0; i < RPY; ++i) {
+                        const int dy = r - i;
+                        if (dy < 0 || dy > 2 * RB) continue;
+                        const float t = iq - ip[i];
+                        const float w = ex2_approx(fmaf(-t, t, kr[dy]));
+                        const float2 w2 = make_float2(w, w);
+#pragma unroll
+                        for (int k = 0; k < NPP; ++k) e[i][k] = __ffma2_rn(w2, c[k], e[i][k]);
+                    }
+                }
+            }
+            // k_fused's running WTA, in increasing d
+#pragma unroll
+            for (int i = 0; i < RPY; ++i)
+#pragma unroll
+                for (int j = 0; j < 2 * NPP; ++j) {
+                    const int d = dw + j;
+                    if (d < rlo[i] || d > rhi[i] || d > hi) continue;
+                    const float v = (j & 1) ? e[i][j >> 1].y : e[i][j >> 1].x;
+                    if (v < best[i]) {
+                        if constexpr (B2) sec[i] = best[i];
+                        best[i] = v;
+                        bd[i] = d;
+                        bm1[i] = prev[i];
+                    } else {
+                        if constexpr (B2) sec[i] = fminf(sec[i], v);
+                        if (d == bd[i] + 1) bp1[i] = v;
+                    }
+                    prev[i] = v;
+                }
+        };
+        if (wneed > 2) pass(std::integral_constant<int, 4>());
+        else if (wneed > 0) pass(std::integral_constant<int, 2>());
+        __syncthreads();
+    }
+
+    // ---- epilogue: eq. (subpixel), add back s_i(v), validity from the row table (k_fused's)
+#pragma unroll
+    for (int i = 0; i < RPY; ++i) {
+        const int py = py0 + i;
+        const int u = x0 + px, v = y0 + py;
+        if (u >= a.W || v >= a.H) continue;
+        const int4 rt = __ldg(a.row_tab + v);   // {s_i(v), max s_i, min s_i over v +- m, run}
+        float delta = 0.f;
+        if (bd[i] > 0 && bd[i] < a.D - 1) {
+            const float den = 2.f * bm1[i] + 2.f * bp1[i] - 4.f * best[i];
+            if (den > 0.f) delta = (bm1[i] - bp1[i]) / den;
+        }
+        const size_t o = (size_t)v * a.W + u;
+        a.disp[o] = (float)bd[i] + delta + (float)rt.x;
+        if (a.wta) a.wta[o] = bd[i];
+        if (a.valid) {
+            const int ulo = a.m + a.D - 1 + max(0, rt.y);
+            const int uhi = a.W - 1 - a.m + min(0, rt.z);
+            a.valid[o] = (uint8_t)(v >= a.m && v <= a.H - 1 - a.m && u >= ulo && u <= uhi);
+        }
+        if constexpr (B2) {
+            // the skipped normaliser sum_q w(p,q), as k_fused sums it
+            const float ipp = sIr[(py + RB) * RPW + px + RB];
+            float ws = 0.f;
+            for (int dx = 0; dx < KB; ++dx)
+                for (int dy = 0; dy < KB; ++dy) {
+                    const float t = sIr[(py + dy) * RPW + px + dx] - ipp;
+                    ws += ex2_approx(fmaf(-t, t, a.K[dx * KB + dy]));
+                }
+            a.best2[2 * o] = best[i] / ws;
+            a.best2[2 * o + 1] = sec[i] / ws;
+        }
+    }
 }
 
 // MODE: kScScreened (the FP32 screened form), or kScPlain (the FP16 / BF16 storage form: the
@@ -471,62 +684,7 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
                 }
         }
         __syncthreads();
-
-        // ---- the tile's refinement range: [dlo - 1, dhi + 1] of every pixel inside the image,
-        // clipped at df + 1, df = max(0, u + m - L + 1), where L is the shortest run of target
-        // values equal to their row's column 0 over the rows v - m .. v + m (row table, .w).
-        // For d >= df every target read behind pixel (u, v) falls at a column below L (or in
-        // the replicate padding left of column 0) and returns its row's column-0 value, so each
-        // block, its statistics and each cost c(q, d) are the same for all such d: E(p, d) =
-        // E(p, df) exactly (the same terms in the same order).  The lowest d wins ties, so
-        // d* <= df and d* + 1 stays inside the clipped range, and E(df) stands for the whole
-        // tail in the smallest E over d != d*: the cut changes none of the outputs.
-        // From here on each thread owns a column of RPY pixels (column lane, rows RPY warp ..),
-        // as the SIMT kernel's aggregation does: its loads serve every pixel of the column.
-        constexpr int RPY = TY / kWarps;              // 3
-        static_assert(TX == 32 && TY % kWarps == 0, "one warp per strip of RPY rows");
-        const int px = lane, py0 = warp * RPY;
-        int rlo[RPY], rhi[RPY];
-        {
-            int ulo = 0x7fffffff, uhi = -1;
-#pragma unroll
-            for (int i = 0; i < RPY; ++i) {
-                const int u = x0 + px, v = y0 + py0 + i;
-                const int lmin = (v < a.H) ? __ldg(&a.row_tab[v].w) : 1;
-                const int cap = min(a.D - 1, max(0, u + a.m - lmin + 1) + 1);
-                const int2 rg = B2 ? make_int2(0, 0) : srange[(py0 + i) * TX + px];
-                rlo[i] = B2 ? 0 : max(rg.x - 1, 0);
-                rhi[i] = min(B2 ? a.D - 1 : rg.y + 1, cap);
-                if (u < a.W && v < a.H) {
-                    ulo = min(ulo, rlo[i]);
-                    uhi = max(uhi, rhi[i]);
-                } else {
-                    rlo[i] = 1;   // nothing to refine
-                    rhi[i] = 0;
-                }
-            }
-            ulo = __reduce_min_sync(0xffffffffu, ulo);
-            uhi = __reduce_max_sync(0xffffffffu, uhi);
-            if (lane == 0 && uhi >= 0) {
-                atomicMin(&s_rlo, ulo);
-                atomicMax(&s_rhi, uhi);
-            }
-        }
-        __syncthreads();
-        const int ulo_t = s_rlo, uhi_t = s_rhi;
-
-        // ---- refinement: k_fused's FP32 arithmetic and running WTA over the candidates, in
-        // chunks of DCR disparities from the tile's lowest candidate.  The FP32 costs come from
-        // the two-pass cost phase (the same integers and the same rounding as k_fused's costs).
-        float best[RPY], bm1[RPY], bp1[RPY], prev[RPY], sec[B2 ? RPY : 1];
-        int bd[RPY];
-#pragma unroll
-        for (int i = 0; i < RPY; ++i) {
-            best[i] = __int_as_float(0x7f800000);
-            bm1[i] = bp1[i] = prev[i] = best[i];
-            if constexpr (B2) sec[i] = best[i];
-            bd[i] = -1;
-        }
+        // ---- refinement of the candidates
         float *sIr = reinterpret_cast<float *>(smem + L.escr + kScRefOff);   // [QH][RPW]
         float *sKr = sIr + QH * RPW;                                           // [KB][12]
         for (int i = tid; i < QH * RPW; i += kThreads) {
@@ -537,138 +695,8 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
             const int dx = i / 12, dy = i - dx * 12;
             sKr[i] = dy < KB ? a.K[dx * KB + dy] : 0.f;
         }
-        float ip[RPY];
-        int tlo = 0x7fffffff, thi = -1;   // the union of this thread's ranges
-#pragma unroll
-        for (int i = 0; i < RPY; ++i) {
-            ip[i] = sI[(py0 + i + RB) * QWI + px + RB];
-            if (rlo[i] <= rhi[i]) {
-                tlo = min(tlo, rlo[i]);
-                thi = max(thi, rhi[i]);
-            }
-        }
-        // (the first refinement chunk's cost phase synchronises before the tables are read)
-        // refinement chunks of DCR disparities; a tile whose candidates span at most 4 takes one
-        // chunk of 4 (half the walkers and items of the two-pass phase)
-        const int dcr = (uhi_t - ulo_t < 4) ? 4 : DCR;
-        for (int cb = ulo_t; cb <= uhi_t; cb += dcr) {
-            if (dcr == 4) {
-                switch (rw) {
-                case 1: cost_chunk<RB, 4, 1, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
-                case 2: cost_chunk<RB, 4, 2, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
-                case 3: cost_chunk<RB, 4, 3, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
-                case 4: cost_chunk<RB, 4, 4, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
-                default: cost_chunk<RB, 4, 5, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
-                }
-            } else {
-                switch (rw) {
-                case 1: cost_chunk<RB, DCR, 1, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
-                case 2: cost_chunk<RB, DCR, 2, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
-                case 3: cost_chunk<RB, DCR, 3, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
-                case 4: cost_chunk<RB, DCR, 4, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
-                default: cost_chunk<RB, DCR, 5, float, TX, TY, kThreads, 0, kScBand, false, 0, RPW, PSZ>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
-                }
-            }
-            const int lo = max(tlo, cb), hi = min(thi, cb + dcr - 1);
-            // four disparities per pass, d = dw .. dw + 3 (reads past the chunk clamped; their
-            // sums are discarded)
-#pragma unroll 1
-            for (int dw = lo; dw <= hi; dw += 4) {
-                int o[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) o[j] = min(dw + j - cb, dcr - 1) * PSZ;
-                float e[RPY][4];
-#pragma unroll
-                for (int i = 0; i < RPY; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) e[i][j] = 0.f;
-                const float *ib = sIr + py0 * RPW + px;
-                const float *cq = cb32 + py0 * RPW + px;
-#pragma unroll 1
-                for (int dx = 0; dx < KB; ++dx) {
-                    float kr[12];
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        const float4 q = *reinterpret_cast<const float4 *>(sKr + dx * 12 + 4 * k);
-                        kr[4 * k] = q.x;
-                        kr[4 * k + 1] = q.y;
-                        kr[4 * k + 2] = q.z;
-                        kr[4 * k + 3] = q.w;
-                    }
-                    // neighbour rows of the column, in increasing order: for every pixel the
-                    // window rows come in k_fused's order (row inner, column outer)
-#pragma unroll
-                    for (int r = 0; r < RPY + 2 * RB; ++r) {
-                        const float iq = ib[r * RPW + dx];
-                        float c[4];
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) c[j] = cq[r * RPW + dx + o[j]];
-#pragma unroll
-                        for (int i = 0; i < RPY; ++i) {
-                            const int dy = r - i;
-                            if (dy < 0 || dy > 2 * RB) continue;
-                            const float t = iq - ip[i];
-                            const float w = ex2_approx(fmaf(-t, t, kr[dy]));
-#pragma unroll
-                            for (int j = 0; j < 4; ++j) e[i][j] = fmaf(w, c[j], e[i][j]);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < RPY; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int d = dw + j;
-                        if (d < rlo[i] || d > rhi[i] || d > hi) continue;
-                        const float v = e[i][j];
-                        if (v < best[i]) {
-                            if constexpr (B2) sec[i] = best[i];
-                            best[i] = v;
-                            bd[i] = d;
-                            bm1[i] = prev[i];
-                        } else {
-                            if constexpr (B2) sec[i] = fminf(sec[i], v);
-                            if (d == bd[i] + 1) bp1[i] = v;
-                        }
-                        prev[i] = v;
-                    }
-            }
-            __syncthreads();
-        }
-
-        // ---- epilogue: eq. (subpixel), add back s_i(v), validity from the row table (k_fused's)
-#pragma unroll
-        for (int i = 0; i < RPY; ++i) {
-            const int py = py0 + i;
-            const int u = x0 + px, v = y0 + py;
-            if (u >= a.W || v >= a.H) continue;
-            const int4 rt = __ldg(a.row_tab + v);   // {s_i(v), max s_i, min s_i over v +- m, run}
-            float delta = 0.f;
-            if (bd[i] > 0 && bd[i] < a.D - 1) {
-                const float den = 2.f * bm1[i] + 2.f * bp1[i] - 4.f * best[i];
-                if (den > 0.f) delta = (bm1[i] - bp1[i]) / den;
-            }
-            const size_t o = (size_t)v * a.W + u;
-            a.disp[o] = (float)bd[i] + delta + (float)rt.x;
-            if (a.wta) a.wta[o] = bd[i];
-            if (a.valid) {
-                const int ulo = a.m + a.D - 1 + max(0, rt.y);
-                const int uhi = a.W - 1 - a.m + min(0, rt.z);
-                a.valid[o] = (uint8_t)(v >= a.m && v <= a.H - 1 - a.m && u >= ulo && u <= uhi);
-            }
-            if constexpr (B2) {
-                // the skipped normaliser sum_q w(p,q), as k_fused sums it
-                const float ipp = sI[(py + RB) * QWI + px + RB];
-                float ws = 0.f;
-                for (int dx = 0; dx < KB; ++dx)
-                    for (int dy = 0; dy < KB; ++dy) {
-                        const float t = sI[(py + dy) * QWI + px + dx] - ipp;
-                        ws += ex2_approx(fmaf(-t, t, a.K[dx * KB + dy]));
-                    }
-                a.best2[2 * o] = best[i] / ws;
-                a.best2[2 * o + 1] = sec[i] / ws;
-            }
-        }
+        sc_refine<RB, B2, kThreads, DCR, kSeg>(a, sref, stgt, cb32, vband, sstr, sstt, sIr, sKr, x0, y0, tid, &s_rlo, &s_rhi,
+                                         [&](int py, int px) { return srange[py * TX + px]; });
     }  // tile loop
 }
 

@@ -82,10 +82,11 @@ def test_batch_equals_single_pair_calls():
     check_disparity(outs[2][0], None, d_o, ds_o, eb, es, min_sure=0.8)
 
 
-@pytest.mark.parametrize("wc,dc", [(1, 12), (4, 12), (2, 4), (8, 12)])
+@pytest.mark.parametrize("wc,dc", [(1, 12), (4, 12), (2, 4), (8, 12), (32, 32)])
 def test_every_tile_configuration_gives_the_same_result(wc, dc):
     """5 x 5 windows, where the 128 x 16 tile's shared memory fits too; wc = 8 is the
-    warp-specialised kernel (producer and consumer warps, two cost buffers)."""
+    warp-specialised kernel (producer and consumer warps, two cost buffers); wc = 32 the
+    screened form (screening kernel, then the refinement kernel over the same work list)."""
     ss = scenes()
     ref, _, _ = run_batch(ss, win=5, bil=5)
     got, cfg, _ = run_batch(ss, wc=wc, dc=dc, win=5, bil=5)
@@ -94,7 +95,7 @@ def test_every_tile_configuration_gives_the_same_result(wc, dc):
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
 
 
-@pytest.mark.parametrize("wc", [2, 8])
+@pytest.mark.parametrize("wc", [2, 8, 32])
 def test_many_tiles_per_cta_with_mixed_search_ranges(wc):
     """More tiles than CTAs, pairs of different search ranges interleaved in the work list:
     every CTA moves between pairs whose shared-memory layouts differ."""
@@ -102,7 +103,7 @@ def test_many_tiles_per_cta_with_mixed_search_ranges(wc):
     ss = [synth.make_scene(W, H, D, 700 + i, roll=0.02, coeffs=(6.0, 0.1, 0.0), n_potholes=0, warp=True,
                            win=5, bil=5) for i, (W, H, D) in enumerate(sizes)]
     qs = [buffers(s, D) for s, (_, _, D) in zip(ss, sizes)]
-    with sg.StereoBatch(qs, win=5, bil=5, sigma0=3.0, sigma1=10.0, tile_wc=wc, tile_dc=12) as b:
+    with sg.StereoBatch(qs, win=5, bil=5, sigma0=3.0, sigma1=10.0, tile_wc=wc, tile_dc=32 if wc == 32 else 12) as b:
         assert b.config()["items"] > 4 * 152
         b.run()
         torch.cuda.synchronize()
