@@ -33,6 +33,7 @@ namespace sgb {
 
 constexpr int kScDC = 32;       // disparities per screening chunk
 constexpr int kScDCR = 8;       // disparities per FP32 refinement chunk
+constexpr int kScRBand4 = 12;   // cost rows per band of a 4-disparity refinement chunk (8: kScBand)
 constexpr int kScBand = 6;      // cost rows per band of the screening chunk's cost phase
 constexpr int kScSeg = 6;       // cost columns per horizontal work item (6 rows x 7 segments x 8 quads = 336 items)
 constexpr int kScQWI = 44;      // row length of the staged FP32 intensities (>= QW, >= 28 + 16)
@@ -197,11 +198,11 @@ __device__ __forceinline__ void sc_refine(const FusedArgs &a, const uint8_t *sre
     for (int cb = ulo_t; cb <= uhi_t; cb += dcr) {
         if (DCR == 4 || dcr == 4) {
             switch (rw) {
-            case 1: cost_chunk<RB, 4, 1, float, TX, TY, NT, 0, kScBand, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
-            case 2: cost_chunk<RB, 4, 2, float, TX, TY, NT, 0, kScBand, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
-            case 3: cost_chunk<RB, 4, 3, float, TX, TY, NT, 0, kScBand, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
-            case 4: cost_chunk<RB, 4, 4, float, TX, TY, NT, 0, kScBand, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
-            default: cost_chunk<RB, 4, 5, float, TX, TY, NT, 0, kScBand, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+            case 1: cost_chunk<RB, 4, 1, float, TX, TY, NT, 0, kScRBand4, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+            case 2: cost_chunk<RB, 4, 2, float, TX, TY, NT, 0, kScRBand4, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+            case 3: cost_chunk<RB, 4, 3, float, TX, TY, NT, 0, kScRBand4, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+            case 4: cost_chunk<RB, 4, 4, float, TX, TY, NT, 0, kScRBand4, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+            default: cost_chunk<RB, 4, 5, float, TX, TY, NT, 0, kScRBand4, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
             }
         } else {
             constexpr int D8 = DCR == 4 ? 4 : 8;
@@ -347,7 +348,11 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
     constexpr int NPW = NPX * NPY / kWarps;      // patches per warp
     static_assert(RB <= kScMaxRB && NKS <= 16 && QW + 2 <= QWI, "a window row spans at most 16 columns");
     static_assert((NPX * NPY) % kWarps == 0 && NPW % 2 == 0, "patches must split evenly over the warps");
-    static_assert(kScBand * (TX + 2 * (RB + kMaxRW)) * kScDCR * 4 <= kScRefOff, "refinement window sums");
+    static_assert(kScBand * (TX + 2 * (RB + kMaxRW)) * kScDCR * 4 <= kScRefOff &&
+                      kScRBand4 * (TX + 2 * (RB + kMaxRW)) * 4 * 4 <= kScRefOff, "refinement window sums");
+    // the refinement's band statistics sit in the cost buffer, past its FP32 planes
+    static_assert((size_t)kScDCR * sc_psz(QH) * 4 + (size_t)kScRBand4 * (2 * QW + kScDCR - 1) * 8 <=
+                      (size_t)QH * QW * kScDC * 2, "refinement statistics");
     static_assert(kScRefOff + (QH * kScRPW + KB * 12) * 4 <= kScRangeOff, "refinement tables");
     static_assert(kScRangeOff + TY * TX * 8 <= kWarps * 2 * 16 * kScDC * 4, "candidate ranges");
     constexpr int RPW = kScRPW, PSZ = sc_psz(QH);
@@ -419,18 +424,20 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
         constexpr int NSEGR = NPY / 3;                // segments per patch column
         constexpr int NR3 = 8 + NKS;                  // window rows of a segment
         static_assert(NPY % 3 == 0 && NPX * NSEGR == 2 * kWarps, "two segments of three patches per warp");
-        // screening state of this lane's pixel m = lane & 15 of patch i of segment si (both half
-        // warps hold the same state): the running minimum of E16 and the candidate range
-        float emin[2][3];
-        int dlo[2][3], dhi[2][3];
+        // screening state of this lane's pixels g (h = 0) and g + 8 (h = 1) of patch i of segment
+        // si (the four lanes of a quad hold the same state): the running minimum of E16 and the
+        // candidate range [dlo, dhi] as dlo | dhi << 16
+        float emin[2][3][2];
+        int rng[2][3][2];
 #pragma unroll
         for (int si = 0; si < 2; ++si)
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                emin[si][i] = __int_as_float(0x7f800000);
-                dlo[si][i] = dhi[si][i] = 0;
-            }
-        float *scr = escr + warp * (16 * DC);         // one 16 x 32 E block per warp
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    emin[si][i][h] = __int_as_float(0x7f800000);
+                    rng[si][i][h] = 0;
+                }
         const int hb = lane >> 4, m = lane & 15;
         // the plain form's running WTA (k_fused's rules on the 16-bit sums): per segment, state 0
         // is pixel m of patch hb, state 1 (lanes 0-15) pixel m of patch 2
@@ -573,55 +580,52 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
                     if (hb == 0) run(0, 1);
                     __syncwarp();
                 } else {
-                    // each patch's 16 x 32 E block through the warp's scratch; lanes 0-15 take
-                    // disparities 0..15 of pixel lane & 15, lanes 16-31 disparities 16..31
-    #pragma unroll
+                    // the screening update, straight from the fragments: lane (g, t4) holds
+                    // disparities 8 nb + 2 t4 + {0, 1} (nb = 0..3) of pixels g and g + 8, and the
+                    // four lanes of a quad hold all 32 disparities of the same two pixels
+#pragma unroll
                     for (int i = 0; i < 3; ++i) {
-    #pragma unroll
-                        for (int nb = 0; nb < 4; ++nb) {
-                            const int u = 2 * nb + (t4 >> 1), o = 2 * (t4 & 1);
-                            *reinterpret_cast<float2 *>(scr + g * DC + (sc_eunit(u, g) << 2) + o) =
-                                make_float2(acc[i][nb][0], acc[i][nb][1]);
-                            *reinterpret_cast<float2 *>(scr + (g + 8) * DC + (sc_eunit(u, g + 8) << 2) + o) =
-                                make_float2(acc[i][nb][2], acc[i][nb][3]);
-                        }
-                        __syncwarp();
-                        float e[16];
-    #pragma unroll
-                        for (int uu = 0; uu < 4; ++uu) {
-                            const float4 v = *reinterpret_cast<const float4 *>(scr + m * DC + (sc_eunit(4 * hb + uu, m) << 2));
-                            e[4 * uu] = v.x;
-                            e[4 * uu + 1] = v.y;
-                            e[4 * uu + 2] = v.z;
-                            e[4 * uu + 3] = v.w;
-                        }
-                        __syncwarp();
-                        float cm = __int_as_float(0x7f800000);
-    #pragma unroll
-                        for (int dd = 0; dd < 16; ++dd) {
-                            if (16 * hb + dd >= dn) e[dd] = __int_as_float(0x7f800000);
-                            cm = fminf(cm, e[dd]);
-                        }
-                        cm = fminf(cm, __shfl_xor_sync(0xffffffffu, cm, 16));
-                        // the pixel's state, selected with static indices (no local memory)
-                        float em = emin[0][i];
-                        if (si == 1) em = emin[1][i];
-                        const float nm = fminf(em, cm);
-                        const float tn = sc_thr(nm);
-                        uint32_t mh = 0;
-    #pragma unroll
-                        for (int dd = 0; dd < 16; ++dd) mh |= (e[dd] <= tn) ? (1u << dd) : 0u;
-                        const uint32_t mo = __shfl_xor_sync(0xffffffffu, mh, 16);
-                        const uint32_t mask = hb ? (mo | (mh << 16)) : (mh | (mo << 16));
-                        const bool reset = mask && tn < em;   // the earlier range cannot hold d*
-                        const int lo = d0 + __ffs(mask) - 1, hi = d0 + 31 - __clz(mask);
-    #pragma unroll
-                        for (int k = 0; k < 2; ++k)
-                            if (k == si) {
-                                if (reset) dlo[k][i] = lo;
-                                if (mask) dhi[k][i] = hi;
-                                emin[k][i] = nm;
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            float v[8];
+#pragma unroll
+                            for (int nb = 0; nb < 4; ++nb) {
+                                v[2 * nb] = acc[i][nb][2 * h];
+                                v[2 * nb + 1] = acc[i][nb][2 * h + 1];
                             }
+                            if (dn < DC) {   // the last chunk of a search range off the chunk grid
+#pragma unroll
+                                for (int j = 0; j < 8; ++j)
+                                    if (8 * (j >> 1) + 2 * t4 + (j & 1) >= dn) v[j] = __int_as_float(0x7f800000);
+                            }
+                            float cm = v[0];
+#pragma unroll
+                            for (int j = 1; j < 8; ++j) cm = fminf(cm, v[j]);
+                            cm = fminf(cm, __shfl_xor_sync(0xffffffffu, cm, 1));
+                            cm = fminf(cm, __shfl_xor_sync(0xffffffffu, cm, 2));
+                            // the pixel's state, selected with static indices (no local memory)
+                            float em = emin[0][i][h];
+                            if (si == 1) em = emin[1][i][h];
+                            const float nm = fminf(em, cm);
+                            const float tn = sc_thr(nm);
+                            uint32_t mk = 0;
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) mk |= (v[j] <= tn) ? (1u << (8 * (j >> 1) + (j & 1))) : 0u;
+                            mk <<= 2 * t4;
+                            mk |= __shfl_xor_sync(0xffffffffu, mk, 1);
+                            mk |= __shfl_xor_sync(0xffffffffu, mk, 2);
+                            const bool reset = mk && tn < em;   // the earlier range cannot hold d*
+                            const int lo = d0 + __ffs(mk) - 1, hi = d0 + 31 - __clz(mk);
+#pragma unroll
+                            for (int k = 0; k < 2; ++k)
+                                if (k == si) {
+                                    int r = rng[k][i][h];
+                                    if (reset) r = (r & ~0xffff) | lo;
+                                    if (mk) r = (r & 0xffff) | (hi << 16);
+                                    rng[k][i][h] = r;
+                                    emin[k][i][h] = nm;
+                                }
+                        }
                     }
                 }
             }
@@ -673,15 +677,17 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
 
         // the candidate ranges, per pixel of the tile, for the refinement's own pixel layout
         int2 *srange = reinterpret_cast<int2 *>(smem + L.escr + kScRangeOff);   // [TY][TX]
-        if (!B2 && hb == 0) {
+        if (!B2 && t4 == 0) {
 #pragma unroll
             for (int si = 0; si < 2; ++si)
 #pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const int sg = warp + kWarps * si;
-                    const int px = (sg % NPX) * 4 + (m & 3), py = (sg / NPX) * 12 + 4 * i + (m >> 2);
-                    srange[py * TX + px] = make_int2(dlo[si][i], dhi[si][i]);
-                }
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int sg = warp + kWarps * si;
+                        const int px = (sg % NPX) * 4 + mx, py = (sg / NPX) * 12 + 4 * i + my0 + 2 * h;
+                        srange[py * TX + px] = make_int2(rng[si][i][h] & 0xffff, rng[si][i][h] >> 16);
+                    }
         }
         __syncthreads();
         // ---- refinement of the candidates
@@ -695,7 +701,9 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
             const int dx = i / 12, dy = i - dx * 12;
             sKr[i] = dy < KB ? a.K[dx * KB + dy] : 0.f;
         }
-        sc_refine<RB, B2, kThreads, DCR, kSeg>(a, sref, stgt, cb32, vband, sstr, sstt, sIr, sKr, x0, y0, tid, &s_rlo, &s_rhi,
+        int2 *rstr = reinterpret_cast<int2 *>(cb32 + (size_t)DCR * PSZ);   // [kScRBand4][QW]
+        int2 *rstt = rstr + kScRBand4 * QW;                                  // [kScRBand4][QW + DCR - 1]
+        sc_refine<RB, B2, kThreads, DCR, kSeg>(a, sref, stgt, cb32, vband, rstr, rstt, sIr, sKr, x0, y0, tid, &s_rlo, &s_rhi,
                                          [&](int py, int px) { return srange[py * TX + px]; });
     }  // tile loop
 }
