@@ -21,11 +21,12 @@
 // previous minimum drops the earlier range (none of its disparities can satisfy the final test).
 //
 // Refinement.  After the last chunk the tile refines [dlo - 1, dhi + 1] of every pixel with
-// k_fused's arithmetic: FP32 costs from the tensor-core cost phase (cost_chunk_mma, bit for bit
-// k_fused's), the weight ex2(fma(-t, t, K)), and the 121-term FMA chain in k_fused's order
-// (window column outer, row inner), then k_fused's running WTA in increasing d.  The winner and
-// its two neighbours (the parabola of eq. subpixel) are therefore k_fused's values exactly.
-// With the best2 output (B2) every pixel refines all D disparities (a diagnostic path).
+// k_fused's arithmetic (sc_refine): FP32 costs from the two-pass cost phase (the same integers
+// and roundings as k_fused's), the weight ex2(fma(-t, t, K)), and the 121-term FMA chain in
+// k_fused's order (window column outer, row inner), then k_fused's running WTA in increasing d.
+// The winner and its two neighbours (the parabola of eq. subpixel) are therefore k_fused's
+// values exactly.  With the best2 output (B2) every pixel refines all D disparities (a
+// diagnostic path).
 #pragma once
 #include "k_fused_tc.cuh"
 
@@ -34,6 +35,7 @@ namespace sgb {
 constexpr int kScDC = 32;       // disparities per screening chunk
 constexpr int kScDCR = 8;       // disparities per FP32 refinement chunk
 constexpr int kScRBand4 = 12;   // cost rows per band of a 4-disparity refinement chunk (8: kScBand)
+constexpr int kScRSeg = 3;      // cost columns per horizontal work item of the refinement chunks
 constexpr int kScBand = 6;      // cost rows per band of the screening chunk's cost phase
 constexpr int kScSeg = 6;       // cost columns per horizontal work item (6 rows x 7 segments x 8 quads = 336 items)
 constexpr int kScQWI = 44;      // row length of the staged FP32 intensities (>= QW, >= 28 + 16)
@@ -56,18 +58,19 @@ __device__ __forceinline__ float sc_thr(float m) { return fmaf(m + kScAbs, kScRh
 // Shared memory of the screened form (offsets from the 128-byte aligned dynamic base):
 //   sref, stgt  image tiles (TMA), as in k_fused
 //   cbuf   screening: [QH][QW][32] FP16 costs (16-byte units swizzled by bits 1..2 of the
-//          column); refinement: 8 FP32 planes of [QH][kScRPW], sc_psz(QH) entries apart -- the
-//          same bytes
-//   escr   the cost phase's vertical window sums ([band][CW][32] i32); the same bytes hold the
-//          per-warp E blocks of the aggregation ([warp][16 pixels][32] f32, 16-byte units
-//          swizzled by the pixel); after the screening, from kScRefOff on: the intensities
-//          again as [QH][kScRPW] f32 and the spatial exponents as [2 RB + 1][12] f32, and from
-//          kScRangeOff on the candidate range of every pixel of the tile ([TY][TX] int2)
+//          column); refinement, in the same bytes: 4 planes of FP32 disparity pairs (float2
+//          [QH][kScRPW], sc_psz(QH) entries apart), then the window statistics of a band
+//   escr   the cost phase's vertical window sums ([band][CW][32] i32); the same bytes hold, in
+//          the 16-bit form, two per-warp E blocks of the aggregation ([warp][2][16 pixels][32]
+//          f32, 16-byte units swizzled by the pixel); after the screening the refinement's
+//          vertical sums, from kScRefOff on the intensities again as [QH][kScRPW] f32 and the
+//          spatial exponents as [2 RB + 1][12] f32, and from kScRangeOff on the candidate range
+//          of every pixel of the tile ([TY][TX] int2)
 //   sstr, sstt  window statistics of one band
 //   sI     [QH][kScQWI] f32  the reference intensities times sqrt(log2 e) / sigma1 of the cost
 //          positions (1e18 outside the image, as in k_fused)
 //   skxy   the row terms of the spatial exponent, (nKy(j), nKy(j - 2)) for j = -1 .. 3 + 2 RB
-//          (float2; the region keeps its earlier, larger size)
+//          (float2)
 struct ScLayout {
     size_t sref, stgt, cbuf, escr, sstr, sstt, sI, skxy, total;
 };
@@ -87,7 +90,7 @@ __host__ __device__ inline ScLayout sc_layout(int rb, int m, int ref_box_w, int 
     L.sstt = align_up(L.sstr + (size_t)kScBand * QW * 8, 16);
     L.sI = align_up(L.sstt + (size_t)kScBand * (QW + kScDC - 1) * 8, 16);
     L.skxy = align_up(L.sI + (size_t)QH * kScQWI * 4, 16);
-    L.total = align_up(L.skxy + (size_t)NKS * 32 * 32, 128);
+    L.total = align_up(L.skxy + (size_t)(NKS + 2) * 8, 128);
     return L;
 }
 
@@ -703,7 +706,7 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
         }
         int2 *rstr = reinterpret_cast<int2 *>(cb32 + (size_t)DCR * PSZ);   // [kScRBand4][QW]
         int2 *rstt = rstr + kScRBand4 * QW;                                  // [kScRBand4][QW + DCR - 1]
-        sc_refine<RB, B2, kThreads, DCR, kSeg>(a, sref, stgt, cb32, vband, rstr, rstt, sIr, sKr, x0, y0, tid, &s_rlo, &s_rhi,
+        sc_refine<RB, B2, kThreads, DCR, kScRSeg>(a, sref, stgt, cb32, vband, rstr, rstt, sIr, sKr, x0, y0, tid, &s_rlo, &s_rhi,
                                          [&](int py, int px) { return srange[py * TX + px]; });
     }  // tile loop
 }
