@@ -184,8 +184,9 @@ int launch_prep(stereo_ctx *ctx, const uint8_t *ref, const uint8_t *tgtw, cudaSt
 // left, so a read of row y at any column below L(y) returns the value of column 0: the
 // screened fused form uses this to find the disparities beyond which every cost behind a
 // pixel no longer changes.  A block of kRowTab rows first rounds its rows and an m-row halo on
-// each side once and measures their runs (one warp per row, 32 columns per step), then takes
-// the window extremes from shared memory.
+// each side once and measures their runs (each warp a set of rows, 256 columns per step, the
+// first step of all of them loaded together), then takes the window extremes from shared
+// memory.
 constexpr int kRowTab = 32, kRowTabHalo = 16;   // m = rw + bilateral radius <= 12
 constexpr int kRowThreads = 256;
 
@@ -200,18 +201,50 @@ __global__ void __launch_bounds__(kRowThreads) k_row_tables(const float *__restr
         si[i] = (y >= 0 && y < H) ? (int)round_half_up(__ldg(shift + y)) : 0;
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int i = wid; i < kRowTab + 2 * m; i += kRowThreads / 32) {
-        const int y = v0 - m + i;
+    constexpr int kWarpsR = kRowThreads / 32, kRowsPerWarp = (kRowTab + 2 * kRowTabHalo) / kWarpsR;
+    static_assert((kRowTab + 2 * kRowTabHalo) % kWarpsR == 0, "rows split evenly over the warps");
+    // 256 columns of a row per step, 8 per lane (8-byte loads where the rows allow them); the
+    // first step of every row of the warp is loaded up front, so that their loads are in flight
+    // together, and a row that holds one value over it continues step by step
+    const bool al8 = ((reinterpret_cast<uintptr_t>(tgt) | (uintptr_t)pitch) & 7) == 0;
+    uint2 first[kRowsPerWarp];
+    int c0v[kRowsPerWarp];
+#pragma unroll
+    for (int k = 0; k < kRowsPerWarp; ++k) {
+        const int i = wid + k * kWarpsR, y = v0 - m + i;
+        first[k] = make_uint2(0u, 0u);
+        c0v[k] = 0;
+        if (i < kRowTab + 2 * m && y >= 0 && y < H) {
+            const uint8_t *row = tgt + (size_t)y * pitch;
+            c0v[k] = __ldg(row);
+            if (al8 && 8 * lane + 8 <= W) first[k] = __ldg(reinterpret_cast<const uint2 *>(row + 8 * lane));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kRowsPerWarp; ++k) {
+        const int i = wid + k * kWarpsR, y = v0 - m + i;   // warp-uniform
+        if (i >= kRowTab + 2 * m) break;
         int run = 1;
         if (y >= 0 && y < H) {
             const uint8_t *row = tgt + (size_t)y * pitch;
-            const uint8_t c0 = __ldg(row);
+            const int c0 = c0v[k];
             run = W;
-            for (int c = 0; c < W; c += 32) {
-                const bool other = c + lane < W && __ldg(row + c + lane) != c0;
-                const unsigned b = __ballot_sync(0xffffffffu, other);
-                if (b) {
-                    run = c + __ffs(b) - 1;
+            for (int c = 0; c < W; c += 256) {
+                const int x = c + 8 * lane;
+                int off = 8;   // the lane's first column (of 8) that differs from column 0
+                if (al8 && x + 8 <= W) {
+                    const uint2 q = c == 0 ? first[k] : __ldg(reinterpret_cast<const uint2 *>(row + x));
+#pragma unroll
+                    for (int j = 7; j >= 0; --j)
+                        if ((int)(((j < 4 ? q.x : q.y) >> (8 * (j & 3))) & 0xffu) != c0) off = j;
+                } else {
+                    for (int j = 7; j >= 0; --j)
+                        if (x + j < W && (int)__ldg(row + x + j) != c0) off = j;
+                }
+                const unsigned bm = __ballot_sync(0xffffffffu, off < 8);
+                if (bm) {
+                    const int src = __ffs(bm) - 1;
+                    run = c + 8 * src + __shfl_sync(0xffffffffu, off, src);
                     break;
                 }
             }

@@ -120,6 +120,27 @@ def test_screened_flat_and_identical_images():
                 run(half, half, shift, D, 7, 9, 3.0, 10.0, sg.STEREO_FUSED_TENSOR))
 
 
+@pytest.mark.parametrize("W", [150, 600])
+def test_screened_rows_with_flat_left_runs(W):
+    """Target rows that repeat their column-0 value over runs of 1 column to the whole row (the
+    row table's run lengths, measured 256 columns per step, decide where the refinement clips
+    the flat tail): the screened form must still equal the SIMT form bit for bit."""
+    H, D = 70, 96
+    rng = np.random.default_rng(11 + W)
+    ref = synth.texture(rng, H, W)
+    tgt = np.empty_like(ref)
+    tgt[:, :W - 3] = ref[:, 3:]
+    tgt[:, W - 3:] = ref[:, -1:]
+    runs = rng.choice([1, 2, 5, 7, 8, 9, 31, 32, 33, 100, 255, 256, 257, 520, W], size=H)
+    runs = np.minimum(runs, W)
+    for v in range(H):
+        tgt[v, :runs[v]] = tgt[v, 0]
+    shift = np.zeros(H, np.float32)
+    for win, bil in ((9, 11), (5, 7)):
+        assert_same(run(ref, tgt, shift, D, win, bil, 3.0, 10.0, sg.STEREO_FUSED_SIMT),
+                    run(ref, tgt, shift, D, win, bil, 3.0, 10.0, sg.STEREO_FUSED_TENSOR))
+
+
 @pytest.mark.parametrize("W,H,D,win,bil", [(90, 50, 24, 7, 9), (64, 40, 40, 9, 11)])
 def test_screened_best2_equals_simt(W, H, D, win, bil):
     ref, tgt, shift = pair(W, H, 4, W + H)
