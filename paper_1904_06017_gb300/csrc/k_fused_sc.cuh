@@ -10,11 +10,11 @@
 // rounded once to FP16 (relative error 2^-11 in the normal range), so for every (p, d)
 //     |E16 - 2^20 E32| <= eps 2^20 E32 + a,
 // where E32 is k_fused's FP32 sum: eps covers the two FP16 roundings of each product (2^-10),
-// the tensor core's FP32 accumulation (at most 17 terms per k-step, 14 k-steps, each addition
-// within 2^-23 of the running sum, truncating or rounding: 2.8e-5), k_fused's own chain of 121
-// FMAs (7.2e-6) and the ex2 / exponent roundings of the scaled weight (1e-5): 1.02e-3, taken as
-// 1.1e-3; a (64, i.e. 6.1e-5 unscaled) covers FP16 subnormal weights and costs even if the
-// tensor core flushed them.  Hence the FP32 argmin d* (lowest d on ties) satisfies
+// the tensor core's FP32 accumulation (at most 17 terms per k-step and 16 k-steps at bil = 13,
+// each addition within 2^-23 of the running sum, truncating or rounding: 3.3e-5), k_fused's own
+// chain of at most 169 FMAs (1.0e-5) and the ex2 / exponent roundings of the scaled weight
+// (1e-5): 1.03e-3, taken as 1.1e-3; a (64, i.e. 6.1e-5 unscaled) covers FP16 subnormal weights
+// and costs even if the tensor core flushed them.  Hence the FP32 argmin d* (lowest d on ties) satisfies
 //     E16(d*) <= thr(min_d E16) = (min_d E16 + a) (1 + eps) / (1 - eps) + a,
 // and so does every d that ties it.  Each pixel keeps the range [dlo, dhi] that holds every d
 // with E16(d) <= thr(running minimum); a chunk whose minimum m makes thr(m) smaller than the
@@ -38,11 +38,16 @@ constexpr int kScRBand4 = 12;   // cost rows per band of a 4-disparity refinemen
 constexpr int kScRSeg = 3;      // cost columns per horizontal work item of the refinement chunks
 constexpr int kScBand = 6;      // cost rows per band of the screening chunk's cost phase
 constexpr int kScSeg = 6;       // cost columns per horizontal work item (6 rows x 7 segments x 8 quads = 336 items)
-constexpr int kScQWI = 44;      // row length of the staged FP32 intensities (>= QW, >= 28 + 16)
+// Row length of the staged FP32 intensities (>= QW + 2, >= 28 + 16): 44 up to bil = 11 (the
+// measured layout), 48 at bil = 13
+__host__ __device__ constexpr int sc_qwi(int rb) { return rb >= 6 ? 48 : 44; }
 // Refinement planes: rows of kScRPW entries and planes a multiple of 32 entries apart, so that
 // a warp's 32 pixels of one row read 32 distinct banks whatever disparity each needs
 constexpr int kScRPW = 44;
 __host__ __device__ constexpr int sc_psz(int qh) { return (qh * kScRPW + 31) / 32 * 32; }
+// Row length of the refinement's spatial-exponent table sKr: the 2 RB + 1 entries of a window
+// column, padded to whole 16-byte rows
+__host__ __device__ constexpr int sc_krw(int rb) { return (2 * rb + 1 + 3) / 4 * 4; }
 constexpr int kScWSh = 12;      // weights scaled by 2^12 before rounding to FP16
 constexpr int kScCSh = 8;       // costs scaled by 2^8
 constexpr float kScEps = 1.1e-3f;
@@ -67,7 +72,7 @@ __device__ __forceinline__ float sc_thr(float m) { return fmaf(m + kScAbs, kScRh
 //          spatial exponents as [2 RB + 1][12] f32, and from kScRangeOff on the candidate range
 //          of every pixel of the tile ([TY][TX] int2)
 //   sstr, sstt  window statistics of one band
-//   sI     [QH][kScQWI] f32  the reference intensities times sqrt(log2 e) / sigma1 of the cost
+//   sI     [QH][sc_qwi(RB)] f32  the reference intensities times sqrt(log2 e) / sigma1 of the cost
 //          positions (1e18 outside the image, as in k_fused)
 //   skxy   the row terms of the spatial exponent, (nKy(j), nKy(j - 2)) for j = -1 .. 3 + 2 RB
 //          (float2)
@@ -89,7 +94,7 @@ __host__ __device__ inline ScLayout sc_layout(int rb, int m, int ref_box_w, int 
     L.sstr = align_up(L.escr + (vb > eb ? vb : eb), 16);
     L.sstt = align_up(L.sstr + (size_t)kScBand * QW * 8, 16);
     L.sI = align_up(L.sstt + (size_t)kScBand * (QW + kScDC - 1) * 8, 16);
-    L.skxy = align_up(L.sI + (size_t)QH * kScQWI * 4, 16);
+    L.skxy = align_up(L.sI + (size_t)QH * sc_qwi(rb) * 4, 16);
     L.total = align_up(L.skxy + (size_t)(NKS + 2) * 8, 128);
     return L;
 }
@@ -135,7 +140,7 @@ template <> __device__ __forceinline__ uint32_t pack_rn<__nv_bfloat16>(float lo,
 // k_fused's costs), stored as planes of [QH][kScRPW] entries sc_psz(QH) apart.
 //
 // On entry: the tile's images are staged; sIr ([QH][kScRPW], the scaled reference intensities
-// of the cost positions) and sKr ([KB][12], the spatial exponents K[dx][dy]) are written; *s_rlo
+// of the cost positions) and sKr ([KB][sc_krw(RB)], the spatial exponents K[dx][dy]) are written; *s_rlo
 // = INT_MAX and *s_rhi = -1; and range_of's data are visible to every thread.  The function
 // synchronises before it reads sIr and returns after the epilogue, without a final barrier.
 template <int RB, bool B2, int NT, int DCR, int RKSEG, typename RangeOf>
@@ -147,6 +152,7 @@ __device__ __forceinline__ void sc_refine(const FusedArgs &a, const uint8_t *sre
     constexpr int KB = 2 * RB + 1, QH = TY + 2 * RB;
     constexpr int RPW = kScRPW, PSZ = sc_psz(QH);
     constexpr int NW = NT / 32, RPY = TY / NW;
+    constexpr int KRW = sc_krw(RB);
     static_assert(TX == 32 && TY % NW == 0, "one warp per strip of RPY rows");
     static_assert(DCR == 4 || DCR == 8, "refinement chunks of 4 or 8 disparities");
     const int lane = tid & 31, warp = tid >> 5;
@@ -239,10 +245,10 @@ __device__ __forceinline__ void sc_refine(const FusedArgs &a, const uint8_t *sre
             const float2 *cq = cb2 + py0 * RPW + px;
 #pragma unroll 1
             for (int dx = 0; dx < KB; ++dx) {
-                float kr[12];
+                float kr[KRW];
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const float4 q = *reinterpret_cast<const float4 *>(sKr + dx * 12 + 4 * k);
+                for (int k = 0; k < KRW / 4; ++k) {
+                    const float4 q = *reinterpret_cast<const float4 *>(sKr + dx * KRW + 4 * k);
                     kr[4 * k] = q.x;
                     kr[4 * k + 1] = q.y;
                     kr[4 * k + 2] = q.z;
@@ -345,18 +351,19 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
     constexpr int TX = tile_x(kScWC), TY = tile_y(kScWC);
     constexpr int KB = 2 * RB + 1;
     constexpr int QH = TY + 2 * RB, QW = TX + 2 * RB;
-    constexpr int QWI = kScQWI;
+    constexpr int QWI = sc_qwi(RB);
     constexpr int NKS = 4 + 2 * RB;              // k-steps: the window rows of a patch
     constexpr int NPX = TX / 4, NPY = TY / 4;    // patches of the tile
     constexpr int NPW = NPX * NPY / kWarps;      // patches per warp
-    static_assert(RB <= kScMaxRB && NKS <= 16 && QW + 2 <= QWI, "a window row spans at most 16 columns");
+    static_assert(RB <= (MODE == kScScreened ? kScMaxRBF32 : kScMaxRB) && NKS <= 16 && QW + 2 <= QWI,
+                  "a window row spans at most 16 columns");
     static_assert((NPX * NPY) % kWarps == 0 && NPW % 2 == 0, "patches must split evenly over the warps");
     static_assert(kScBand * (TX + 2 * (RB + kMaxRW)) * kScDCR * 4 <= kScRefOff &&
                       kScRBand4 * (TX + 2 * (RB + kMaxRW)) * 4 * 4 <= kScRefOff, "refinement window sums");
     // the refinement's band statistics sit in the cost buffer, past its FP32 planes
     static_assert((size_t)kScDCR * sc_psz(QH) * 4 + (size_t)kScRBand4 * (2 * QW + kScDCR - 1) * 8 <=
                       (size_t)QH * QW * kScDC * 2, "refinement statistics");
-    static_assert(kScRefOff + (QH * kScRPW + KB * 12) * 4 <= kScRangeOff, "refinement tables");
+    static_assert(kScRefOff + (QH * kScRPW + KB * sc_krw(RB)) * 4 <= kScRangeOff, "refinement tables");
     static_assert(kScRangeOff + TY * TX * 8 <= kWarps * 2 * 16 * kScDC * 4, "candidate ranges");
     constexpr int RPW = kScRPW, PSZ = sc_psz(QH);
     extern __shared__ __align__(128) uint8_t smem[];
@@ -695,13 +702,13 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
         __syncthreads();
         // ---- refinement of the candidates
         float *sIr = reinterpret_cast<float *>(smem + L.escr + kScRefOff);   // [QH][RPW]
-        float *sKr = sIr + QH * RPW;                                           // [KB][12]
+        float *sKr = sIr + QH * RPW;                                           // [KB][sc_krw(RB)]
         for (int i = tid; i < QH * RPW; i += kThreads) {
             const int yq = i / RPW, xq = i - yq * RPW;
             sIr[i] = xq < QWI ? sI[yq * QWI + xq] : 1e18f;
         }
-        for (int i = tid; i < KB * 12; i += kThreads) {
-            const int dx = i / 12, dy = i - dx * 12;
+        for (int i = tid; i < KB * sc_krw(RB); i += kThreads) {
+            const int dx = i / sc_krw(RB), dy = i - dx * sc_krw(RB);
             sKr[i] = dy < KB ? a.K[dx * KB + dy] : 0.f;
         }
         int2 *rstr = reinterpret_cast<int2 *>(cb32 + (size_t)DCR * PSZ);   // [kScRBand4][QW]
@@ -722,6 +729,8 @@ FusedKernel pick_sc_rb(int rb)
     case 4: return k_fused_sc<4, B2, MODE, T>;
     case 5: return k_fused_sc<5, B2, MODE, T>;
     }
+    if constexpr (MODE == kScScreened)
+        if (rb == 6) return k_fused_sc<6, B2, MODE, T>;   // bil = 13: a window row fills the 16 k-slots
     return nullptr;
 }
 

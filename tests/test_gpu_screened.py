@@ -3,7 +3,8 @@ tensor-core screening of the aggregation with a certified error bound, then k_fu
 arithmetic on the certified candidates.  Its outputs must equal the SIMT FP32 form's bit for bit
 -- disparity, integer WTA, validity and the best2 values -- on every shape: ragged tiles, search
 ranges off the 32-disparity chunk, every window pair the form takes, ties (a flat image, where
-every disparity ties and the whole range is refined), and the 1920 x 1080 D = 128 workload."""
+every disparity ties and the whole range is refined), and the 1920 x 1080 workloads (D = 128,
+k = 11; D = 192, k = 13)."""
 import numpy as np
 import pytest
 import torch
@@ -70,6 +71,9 @@ def pair(W, H, shift_px, seed, noise=2.0):
     (80, 44, 40, 11, 3),     # the largest block
     (64, 72, 17, 5, 5),
     (96, 36, 100, 7, 11),
+    (80, 44, 40, 11, 13),    # bil = 13: a window row fills the 16 k-slots, the largest block
+    (70, 41, 20, 9, 13),
+    (33, 50, 70, 3, 13),
 ])
 def test_screened_equals_simt_bit_for_bit(W, H, D, win, bil):
     ref, tgt, shift = pair(W, H, min(5, D - 1), W * 31 + H)
@@ -141,7 +145,7 @@ def test_screened_rows_with_flat_left_runs(W):
                     run(ref, tgt, shift, D, win, bil, 3.0, 10.0, sg.STEREO_FUSED_TENSOR))
 
 
-@pytest.mark.parametrize("W,H,D,win,bil", [(90, 50, 24, 7, 9), (64, 40, 40, 9, 11)])
+@pytest.mark.parametrize("W,H,D,win,bil", [(90, 50, 24, 7, 9), (64, 40, 40, 9, 11), (70, 45, 36, 9, 13)])
 def test_screened_best2_equals_simt(W, H, D, win, bil):
     ref, tgt, shift = pair(W, H, 4, W + H)
     a = run(ref, tgt, shift, D, win, bil, 3.0, 10.0, sg.STEREO_FUSED_SIMT, best2=True)
@@ -149,9 +153,11 @@ def test_screened_best2_equals_simt(W, H, D, win, bil):
     assert_same(a, b)
 
 
-def test_screened_hd_workload_equals_simt():
-    """The benchmark workload, 1920 x 1080, D = 128, w = 9, k = 11, whole map."""
-    s = synth.make_config_scene("hd")
+@pytest.mark.parametrize("preset", ["hd", "precision"])
+def test_screened_hd_workload_equals_simt(preset):
+    """The benchmark workload, 1920 x 1080, D = 128, w = 9, k = 11, and the precision workload,
+    1920 x 1080, D = 192, w = 9, k = 13: whole maps."""
+    s = synth.make_config_scene(preset)
     p = s.params
     pitch = pitch_of(s.width)
     H, W = s.height, s.width
@@ -173,7 +179,7 @@ def test_screened_hd_workload_equals_simt():
 
 def test_tensor_form_rejected_where_it_does_not_apply():
     with pytest.raises(sg.StereoError) as e:
-        sg.Stereo(64, 48, 16, win=9, bil=13, fused_form=sg.STEREO_FUSED_TENSOR)
+        sg.Stereo(64, 48, 16, win=9, bil=15, fused_form=sg.STEREO_FUSED_TENSOR)
     assert e.value.code == sg.STEREO_ENOTSUP
     with pytest.raises(sg.StereoError) as e:
         sg.Stereo(64, 48, 16, fused_form=7)
