@@ -723,7 +723,7 @@ def run_ours(args):
         v["fused_frac_of_fp32_roofline"] = agg_flops / (v["fused_ms"] * 1e-3) / 1e12 / peak
     # the tensor-core forms' executed mma work: per 4 x 4 patch, chunk of 32 disparities and
     # window row, four m16n8k16 (4096 flop each), including the zero-weight K slots (32 x 36
-    # tiles of 72 patches; bil <= 11)
+    # tiles of 72 patches; bil <= 13)
     peaks = measured_peaks()
     nks = 4 + 2 * (bil // 2)
     mma_flops = ((W + 31) // 32) * ((H + 35) // 36) * 72 * ((D + 31) // 32) * nks * 4 * 4096.0

@@ -79,9 +79,9 @@ typedef struct {
  *                        tensor cores with a certified error bound, the certified candidates
  *                        refined with the SIMT form's FP32 arithmetic; its outputs equal the SIMT
  *                        form's bit for bit (bil <= 13).  FP16 / BF16 storage: the tensor-core
- *                        aggregation of the 16-bit costs -- for bil <= 11 on the screened form's
- *                        32 x 36 tiles with weights rounded from the FP32 ones, for bil = 13 on
- *                        64 x 36 tiles with weights formed in 16-bit arithmetic (sigma1 <= 150).
+ *                        aggregation of the 16-bit costs on the screened form's 32 x 36 tiles,
+ *                        with weights rounded from the FP32 ones (bil <= 13).  (Batches may also
+ *                        take 64 x 36 tiles with weights formed in 16-bit arithmetic, tile_wc 16.)
  *   STEREO_FUSED_AUTO    TENSOR where it applies, else SIMT.
  * stereo_create returns STEREO_ENOTSUP when TENSOR is asked for and does not apply. */
 #define STEREO_FUSED_AUTO 0
@@ -237,9 +237,8 @@ typedef struct {
                                   bil <= 11); 16: 64x36 tiles with the aggregation on the tensor cores
                                   (FP16 / BF16 storage, tile_dc 16, bil <= 13, sigma1 <= 150);
                                   32: 32x36 tiles with the aggregation on the tensor cores, 32
-                                  disparities per chunk (tile_dc 32; FP32 storage: the screened
-                                  form, bil <= 13, see stereo_params.fused_form; FP16 / BF16
-                                  storage: bil <= 11); 0 = autotune */
+                                  disparities per chunk (tile_dc 32, bil <= 13; FP32 storage: the
+                                  screened form, see stereo_params.fused_form); 0 = autotune */
     int32_t tile_dc;           /* disparities per chunk (12 or 4; 16 with tile_wc 16; 32 with
                                   tile_wc 32); 0 = autotune */
 } stereo_batch_params;

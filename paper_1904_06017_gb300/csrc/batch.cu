@@ -377,8 +377,8 @@ int stereo_batch_create(const stereo_batch_params *p, int32_t n, const stereo_pa
         (p->tile_dc && p->tile_dc != 4 && p->tile_dc != 12 && p->tile_dc != 16 && p->tile_dc != 32))
         return set_error(STEREO_EINVAL,
                          "stereo_batch_create: tile_wc must be 0, 1, 2, 4, 8, 16 or 32 and tile_dc 0, 4, 12, 16 or 32");
-    if (p->tile_wc == kScWC && p->bil / 2 > sc_max_rb(p->cost_dtype == STEREO_F32))
-        return set_error(STEREO_ENOTSUP, "stereo_batch_create: tile_wc 32 needs bil <= 13 (FP32) or bil <= 11 (FP16 / BF16)");
+    if (p->tile_wc == kScWC && p->bil / 2 > kScMaxRB)
+        return set_error(STEREO_ENOTSUP, "stereo_batch_create: tile_wc 32 needs bil <= 13");
     if (p->tile_wc == kTcWC && !tc_supported(p->cost_dtype, p->bil, p->sigma1))
         return set_error(STEREO_ENOTSUP, "stereo_batch_create: tile_wc 16 needs FP16 / BF16 storage, bil <= 13 and sigma1 <= 150");
     for (int i = 0; i < n; ++i) {

@@ -36,11 +36,9 @@ constexpr int kTcMaxRB = 6;
 constexpr float kTcMaxSigma1 = 150.f;   // -s^2 stays a normal FP16 number
 // The screened FP32 form (tile code kScWC): 32 x 36 tiles, kWarps warps, tensor-core screening
 // over 32 disparities per chunk and an exact FP32 refinement of the certified candidates
-// (k_fused_sc.cuh); bil <= 13 with FP32 storage (the screened form), bil <= 11 with FP16 / BF16.
+// (k_fused_sc.cuh); bil <= 13 (at 13 a window row fills the 16 k-slots of an mma).
 constexpr int kScWC = 32;
-constexpr int kScMaxRB = 5;
-constexpr int kScMaxRBF32 = 6;
-__host__ __device__ constexpr int sc_max_rb(bool f32) { return f32 ? kScMaxRBF32 : kScMaxRB; }
+constexpr int kScMaxRB = 6;
 __host__ __device__ constexpr int tile_x(int wc)
 {
     return wc == kWsWC || wc == kTcWC ? 64 : wc == kScWC ? 32 : 32 * wc;

@@ -3,6 +3,6 @@
 
 namespace sgb {
 
-FusedKernel pick_fused_sc(int rb) { return rb <= kScMaxRBF32 ? pick_sc_rb<false>(rb) : nullptr; }
+FusedKernel pick_fused_sc(int rb) { return rb <= kScMaxRB ? pick_sc_rb<false>(rb) : nullptr; }
 
 }  // namespace sgb

@@ -355,7 +355,7 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
     constexpr int NKS = 4 + 2 * RB;              // k-steps: the window rows of a patch
     constexpr int NPX = TX / 4, NPY = TY / 4;    // patches of the tile
     constexpr int NPW = NPX * NPY / kWarps;      // patches per warp
-    static_assert(RB <= (MODE == kScScreened ? kScMaxRBF32 : kScMaxRB) && NKS <= 16 && QW + 2 <= QWI,
+    static_assert(RB <= kScMaxRB && NKS <= 16 && QW + 2 <= QWI,
                   "a window row spans at most 16 columns");
     static_assert((NPX * NPY) % kWarps == 0 && NPW % 2 == 0, "patches must split evenly over the warps");
     static_assert(kScBand * (TX + 2 * (RB + kMaxRW)) * kScDCR * 4 <= kScRefOff &&
@@ -728,9 +728,8 @@ FusedKernel pick_sc_rb(int rb)
     case 3: return k_fused_sc<3, B2, MODE, T>;
     case 4: return k_fused_sc<4, B2, MODE, T>;
     case 5: return k_fused_sc<5, B2, MODE, T>;
+    case 6: return k_fused_sc<6, B2, MODE, T>;   // bil = 13: a window row fills the 16 k-slots
     }
-    if constexpr (MODE == kScScreened)
-        if (rb == 6) return k_fused_sc<6, B2, MODE, T>;   // bil = 13: a window row fills the 16 k-slots
     return nullptr;
 }
 

@@ -4,6 +4,6 @@
 
 namespace sgb {
 
-FusedKernel pick_fused_sc_b2(int rb) { return rb <= kScMaxRBF32 ? pick_sc_rb<true>(rb) : nullptr; }
+FusedKernel pick_fused_sc_b2(int rb) { return rb <= kScMaxRB ? pick_sc_rb<true>(rb) : nullptr; }
 
 }  // namespace sgb

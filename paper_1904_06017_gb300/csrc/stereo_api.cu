@@ -217,9 +217,9 @@ int create_context(const stereo_params *p, int force_dc, int force_wc, stereo_ct
     // allows it, else 4
     const int smem_max = max_smem_optin() - kFusedStaticSmem;
     const bool want_tensor = p->fused_form != STEREO_FUSED_SIMT;
-    // the kScWC tiles take FP32 storage up to bil = 13 and FP16 / BF16 up to bil = 11; the
-    // 64 x 36 tensor-core form covers FP16 / BF16 at bil = 13
-    const bool sc = !force_wc && !force_dc && want_tensor && p->bil / 2 <= sc_max_rb(p->cost_dtype == STEREO_F32);
+    // the kScWC tiles take every storage type up to bil = 13 (the 64 x 36 tensor-core form, whose
+    // weights are formed in 16-bit arithmetic, stays a batch tile choice)
+    const bool sc = !force_wc && !force_dc && want_tensor && p->bil / 2 <= kScMaxRB;
     const bool tc = !force_wc && !force_dc && want_tensor && !sc && tc_supported(p->cost_dtype, p->bil, p->sigma1);
     if (p->fused_form == STEREO_FUSED_TENSOR && !force_wc && !tc && !sc) {
         free_ctx(c);

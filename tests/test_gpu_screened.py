@@ -74,6 +74,7 @@ def pair(W, H, shift_px, seed, noise=2.0):
     (80, 44, 40, 11, 13),    # bil = 13: a window row fills the 16 k-slots, the largest block
     (70, 41, 20, 9, 13),
     (33, 50, 70, 3, 13),
+    (300, 40, 256, 11, 13),  # D = 256 with the largest blocks: the layout at its largest
 ])
 def test_screened_equals_simt_bit_for_bit(W, H, D, win, bil):
     ref, tgt, shift = pair(W, H, min(5, D - 1), W * 31 + H)

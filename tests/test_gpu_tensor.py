@@ -1,7 +1,7 @@
 """Tensor-core aggregation of the FP16 / BF16 storage forms (mma.sync over 4 x 4 pixel
-patches, FP32 accumulators), the default kernel of those forms for bil <= 13: for bil <= 11 on
-32 x 36 tiles with weights rounded from the FP32 ones (k_fused_sc, plain mode), for bil = 13 on
-64 x 36 tiles with weights formed in 16-bit arithmetic (k_fused_tc).
+patches, FP32 accumulators), the default kernel of those forms for bil <= 13: 32 x 36 tiles
+with weights rounded from the FP32 ones (k_fused_sc, plain mode); batches may also take 64 x 36
+tiles with weights formed in 16-bit arithmetic (k_fused_tc, tile_wc 16).
 
 Its costs and bilateral weights are rounded to the 16-bit type, so it is held to bounds
 derived from that rounding rather than the FP32 path's 1e-3 gap.  FP16: a cost moves by at
@@ -78,10 +78,10 @@ def test_tensor_form_matches_oracle(W, H, D, win, bil, dtype):
     assert err.mean() < (0.01 if dtype == sg.STEREO_F16 else 0.05)
 
 
-@pytest.mark.parametrize("W,H,D,win,bil", [(300, 40, 256, 11, 11), (300, 40, 256, 9, 13)])
+@pytest.mark.parametrize("W,H,D,win,bil", [(300, 40, 256, 11, 11), (300, 40, 256, 9, 13), (300, 40, 256, 11, 13)])
 def test_tensor_form_maximum_disparity(W, H, D, win, bil):
-    """D = 256: the widest target strip; with w = k = 11 the form's shared memory is at its
-    largest (about 228 KB)."""
+    """D = 256: the widest target strip; with w = 11, k = 13 the form's shared memory is at its
+    largest (about 218 KB)."""
     s = synth.make_scene(W, H, D, 4242 + bil, roll=0.0, coeffs=(100.0, 0.0, 0.0), n_potholes=0,
                          warp=False, win=win, bil=bil)
     tw = s.tgt
@@ -184,7 +184,7 @@ def _batch(ss, dtype, wc, dc):
 @pytest.mark.parametrize("wc,dc", [(32, 32), (16, 16)])
 def test_tensor_form_batch_equals_single_and_tracks_simt_form(wc, dc):
     """tile_wc 32: the 32 x 36 form with weights rounded from FP32 (the default single-pair
-    context for bil <= 11); tile_wc 16: the 64 x 36 form with 16-bit weights."""
+    context for bil <= 13); tile_wc 16: the 64 x 36 form with 16-bit weights."""
     ss = [synth.make_scene(W, H, D, 700 + i, roll=math.radians(2.0 * (i - 2)), coeffs=(6.0, 0.1, 0.0),
                            n_potholes=1, warp=True, win=7, bil=9) for i, (W, H, D) in enumerate(SIZES)]
     tc, qs, cfg = _batch(ss, sg.STEREO_F16, wc, dc)
