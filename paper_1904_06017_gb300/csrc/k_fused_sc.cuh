@@ -56,7 +56,6 @@ constexpr float kScAbs = 64.f;  // in the scaled units of E16 (2^20 x E32)
 constexpr float kScRho = (1.0f + kScEps) / (1.0f - kScEps) + 1e-6f;
 
 constexpr int kScRefOff = 16384;     // bytes into escr: past the refinement's window sums (<= 10 KB)
-constexpr int kScRangeOff = 32768;   // bytes into escr: the per-pixel candidate ranges (int2 [36][32])
 
 __device__ __forceinline__ float sc_thr(float m) { return fmaf(m + kScAbs, kScRho, kScAbs); }
 
@@ -68,16 +67,17 @@ __device__ __forceinline__ float sc_thr(float m) { return fmaf(m + kScAbs, kScRh
 //   escr   the cost phase's vertical window sums ([band][CW][32] i32); the same bytes hold, in
 //          the 16-bit form, two per-warp E blocks of the aggregation ([warp][2][16 pixels][32]
 //          f32, 16-byte units swizzled by the pixel); after the screening the refinement's
-//          vertical sums, from kScRefOff on the intensities again as [QH][kScRPW] f32 and the
-//          spatial exponents as [2 RB + 1][12] f32, and from kScRangeOff on the candidate range
-//          of every pixel of the tile ([TY][TX] int2)
+//          vertical sums, and from kScRefOff on the intensities again as [QH][kScRPW] f32 and
+//          the spatial exponents as [2 RB + 1][sc_krw(RB)] f32
 //   sstr, sstt  window statistics of one band
 //   sI     [QH][sc_qwi(RB)] f32  the reference intensities times sqrt(log2 e) / sigma1 of the cost
 //          positions (1e18 outside the image, as in k_fused)
 //   skxy   the row terms of the spatial exponent, (nKy(j), nKy(j - 2)) for j = -1 .. 3 + 2 RB
 //          (float2)
+//   sst    the screening state of every pixel of the tile ([TY][TX] float2: the running minimum
+//          of E16, and the candidate range dlo | dhi << 16 as the bits of the second float)
 struct ScLayout {
-    size_t sref, stgt, cbuf, escr, sstr, sstt, sI, skxy, total;
+    size_t sref, stgt, cbuf, escr, sstr, sstt, sI, skxy, sst, total;
 };
 
 __host__ __device__ inline ScLayout sc_layout(int rb, int m, int ref_box_w, int tgt_box_w, int box_h)
@@ -95,7 +95,8 @@ __host__ __device__ inline ScLayout sc_layout(int rb, int m, int ref_box_w, int 
     L.sstt = align_up(L.sstr + (size_t)kScBand * QW * 8, 16);
     L.sI = align_up(L.sstt + (size_t)kScBand * (QW + kScDC - 1) * 8, 16);
     L.skxy = align_up(L.sI + (size_t)QH * sc_qwi(rb) * 4, 16);
-    L.total = align_up(L.skxy + (size_t)(NKS + 2) * 8, 128);
+    L.sst = align_up(L.skxy + (size_t)(NKS + 2) * 8, 16);
+    L.total = align_up(L.sst + (size_t)TY * TX * 8, 128);
     return L;
 }
 
@@ -363,8 +364,8 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
     // the refinement's band statistics sit in the cost buffer, past its FP32 planes
     static_assert((size_t)kScDCR * sc_psz(QH) * 4 + (size_t)kScRBand4 * (2 * QW + kScDCR - 1) * 8 <=
                       (size_t)QH * QW * kScDC * 2, "refinement statistics");
-    static_assert(kScRefOff + (QH * kScRPW + KB * sc_krw(RB)) * 4 <= kScRangeOff, "refinement tables");
-    static_assert(kScRangeOff + TY * TX * 8 <= kWarps * 2 * 16 * kScDC * 4, "candidate ranges");
+    static_assert(kScRefOff + (QH * kScRPW + KB * sc_krw(RB)) * 4 <= kScBand * (TX + 2 * RB) * kScDC * 4,
+                  "refinement tables");
     constexpr int RPW = kScRPW, PSZ = sc_psz(QH);
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(16) FusedArgs s_args;
@@ -419,6 +420,10 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
         float2 *sky = reinterpret_cast<float2 *>(smem + L.skxy);
         auto nky = [&](int j) { return (j >= 0 && j <= 2 * RB) ? -a.K[RB * KB + j] : 1e30f; };
         for (int j = tid; j < NKS + 2; j += kThreads) sky[j] = make_float2(nky(j - 1), nky(j - 3));
+        if constexpr (!PLAIN) {
+            float2 *sst0 = reinterpret_cast<float2 *>(smem + L.sst);
+            for (int j = tid; j < TY * TX; j += kThreads) sst0[j] = make_float2(__int_as_float(0x7f800000), 0.f);
+        }
         // this lane's column terms: columns 2 t4 + {0, 1} and 2 t4 + {8, 9} of a window row
         auto nkx = [&](int col) {
             const int i = col - mx;
@@ -434,20 +439,9 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
         constexpr int NSEGR = NPY / 3;                // segments per patch column
         constexpr int NR3 = 8 + NKS;                  // window rows of a segment
         static_assert(NPY % 3 == 0 && NPX * NSEGR == 2 * kWarps, "two segments of three patches per warp");
-        // screening state of this lane's pixels g (h = 0) and g + 8 (h = 1) of patch i of segment
-        // si (the four lanes of a quad hold the same state): the running minimum of E16 and the
-        // candidate range [dlo, dhi] as dlo | dhi << 16
-        float emin[2][3][2];
-        int rng[2][3][2];
-#pragma unroll
-        for (int si = 0; si < 2; ++si)
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    emin[si][i][h] = __int_as_float(0x7f800000);
-                    rng[si][i][h] = 0;
-                }
+        // the screening state of each pixel lives in sst between chunks (set before the barrier
+        // above); a quad reads its two pixels' entries and its first lane writes them back
+        float2 *sst = reinterpret_cast<float2 *>(smem + L.sst);
         const int hb = lane >> 4, m = lane & 15;
         // the plain form's running WTA (k_fused's rules on the 16-bit sums): per segment, state 0
         // is pixel m of patch hb, state 1 (lanes 0-15) pixel m of patch 2
@@ -613,9 +607,10 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
                             for (int j = 1; j < 8; ++j) cm = fminf(cm, v[j]);
                             cm = fminf(cm, __shfl_xor_sync(0xffffffffu, cm, 1));
                             cm = fminf(cm, __shfl_xor_sync(0xffffffffu, cm, 2));
-                            // the pixel's state, selected with static indices (no local memory)
-                            float em = emin[0][i][h];
-                            if (si == 1) em = emin[1][i][h];
+                            // the pixel's state
+                            const int pidx = ((sg / NPX) * 12 + 4 * i + my0 + 2 * h) * TX + px0 + mx;
+                            const float2 sv = sst[pidx];
+                            const float em = sv.x;
                             const float nm = fminf(em, cm);
                             const float tn = sc_thr(nm);
                             uint32_t mk = 0;
@@ -626,15 +621,10 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
                             mk |= __shfl_xor_sync(0xffffffffu, mk, 2);
                             const bool reset = mk && tn < em;   // the earlier range cannot hold d*
                             const int lo = d0 + __ffs(mk) - 1, hi = d0 + 31 - __clz(mk);
-#pragma unroll
-                            for (int k = 0; k < 2; ++k)
-                                if (k == si) {
-                                    int r = rng[k][i][h];
-                                    if (reset) r = (r & ~0xffff) | lo;
-                                    if (mk) r = (r & 0xffff) | (hi << 16);
-                                    rng[k][i][h] = r;
-                                    emin[k][i][h] = nm;
-                                }
+                            int r = __float_as_int(sv.y);
+                            if (reset) r = (r & ~0xffff) | lo;
+                            if (mk) r = (r & 0xffff) | (hi << 16);
+                            if (t4 == 0) sst[pidx] = make_float2(nm, __int_as_float(r));
                         }
                     }
                 }
@@ -685,21 +675,6 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
             continue;   // the next tile
         }
 
-        // the candidate ranges, per pixel of the tile, for the refinement's own pixel layout
-        int2 *srange = reinterpret_cast<int2 *>(smem + L.escr + kScRangeOff);   // [TY][TX]
-        if (!B2 && t4 == 0) {
-#pragma unroll
-            for (int si = 0; si < 2; ++si)
-#pragma unroll
-                for (int i = 0; i < 3; ++i)
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int sg = warp + kWarps * si;
-                        const int px = (sg % NPX) * 4 + mx, py = (sg / NPX) * 12 + 4 * i + my0 + 2 * h;
-                        srange[py * TX + px] = make_int2(rng[si][i][h] & 0xffff, rng[si][i][h] >> 16);
-                    }
-        }
-        __syncthreads();
         // ---- refinement of the candidates
         float *sIr = reinterpret_cast<float *>(smem + L.escr + kScRefOff);   // [QH][RPW]
         float *sKr = sIr + QH * RPW;                                           // [KB][sc_krw(RB)]
@@ -714,7 +689,10 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
         int2 *rstr = reinterpret_cast<int2 *>(cb32 + (size_t)DCR * PSZ);   // [kScRBand4][QW]
         int2 *rstt = rstr + kScRBand4 * QW;                                  // [kScRBand4][QW + DCR - 1]
         sc_refine<RB, B2, kThreads, DCR, kScRSeg>(a, sref, stgt, cb32, vband, rstr, rstt, sIr, sKr, x0, y0, tid, &s_rlo, &s_rhi,
-                                         [&](int py, int px) { return srange[py * TX + px]; });
+                                         [&](int py, int px) {
+                                             const int r = __float_as_int(sst[py * TX + px].y);
+                                             return make_int2(r & 0xffff, r >> 16);
+                                         });
     }  // tile loop
 }
 
