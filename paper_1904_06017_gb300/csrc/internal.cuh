@@ -82,6 +82,7 @@ struct stereo_ctx {
     stereo_params p;
     sgb::Geometry g;
     int device;
+    int nsm;                       // SMs of the device (grid of the persistent screened kernel)
     uint8_t *ref_pad, *tgt_pad;    // replicate-padded copies (pad_pitch x pad_h)
     int2 *ref_stats, *tgt_stats;   // per padded position: {sum, bits of 1/sqrt(n*sumsq - sum^2)}
     int4 *row_tab;                 // per image row: {s_i(v), max and min of s_i over rows v-m..v+m,

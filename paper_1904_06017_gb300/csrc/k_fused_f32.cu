@@ -2,6 +2,8 @@
 // side shared by all storage types (shared-memory sizing, kernel choice, launch).
 #include <string.h>
 
+#include <algorithm>
+
 #include "k_fused.cuh"
 #include "k_fused_sc.cuh"
 
@@ -119,7 +121,10 @@ int launch_fused(stereo_ctx *ctx, const float *shift, float *disp, int32_t *wta,
     PairDesc d;
     fill_pair_desc(ctx, disp, wta, valid, d, best2);
     const int ntiles = g.ntx * g.nty;
-    k<<<ntiles, fused_threads(g.wc), g.smem_bytes, s>>>(d, nullptr, nullptr, ntiles, nullptr);
+    // the screened form is persistent (one CTA per SM, tiles in turn, the next tile's images
+    // staged while the current one finishes); the others take one tile per CTA
+    const int grid = g.wc == kScWC ? std::min(ntiles, ctx->nsm) : ntiles;
+    k<<<grid, fused_threads(g.wc), g.smem_bytes, s>>>(d, nullptr, nullptr, ntiles, nullptr);
     return cuda_error(cudaGetLastError(), "k_fused launch");
 }
 

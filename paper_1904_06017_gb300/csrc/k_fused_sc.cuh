@@ -144,10 +144,13 @@ template <> __device__ __forceinline__ uint32_t pack_rn<__nv_bfloat16>(float lo,
 // of the cost positions) and sKr ([KB][sc_krw(RB)], the spatial exponents K[dx][dy]) are written; *s_rlo
 // = INT_MAX and *s_rhi = -1; and range_of's data are visible to every thread.  The function
 // synchronises before it reads sIr and returns after the epilogue, without a final barrier.
-template <int RB, bool B2, int NT, int DCR, int RKSEG, typename RangeOf>
+// images_free() is called by every thread right after the barrier that ends the last chunk's
+// cost phase: sref and stgt are not read after it.
+template <int RB, bool B2, int NT, int DCR, int RKSEG, typename RangeOf, typename OnFree>
 __device__ __forceinline__ void sc_refine(const FusedArgs &a, const uint8_t *sref, const uint8_t *stgt, float *cb32,
                                           int *vband, int2 *sstr, int2 *sstt, const float *sIr, const float *sKr,
-                                          int x0, int y0, int tid, int *s_rlo, int *s_rhi, RangeOf range_of)
+                                          int x0, int y0, int tid, int *s_rlo, int *s_rhi, RangeOf range_of,
+                                          OnFree images_free)
 {
     constexpr int TX = tile_x(kScWC), TY = tile_y(kScWC);
     constexpr int KB = 2 * RB + 1, QH = TY + 2 * RB;
@@ -224,6 +227,7 @@ __device__ __forceinline__ void sc_refine(const FusedArgs &a, const uint8_t *sre
             default: cost_chunk<RB, D8, 5, float, TX, TY, NT, 0, kScBand, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
             }
         }
+        if (cb + dcr > uhi_t) images_free();   // the last chunk's cost phase has read the images
         // One pass per thread and chunk: disparities dw .. dw + 2 NPP - 1 from the pair below
         // the thread's lowest candidate in the chunk, NPP pairs (the warp's largest need; 2 or
         // 4).  Pairs past the chunk read its last pair (their sums are discarded), and so do the
@@ -336,6 +340,79 @@ __device__ __forceinline__ void sc_refine(const FusedArgs &a, const uint8_t *sre
     }
 }
 
+// ---- persistent tiles: the next work item is claimed while the current tile is still being
+// worked on, and its images are staged into sref / stgt as soon as the tile's last cost phase
+// has read them, so that the copies land during the refinement's evaluation and the epilogue.
+
+// The pair and tile of work item `item` (a batch's work list, or one pair's tiles in order).
+__device__ __forceinline__ const PairDesc *sc_decode(const PairDesc &single, const PairDesc *pairs,
+                                                     const int2 *items, int item, int &tx, int &ty)
+{
+    if (pairs) {
+        const int2 it = items[item];
+        tx = it.y & 0xffff;
+        ty = it.y >> 16;
+        return pairs + it.x;
+    }
+    tx = item % single.ntx;
+    ty = item / single.ntx;
+    return &single;
+}
+
+// Waits for the images of the tile at (x0, y0), issuing their copies first unless an earlier
+// call of sc_claim_ahead did (issued).  The wait is bounded as in stage_images, with the same
+// fail-safe: false, with the status word set, when the copies did not land.
+__device__ __forceinline__ bool sc_stage(const PairDesc *pd, const FusedArgs &a, uint8_t *sref, uint8_t *stgt,
+                                         uint64_t *bar, int *flag, int x0, int y0, int iter, int tid, bool issued)
+{
+    if (tid == 0) {
+        const bool stall = a.stall_test != 0;
+        if (!issued) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(bar, (uint32_t)(a.box_h * (a.ref_box_w + a.tgt_box_w)));
+            if (!stall) {
+                tma_load_3d(sref, &pd->tmap_ref, 0, (x0 + a.ref_box_x) / 16, y0, bar);
+                tma_load_3d(stgt, &pd->tmap_tgt, 0, x0 / 16, y0, bar);
+            }
+        }
+        const long long limit = stall ? (1ll << 21) : (1ll << 31);
+        const long long t0 = clock64();
+        bool ok = false;
+        while (!(ok = mbar_try_wait(bar, (uint32_t)(iter & 1))) && clock64() - t0 < limit) {
+        }
+        *flag = ok ? 1 : 0;
+        if (!ok) atomicOr(a.status, 1);
+    }
+    __syncthreads();
+    return *flag != 0;
+}
+
+// Thread 0, once per tile, after a barrier that follows the tile's last read of sref / stgt:
+// claims the next work item (*next) and, when its boxes fit the current ones (always within one
+// pair), issues its image copies (*staged = 1).  Nothing is issued under the stall test hook.
+__device__ __forceinline__ void sc_claim_ahead(const PairDesc &single, const PairDesc *pairs, const int2 *items,
+                                               int nitems, int *counter, int item, const FusedArgs &a,
+                                               uint8_t *sref, uint8_t *stgt, uint64_t *bar, int *next,
+                                               int *claimed, int *staged, int tx_w, int ty_h)
+{
+    if (*claimed) return;
+    *claimed = 1;
+    *staged = 0;
+    const int nx = pairs ? atomicAdd(counter, 1) : item + (int)gridDim.x;
+    *next = nx;
+    if (nx >= nitems || a.stall_test) return;
+    int txn = 0, tyn = 0;
+    const PairDesc *pn = sc_decode(single, pairs, items, nx, txn, tyn);
+    const int bh = pn->a.box_h, rbw = pn->a.ref_box_w, tbw = pn->a.tgt_box_w;
+    if (bh != a.box_h || rbw != a.ref_box_w || tbw > a.tgt_box_w || pn->a.stall_test) return;
+    const int x0n = txn * tx_w, y0n = tyn * ty_h;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, (uint32_t)(bh * (rbw + tbw)));
+    tma_load_3d(sref, &pn->tmap_ref, 0, (x0n + pn->a.ref_box_x) / 16, y0n, bar);
+    tma_load_3d(stgt, &pn->tmap_tgt, 0, x0n / 16, y0n, bar);
+    *staged = 1;
+}
+
 // MODE: kScScreened (the FP32 screened form), or kScPlain (the FP16 / BF16 storage form: the
 // same tensor-core aggregation of the 16-bit costs with a running WTA on its sums, no
 // refinement).  B2: the best2 output.  T: the 16-bit type of the costs and weights.
@@ -373,17 +450,36 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ int s_flag;
     __shared__ int s_rlo, s_rhi;
+    __shared__ int s_next, s_claimed, s_staged;   // the work item claimed ahead, its copies issued
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t4 = lane & 3;      // fragment row group and column pair
     const int mx = g & 3, my0 = g >> 2;          // this lane's fragment pixels m0 = g, m1 = g + 8
     const FusedArgs &a = s_args;
-    if (tid == 0) mbar_init(&s_bar, 1);
+    if (tid == 0) {
+        mbar_init(&s_bar, 1);
+        s_staged = 0;
+    }
 
     for (int iter = 0;; ++iter) {
+        // the work item: the first one claimed here, every later one claimed ahead (the barrier
+        // also orders the previous tile's last reads of s_args before it is overwritten)
+        if (tid == 0) {
+            s_item = iter == 0 ? (pairs ? atomicAdd(counter, 1) : (int)blockIdx.x) : s_next;
+            s_claimed = 0;
+        }
+        __syncthreads();
+        const int item = s_item;
+        if (item >= nitems) return;
+        const bool issued = iter > 0 && s_staged;
         int tx = 0, ty = 0;
-        const PairDesc *pd = claim_tile<kThreads>(single, pairs, items, nitems, counter, iter, s_args, s_item, tid, tx, ty);
-        if (!pd) return;
+        const PairDesc *pd = sc_decode(single, pairs, items, item, tx, ty);
+        {
+            const int *src = reinterpret_cast<const int *>(&pd->a);
+            int *dst = reinterpret_cast<int *>(&s_args);
+            for (int i = tid; i < (int)(sizeof(FusedArgs) / 4); i += kThreads) dst[i] = src[i];
+        }
+        __syncthreads();
         const int RP = a.ref_box_w;
         const ScLayout L = sc_layout(RB, a.m, RP, a.tgt_box_w, a.box_h);
         uint8_t *sref = smem + L.sref;
@@ -401,7 +497,13 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
             s_rhi = -1;
         }
 
-        if (!stage_images(pd, a, sref, stgt, &s_bar, &s_flag, x0, y0, iter, tid)) return;
+        if (!sc_stage(pd, a, sref, stgt, &s_bar, &s_flag, x0, y0, iter, tid, issued)) return;
+        // called after a barrier that follows the tile's last read of sref / stgt
+        auto images_free = [&]() {
+            if (tid == 0)
+                sc_claim_ahead(single, pairs, items, nitems, counter, item, a, sref, stgt, &s_bar, &s_next,
+                               &s_claimed, &s_staged, TX, TY);
+        };
 
         const int rw = a.rw;
         // scaled reference intensities of the cost positions, exactly as k_fused stages them;
@@ -467,6 +569,8 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
             case 4: cost_chunk<RB, DC, 4, T, TX, TY, kThreads, 0, kScBand, true, kScCSh, 0, 0, kScSeg>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
             default: cost_chunk<RB, DC, 5, T, TX, TY, kThreads, 0, kScBand, true, kScCSh, 0, 0, kScSeg>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
             }
+            if constexpr (PLAIN)
+                if (d0 + DC >= a.D) images_free();   // the aggregation and epilogue read no image
             const int dn = min(DC, a.D - d0);
 #pragma unroll 1
             for (int si = 0; si < 2; ++si) {
@@ -672,7 +776,9 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
                         a.best2[2 * o + 1] = st.sec * sc / wsum;
                     }
                 }
-            continue;   // the next tile
+            __syncthreads();
+            images_free();   // (claimed already, unless the chunk loop did not run)
+            continue;        // the next tile
         }
 
         // ---- refinement of the candidates
@@ -692,7 +798,10 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
                                          [&](int py, int px) {
                                              const int r = __float_as_int(sst[py * TX + px].y);
                                              return make_int2(r & 0xffff, r >> 16);
-                                         });
+                                         },
+                                         images_free);
+        __syncthreads();
+        images_free();   // (claimed already, unless the tile had no candidates to refine)
     }  // tile loop
 }
 

@@ -207,7 +207,8 @@ int create_context(const stereo_params *p, int force_dc, int force_wc, stereo_ct
     if (!c) return set_error(STEREO_ENOMEM, "stereo_create: host allocation failed");
     c->p = *p;
     int rc;
-    if (cudaGetDevice(&c->device) != cudaSuccess) {
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || c->nsm < 1) {
         free_ctx(c);
         return cuda_error(cudaErrorNoDevice, "stereo_create: no CUDA device");
     }
