@@ -711,10 +711,13 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
                             for (int j = 1; j < 8; ++j) cm = fminf(cm, v[j]);
                             cm = fminf(cm, __shfl_xor_sync(0xffffffffu, cm, 1));
                             cm = fminf(cm, __shfl_xor_sync(0xffffffffu, cm, 2));
-                            // the pixel's state
+                            // the pixel's state.  A chunk whose minimum lies above thr(running
+                            // minimum) changes neither (every E16 of it fails the test, and the
+                            // minimum stays): a warp with no such pixel skips the update
                             const int pidx = ((sg / NPX) * 12 + 4 * i + my0 + 2 * h) * TX + px0 + mx;
                             const float2 sv = sst[pidx];
                             const float em = sv.x;
+                            if (!__any_sync(0xffffffffu, cm <= sc_thr(em))) continue;
                             const float nm = fminf(em, cm);
                             const float tn = sc_thr(nm);
                             uint32_t mk = 0;
@@ -733,8 +736,14 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
                     }
                 }
             }
-            __syncthreads();
+            // The 16-bit form's E blocks share escr with the next cost phase's window sums.  The
+            // screened form's aggregation reads nothing the next cost phase writes before its
+            // first barrier (window sums, band statistics), so its fast warps go on to that
+            // phase; the barrier there orders every read of this chunk's costs before the new
+            // ones are stored.
+            if constexpr (PLAIN) __syncthreads();
         }
+        if constexpr (!PLAIN) __syncthreads();   // every pixel's screening state is final
 
         if constexpr (PLAIN) {
             // ---- epilogue of the plain form: eq. (subpixel), add back s_i(v), validity
@@ -782,12 +791,16 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
         }
 
         // ---- refinement of the candidates
-        float *sIr = reinterpret_cast<float *>(smem + L.escr + kScRefOff);   // [QH][RPW]
-        float *sKr = sIr + QH * RPW;                                           // [KB][sc_krw(RB)]
-        for (int i = tid; i < QH * RPW; i += kThreads) {
-            const int yq = i / RPW, xq = i - yq * RPW;
-            sIr[i] = xq < QWI ? sI[yq * QWI + xq] : 1e18f;
+        // the intensities on the refinement's row pitch: sI itself where the pitches agree
+        float *sIc = reinterpret_cast<float *>(smem + L.escr + kScRefOff);   // [QH][RPW]
+        float *sKr = sIc + QH * RPW;                                           // [KB][sc_krw(RB)]
+        if constexpr (QWI != RPW) {
+            for (int i = tid; i < QH * RPW; i += kThreads) {
+                const int yq = i / RPW, xq = i - yq * RPW;
+                sIc[i] = xq < QWI ? sI[yq * QWI + xq] : 1e18f;
+            }
         }
+        const float *sIr = QWI == RPW ? sI : sIc;
         for (int i = tid; i < KB * sc_krw(RB); i += kThreads) {
             const int dx = i / sc_krw(RB), dy = i - dx * sc_krw(RB);
             sKr[i] = dy < KB ? a.K[dx * KB + dy] : 0.f;
