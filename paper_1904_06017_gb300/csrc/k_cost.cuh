@@ -147,7 +147,7 @@ __device__ __forceinline__ void cost_chunk(const FusedArgs &a, const uint8_t *sr
         // vertical pass, in sub-bands of at most kSub rows: the product rows entering those
         // rows' windows, all loads first, then the running sums (the leaving row read back
         // from the ring) and their stores
-        constexpr int kSub = kBand < 6 ? kBand : 6;
+        constexpr int kSub = kBand <= 6 ? kBand : kBand % 6 == 0 ? 6 : kBand % 8 == 0 ? 8 : kBand % 4 == 0 ? 4 : 1;
         static_assert(kBand % kSub == 0, "a band is a whole number of sub-bands");
         static_for<kBand / kSub>([&](auto sub) {
             constexpr int R0 = decltype(sub)::value * kSub;

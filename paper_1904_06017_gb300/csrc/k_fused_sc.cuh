@@ -34,7 +34,8 @@ namespace sgb {
 
 constexpr int kScDC = 32;       // disparities per screening chunk
 constexpr int kScDCR = 8;       // disparities per FP32 refinement chunk
-constexpr int kScRBand4 = 12;   // cost rows per band of a 4-disparity refinement chunk (8: kScBand)
+constexpr int kScRBand4 = 12;   // cost rows per band of a 4-disparity refinement chunk
+constexpr int kScRBand8 = 8;    // cost rows per band of an 8-disparity refinement chunk
 constexpr int kScRSeg = 3;      // cost columns per horizontal work item of the refinement chunks
 constexpr int kScBand = 6;      // cost rows per band of the screening chunk's cost phase
 constexpr int kScSeg = 6;       // cost columns per horizontal work item (6 rows x 7 segments x 8 quads = 336 items)
@@ -220,11 +221,11 @@ __device__ __forceinline__ void sc_refine(const FusedArgs &a, const uint8_t *sre
         } else {
             constexpr int D8 = DCR == 4 ? 4 : 8;
             switch (rw) {
-            case 1: cost_chunk<RB, D8, 1, float, TX, TY, NT, 0, kScBand, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
-            case 2: cost_chunk<RB, D8, 2, float, TX, TY, NT, 0, kScBand, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
-            case 3: cost_chunk<RB, D8, 3, float, TX, TY, NT, 0, kScBand, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
-            case 4: cost_chunk<RB, D8, 4, float, TX, TY, NT, 0, kScBand, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
-            default: cost_chunk<RB, D8, 5, float, TX, TY, NT, 0, kScBand, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+            case 1: cost_chunk<RB, D8, 1, float, TX, TY, NT, 0, kScRBand8, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+            case 2: cost_chunk<RB, D8, 2, float, TX, TY, NT, 0, kScRBand8, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+            case 3: cost_chunk<RB, D8, 3, float, TX, TY, NT, 0, kScRBand8, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+            case 4: cost_chunk<RB, D8, 4, float, TX, TY, NT, 0, kScRBand8, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
+            default: cost_chunk<RB, D8, 5, float, TX, TY, NT, 0, kScRBand8, false, 0, RPW, PSZ, RKSEG, true>(a, sref, stgt, cb32, vband, sstr, sstt, x0, y0, cb, tid); break;
             }
         }
         if (cb + dcr > uhi_t) images_free();   // the last chunk's cost phase has read the images
@@ -436,9 +437,10 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
     static_assert(RB <= kScMaxRB && NKS <= 16 && QW + 2 <= QWI,
                   "a window row spans at most 16 columns");
     static_assert((NPX * NPY) % kWarps == 0 && NPW % 2 == 0, "patches must split evenly over the warps");
-    static_assert(kScBand * (TX + 2 * (RB + kMaxRW)) * kScDCR * 4 <= kScRefOff &&
+    static_assert(kScRBand8 * (TX + 2 * (RB + kMaxRW)) * kScDCR * 4 <= kScRefOff &&
                       kScRBand4 * (TX + 2 * (RB + kMaxRW)) * 4 * 4 <= kScRefOff, "refinement window sums");
     // the refinement's band statistics sit in the cost buffer, past its FP32 planes
+    static_assert(kScRBand8 <= kScRBand4, "the refinement statistics are sized for the taller band");
     static_assert((size_t)kScDCR * sc_psz(QH) * 4 + (size_t)kScRBand4 * (2 * QW + kScDCR - 1) * 8 <=
                       (size_t)QH * QW * kScDC * 2, "refinement statistics");
     static_assert(kScRefOff + (QH * kScRPW + KB * sc_krw(RB)) * 4 <= kScBand * (TX + 2 * RB) * kScDC * 4,
