@@ -395,7 +395,7 @@ def bench_diff(args, dev, stream, flush):
     """The differentiation workload: 8 pairs of 960 x 540, D = 64, w = 9, k = 11, T = 0.1.
     One step = soft-argmin forward, eq. (E2) forward, and the backward of both (gradients
     in both images and theta), through torch.autograd; plus 50 steps of roll refinement.
-    Its workspace (about 4.3 GB) exceeds L2."""
+    Its workspace (about 3.4 GB) exceeds L2."""
     import numpy as np
     import torch
     from paper_1904_06017_gb300 import diff as sgd

@@ -18,8 +18,10 @@
 //   k_dcost_bwd adjoint of eq. (c): with A = -gc/(n s_a s_b), B = gc ncc/(n s_a^2),
 //               C = gc ncc/(n s_b^2) per window pair, every extended reference position X
 //               collects  sum_d sum_q A (t - mu_b) + B (r - mu_a)            -> gref_ext(X)
-//               and for the target position X - d:  sum_q A (r - mu_a) + C (t - mu_b) -> Gamma(X,d)
-//   k_dtgt_diag gtw_ext(Xt) = sum_d Gamma(Xt + d, d)
+//               and for the target position X - d:  sum_q A (r - mu_a) + C (t - mu_b) -> Gamma(X,d),
+//               summed over d per X - d inside each tile (partial diagonal sums; Gamma itself
+//               is never stored)
+//   k_dtgt_diag gtw_ext(Xt) = sum_d Gamma(Xt + d, d): the tiles' partial sums added
 //   k_dfold     fold the clamp-to-edge positions back onto the image and undo the warp
 #include <cuda_runtime.h>
 #include <math.h>
@@ -48,6 +50,11 @@ constexpr int kAggDC = 8;            // disparities per chunk in k_dagg
 constexpr int kCostDC = 16;          // disparities per block in k_dcost
 constexpr float kFar = 1e18f;        // scaled intensity of an out-of-image neighbour: weight 0
 constexpr float kLog2e = 1.4426950408889634f;
+
+// The cost adjoint's tiles are 32 extended columns wide; each sums Gamma(X, d) over d into
+// 32 + D - 1 entries per row, one per target column X - d its columns reach.
+__host__ __device__ constexpr int cb_tiles_x(int Wr) { return (Wr + 31) / 32; }
+__host__ __device__ constexpr int cb_diag_w(int D) { return 32 + D - 1; }
 
 __device__ __forceinline__ int clampi(int x, int lo, int hi) { return min(max(x, lo), hi); }
 
@@ -83,7 +90,7 @@ struct Dims {
 
 struct Ws {
     float *tw, *mur, *sdr, *mut, *sdt, *cost, *lse, *lbar;      // forward
-    float *h, *gc, *beta, *t1, *gw, *gamma, *grefx, *gtwx;      // backward
+    float *h, *gc, *beta, *t1, *gw, *gpart, *grefx, *gtwx;      // backward
 };
 
 size_t layout(const Dims &d, char *base, Ws *w)
@@ -109,7 +116,7 @@ size_t layout(const Dims &d, char *base, Ws *w)
     take(&o->beta, B * img);
     take(&o->t1, B * img);
     take(&o->gw, B * img);
-    take(&o->gamma, B * (size_t)d.D * d.Hr * d.Wr);
+    take(&o->gpart, B * (size_t)d.Hr * cb_tiles_x(d.Wr) * cb_diag_w(d.D));
     take(&o->grefx, B * (size_t)d.Hr * d.Wr);
     take(&o->gtwx, B * (size_t)d.Hr * d.Wt);
     return off;
@@ -598,7 +605,8 @@ __global__ void __launch_bounds__(agg_threads(MODE), MODE == AGG_FWD ? 3 : MODE 
 // ------------------------------------------------------------------ cost adjoint
 struct CbArgs {
     const float *ref, *tw, *mur, *sdr, *mut, *sdt, *cost, *gc;
-    float *gamma, *grefx;
+    float *gpart;          // [B][Hr][tile column][32 + D - 1] partial diagonal sums of Gamma (or null)
+    float *grefx;
     int W, H, D, Wr, Hr, We;
     float inv_n;
 };
@@ -608,7 +616,10 @@ struct CbArgs {
 // in the tile's halo are staged and box-summed with running sums (along rows, then along
 // columns); the d-independent terms of the reference gradient are summed over d per q and
 // box-summed once at the end.  Row strides are padded to odd lengths so that the running
-// sums of neighbouring rows hit distinct shared-memory banks.
+// sums of neighbouring rows hit distinct shared-memory banks.  Gamma(X, d) is added into a
+// shared row per tile row at entry X - X0 - d + D - 1 (within one step of d every lane of a
+// warp meets a distinct entry; the two steps of a round are ordered by a warp barrier, the
+// rounds by the block's), and the tile's rows of partial sums are written once at the end.
 constexpr int kCbDC = 2;
 
 // Running box sums of one plane row: out[x] = sum_{j < WN} in[x + j], x < 32.
@@ -637,6 +648,7 @@ __global__ void __launch_bounds__(256, 3) k_dcost_bwd(const CbArgs a)
     float *st = cb_smem;                       // [NP][QH][SW]
     float *hb = st + NP * SP;                  // [NP][QH][33]
     float *vb = hb + NP * HP;                  // [NP][8][32]
+    float *gts = vb + NP * 256;                // [8][32 + D - 1] partial diagonal sums
     const int b = blockIdx.z;
     const int W = a.W, H = a.H, D = a.D;
     const size_t HW = (size_t)H * W;
@@ -666,6 +678,9 @@ __global__ void __launch_bounds__(256, 3) k_dcost_bwd(const CbArgs a)
     const int yc = clampi(Y, 0, H - 1);
     const float rv = a.ref[b * HW + (size_t)yc * W + clampi(X, 0, W - 1)];
     const float *twrow = a.tw + b * HW + (size_t)yc * W;
+    const int GW = cb_diag_w(D);
+    if (a.gpart)
+        for (int i = threadIdx.x; i < 8 * GW; i += 256) gts[i] = 0.f;   // (the first round's barriers order these)
     float gacc = 0.f;
     // the loads of a round are issued one round ahead, so that they are in flight while the
     // previous round's box sums run
@@ -740,16 +755,23 @@ __global__ void __launch_bounds__(256, 3) k_dcost_bwd(const CbArgs a)
             const float bC = vb[(2 * DC + k) * 256 + ty * 32 + tx], bCm = vb[(3 * DC + k) * 256 + ty * 32 + tx];
             if (xin && d < D) {
                 const float t = twrow[clampi(X - d, 0, W - 1)];
-                if (a.gamma)
-                    a.gamma[(((size_t)b * D + d) * a.Hr + (Y + RW)) * a.Wr + (X + RW)] =
-                        fmaf(rv, bA, -bAm) + fmaf(t, bC, -bCm);
+                if (a.gpart) gts[ty * GW + tx - d + D - 1] += fmaf(rv, bA, -bAm) + fmaf(t, bC, -bCm);
                 gacc = fmaf(t, bA, gacc);
             }
+            __syncwarp();   // lane x at d + 1 meets the entry of lane x - 1 at d
         }
         // the next round's staging writes st only: hb and vb are rewritten after its barrier
     }
     // the d-independent terms: - box(sum_d A mu_b) + r box(sum_d B) - box(sum_d B mu_a)
     __syncthreads();
+    if (a.gpart) {
+        // this tile's partial diagonal sums, one row per tile row inside the extended grid
+        const int nbx = cb_tiles_x(a.Wr);
+        for (int i = threadIdx.x; i < 8 * GW; i += 256) {
+            const int r = i / GW, j = i - r * GW, row = blockIdx.y * 8 + r;
+            if (row < a.Hr) a.gpart[(((size_t)b * a.Hr + row) * nbx + blockIdx.x) * GW + j] = gts[i];
+        }
+    }
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         const int j = threadIdx.x + 256 * s;
@@ -777,16 +799,19 @@ __global__ void __launch_bounds__(256, 3) k_dcost_bwd(const CbArgs a)
         a.grefx[((size_t)b * a.Hr + (Y + RW)) * a.Wr + (X + RW)] = gacc - bx[0] + fmaf(rv, bx[1], -bx[2]);
 }
 
-// Target positions Xt in [-rw-(D-1), W-1+rw]: the sum over d of Gamma(Xt + d, d).
-__global__ void __launch_bounds__(256) k_dtgt_diag(const float *__restrict__ gamma, float *__restrict__ gtwx,
-                                                   int D, int rw, int Wr, int Hr, int Wt)
+// Target positions Xt in [-rw-(D-1), W-1+rw] (column c = Xt + rw + D - 1): the sum over d of
+// Gamma(Xt + d, d), as the partial sums of the cost adjoint's tiles whose columns reach it
+// (tile bx holds c in entry c - 32 bx), added in tile order.
+__global__ void __launch_bounds__(256) k_dtgt_diag(const float *__restrict__ gpart, float *__restrict__ gtwx,
+                                                   int D, int Wr, int Hr, int Wt)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x, row = blockIdx.y, b = blockIdx.z;
     if (c >= Wt) return;
-    const int xr = c - (D - 1);                  // Xt + rw
-    const int dlo = max(0, -xr), dhi = min(D - 1, Wr - 1 - xr);
+    const int GW = cb_diag_w(D), nbx = cb_tiles_x(Wr);
+    const int bxlo = max(0, (c - GW + 1 + 31) / 32), bxhi = min(nbx - 1, c / 32);
+    const float *p = gpart + ((size_t)b * Hr + row) * nbx * GW;
     float s = 0.f;
-    for (int d = dlo; d <= dhi; ++d) s += gamma[(((size_t)b * D + d) * Hr + row) * Wr + xr + d];
+    for (int bx = bxlo; bx <= bxhi; ++bx) s += p[(size_t)bx * GW + c - 32 * bx];
     gtwx[((size_t)b * Hr + row) * Wt + c] = s;
 }
 
@@ -932,7 +957,7 @@ template <int RW>
 cudaError_t launch_cb_rw(const CbArgs &a, int B, cudaStream_t st)
 {
     constexpr int QW = 32 + 2 * RW, QH = 8 + 2 * RW, NP = 4 * kCbDC;
-    const size_t smem = (size_t)NP * ((QW | 1) * QH + 33 * QH + 8 * 32) * sizeof(float);
+    const size_t smem = ((size_t)NP * ((QW | 1) * QH + 33 * QH + 8 * 32) + 8 * cb_diag_w(a.D)) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_dcost_bwd<RW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -1087,7 +1112,7 @@ extern "C" int stereo_softargmin_bwd(const stereo_diff_params *p, const float *r
     c.cost = w.cost;
     c.gc = w.gc;
     const bool need_tw = gtgt || gshift;    // the warped-target gradient feeds both
-    c.gamma = need_tw ? w.gamma : nullptr;
+    c.gpart = need_tw ? w.gpart : nullptr;
     c.grefx = w.grefx;
     c.W = d.W;
     c.H = d.H;
@@ -1098,8 +1123,7 @@ extern "C" int stereo_softargmin_bwd(const stereo_diff_params *p, const float *r
     c.inv_n = 1.0f / (float)d.n;
     if ((e = launch_cb(c, d.rw, B, st)) != cudaSuccess) return cuda_error(e, who);
     if (need_tw)
-        k_dtgt_diag<<<dim3((d.Wt + 255) / 256, d.Hr, B), 256, 0, st>>>(w.gamma, w.gtwx, d.D, d.rw, d.Wr,
-                                                                       d.Hr, d.Wt);
+        k_dtgt_diag<<<dim3((d.Wt + 255) / 256, d.Hr, B), 256, 0, st>>>(w.gpart, w.gtwx, d.D, d.Wr, d.Hr, d.Wt);
     if (gref || gtgt)
         k_dfold<<<dim3((d.W + 255) / 256, d.H, B), 256, 0, st>>>(w.grefx, w.gw, w.gtwx, shift, gref, gtgt, d.W,
                                                                  d.H, d.D, d.rw, d.Wr, d.Hr, d.Wt, d.warp_mode);

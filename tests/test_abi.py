@@ -162,7 +162,9 @@ def test_diff_defaults_and_workspace_size(lib):
     n = sgd.stereo_softargmin_workspace_bytes(p)
     W, H, B, D, rw = 960, 540, 8, 64, 4
     vol = B * D * H * W * 4
-    assert n >= 3 * vol + B * D * (H + 2 * rw) * (W + 2 * rw) * 4
+    # three volumes (c, h, dS/dc) and per-pixel arrays; the cost adjoint's Gamma(X, d) is summed
+    # along its diagonals inside the kernel, so no fourth volume
+    assert 3 * vol <= n <= 3.3 * vol
     assert n % 256 == 0
     # grows linearly in the batch
     p1 = sgd.stereo_diff_params_default(width=960, height=540, batch=1, max_disp=64)
