@@ -622,6 +622,21 @@ struct CbArgs {
 // rounds by the block's), and the tile's rows of partial sums are written once at the end.
 constexpr int kCbDC = 2;
 
+// Running box sums of one half of a plane row: out[x] = sum_{j < WN} in[x + j], x < 16.
+template <int WN>
+__device__ __forceinline__ void row_box16(const float *in, float *out)
+{
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < WN; ++j) s += in[j];
+    out[0] = s;
+#pragma unroll
+    for (int x = 1; x < 16; ++x) {
+        s += in[x + WN - 1] - in[x - 1];
+        out[x] = s;
+    }
+}
+
 // Running box sums of one plane row: out[x] = sum_{j < WN} in[x + j], x < 32.
 template <int WN>
 __device__ __forceinline__ void row_box(const float *in, float *out)
@@ -726,10 +741,12 @@ __global__ void __launch_bounds__(256, 3) k_dcost_bwd(const CbArgs a)
         }
         if (d0 + DC < D) load_round(d0 + DC);
         __syncthreads();
-        // ---- box sums along rows: one running sum per (plane, halo row)
-        for (int t = threadIdx.x; t < NP * QH; t += 256) {
-            const int p = t / QH, row = t - p * QH;
-            row_box<WN>(st + p * SP + row * SW, hb + p * HP + row * HW_);
+        // ---- box sums along rows: one running sum per (plane, halo row, half row); with the
+        // odd row strides the 32 lanes of a warp (16 rows, both halves) meet 32 distinct banks
+        for (int t = threadIdx.x; t < NP * QH * 2; t += 256) {
+            const int half = t & 1, pr = t >> 1;
+            const int p = pr / QH, row = pr - p * QH;
+            row_box16<WN>(st + p * SP + row * SW + 16 * half, hb + p * HP + row * HW_ + 16 * half);
         }
         __syncthreads();
         // ---- box sums along columns: one running sum per (plane, column) over the 8 tile rows
