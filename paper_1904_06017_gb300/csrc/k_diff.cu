@@ -89,7 +89,7 @@ struct Dims {
 };
 
 struct Ws {
-    float *tw, *mur, *sdr, *mut, *sdt, *cost, *lse, *lbar;      // forward
+    float *tw, *mur, *sdr, *mut, *sdt, *isdt, *cost, *lse, *lbar;      // forward (isdt: 1 / sdt, 0 where flat)
     float *h, *gc, *beta, *t1, *gw, *gpart, *grefx, *gtwx;      // backward
 };
 
@@ -108,6 +108,7 @@ size_t layout(const Dims &d, char *base, Ws *w)
     take(&o->sdr, B * img);
     take(&o->mut, B * (size_t)d.H * d.We);
     take(&o->sdt, B * (size_t)d.H * d.We);
+    take(&o->isdt, B * (size_t)d.H * d.We);
     take(&o->cost, B * vol);
     take(&o->lse, B * img);
     take(&o->lbar, B * img);
@@ -205,7 +206,8 @@ __global__ void __launch_bounds__(256) k_dwarp(const float *__restrict__ tgt, co
 // Window mean and population standard deviation over (2rw+1)^2 clamp-to-edge reads, on an
 // output grid of Wout columns whose column xo is centred on image column xo + off.
 __global__ void __launch_bounds__(256) k_dstats(const float *__restrict__ img, int W, int H, int Wout, int off,
-                                                int rw, float *__restrict__ mu, float *__restrict__ sd)
+                                                int rw, float *__restrict__ mu, float *__restrict__ sd,
+                                                float *__restrict__ isd)
 {
     extern __shared__ float s[];
     const int sw = 32 + 2 * rw, sh = 8 + 2 * rw;
@@ -235,7 +237,9 @@ __global__ void __launch_bounds__(256) k_dstats(const float *__restrict__ img, i
         }
     const size_t o = ((size_t)b * H + v) * Wout + xo;
     mu[o] = c0 + m;
-    sd[o] = sqrtf(q / n);
+    const float sv = sqrtf(q / n);
+    sd[o] = sv;
+    if (isd) isd[o] = sv > 0.f ? __frcp_rn(sv) : 0.f;   // the cost adjoint's 1 / s_b, once per position
 }
 
 // eq. (c) for a 32 x 8 pixel tile and kCostDC disparities: the centred reference window
@@ -604,7 +608,7 @@ __global__ void __launch_bounds__(agg_threads(MODE), MODE == AGG_FWD ? 3 : MODE 
 
 // ------------------------------------------------------------------ cost adjoint
 struct CbArgs {
-    const float *ref, *tw, *mur, *sdr, *mut, *sdt, *cost, *gc;
+    const float *ref, *tw, *mur, *sdr, *mut, *isdt, *cost, *gc;
     float *gpart;          // [B][Hr][tile column][32 + D - 1] partial diagonal sums of Gamma (or null)
     float *grefx;
     int W, H, D, Wr, Hr, We;
@@ -709,7 +713,7 @@ __global__ void __launch_bounds__(256, 3) k_dcost_bwd(const CbArgs a)
                 const size_t vo = vbase[s] + (size_t)(ok ? d0 + k : 0) * HW, so = sbase[s] - (ok ? d0 + k : 0);
                 g[s][k] = ok ? a.gc[vo] : 0.f;
                 cc[s][k] = ok ? a.cost[vo] : 1.f;
-                sb[s][k] = ok ? a.sdt[so] : 0.f;
+                sb[s][k] = ok ? a.isdt[so] : 0.f;   // 1 / s_b (0: a flat target block)
                 mb[s][k] = ok ? a.mut[so] : 0.f;
             }
     };
@@ -724,7 +728,7 @@ __global__ void __launch_bounds__(256, 3) k_dcost_bwd(const CbArgs a)
             for (int k = 0; k < DC; ++k) {
                 float A = 0.f, C = 0.f, Bq = 0.f;
                 if (qisa[s] > 0.f && sb[s][k] > 0.f) {
-                    const float isb = __frcp_rn(sb[s][k]);
+                    const float isb = sb[s][k];
                     const float gn = g[s][k] * a.inv_n, gnc = gn * (1.f - cc[s][k]);
                     A = -gn * qisa[s] * isb;
                     Bq = gnc * qisa[s] * qisa[s];
@@ -1060,9 +1064,9 @@ extern "C" int stereo_softargmin_fwd(const stereo_diff_params *p, const float *r
     k_dwarp<<<dim3((d.W + 255) / 256, d.H, B), 256, 0, st>>>(tgt, shift, w.tw, d.W, d.H, d.warp_mode);
     const size_t ssm = (size_t)(32 + 2 * d.rw) * (8 + 2 * d.rw) * sizeof(float);
     k_dstats<<<dim3((d.W + 31) / 32, (d.H + 7) / 8, B), 256, ssm, st>>>(ref, d.W, d.H, d.W, 0, d.rw, w.mur,
-                                                                        w.sdr);
+                                                                        w.sdr, nullptr);
     k_dstats<<<dim3((d.We + 31) / 32, (d.H + 7) / 8, B), 256, ssm, st>>>(w.tw, d.W, d.H, d.We, -(d.D - 1),
-                                                                         d.rw, w.mut, w.sdt);
+                                                                         d.rw, w.mut, w.sdt, w.isdt);
     const int nchunk = (d.D + kCostDC - 1) / kCostDC;
     const size_t csm = ((size_t)(32 + 2 * d.rw) + (32 + 2 * d.rw + kCostDC - 1)) * (8 + 2 * d.rw) * sizeof(float);
     {
@@ -1125,7 +1129,7 @@ extern "C" int stereo_softargmin_bwd(const stereo_diff_params *p, const float *r
     c.mur = w.mur;
     c.sdr = w.sdr;
     c.mut = w.mut;
-    c.sdt = w.sdt;
+    c.isdt = w.isdt;
     c.cost = w.cost;
     c.gc = w.gc;
     const bool need_tw = gtgt || gshift;    // the warped-target gradient feeds both
