@@ -28,6 +28,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <type_traits>
+
 #include "internal.cuh"
 #include "row_shift.cuh"
 #include "stereo_diff.h"
@@ -425,6 +427,10 @@ __global__ void __launch_bounds__(agg_threads(MODE), MODE == AGG_FWD ? 3 : MODE 
         }
     }
     float S[kAggRows];          // sum_q w (sI_q - sI_p), the same in every chunk
+    float Z[kAggRows];          // sum_q w, the same in every chunk
+    float invZ[kAggRows];
+    // Z and S depend on no disparity: the first chunk sums them (the same terms in the same
+    // order as any chunk would) and later chunks reuse them
     float beta[kAggRows], tacc[kAggRows];
 #pragma unroll
     for (int i = 0; i < kAggRows; ++i) S[i] = beta[i] = tacc[i] = 0.f;
@@ -446,66 +452,78 @@ __global__ void __launch_bounds__(agg_threads(MODE), MODE == AGG_FWD ? 3 : MODE 
 
         // accumulators in pairs of disparities (packed f32x2 FMAs)
         float2 acc0[kAggRows][DC / 2], acc1[kAggRows][TWO ? DC / 2 : 1];
-        float Z[kAggRows];
 #pragma unroll
         for (int i = 0; i < kAggRows; ++i) {
-            Z[i] = 0.f;
-            if constexpr (TWO) S[i] = 0.f;
+            if (kc == 0) {
+                Z[i] = 0.f;
+                if constexpr (TWO) S[i] = 0.f;
+            }
 #pragma unroll
             for (int k = 0; k < DC / 2; ++k) {
                 acc0[i][k] = make_float2(0.f, 0.f);
                 if constexpr (TWO) acc1[i][k] = make_float2(0.f, 0.f);
             }
         }
+        auto accumulate = [&](auto first_c) {
+            constexpr bool FIRST = decltype(first_c)::value;
 #pragma unroll 1
-        for (int dx = -RB; dx <= RB; ++dx) {
-            const float kx = a.k0 * (float)(dx * dx);
-            const int col = tx + RB + dx;
+            for (int dx = -RB; dx <= RB; ++dx) {
+                const float kx = a.k0 * (float)(dx * dx);
+                const int col = tx + RB + dx;
 #pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                const int srow = kAggRows * ty + r;
-                const float sq = sI[srow * TW + col];
-                float4 v4[NQ];
+                for (int r = 0; r < NR; ++r) {
+                    const int srow = kAggRows * ty + r;
+                    const float sq = sI[srow * TW + col];
+                    float4 v4[NQ];
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) v4[q] = V[(q * TH + srow) * TW + col];
+                    for (int q = 0; q < NQ; ++q) v4[q] = V[(q * TH + srow) * TW + col];
 #pragma unroll
-                for (int i = 0; i < kAggRows; ++i) {
-                    const int dy = r - RB - i;
-                    if (dy < -RB || dy > RB) continue;
-                    const float dd = sIp[i] - sq;
-                    const float w = ex2_fast(fmaf(-dd, dd, kx + ky[dy + RB]));
-                    Z[i] += w;
-                    const float2 w2 = make_float2(w, w);
-#pragma unroll
-                    for (int q = 0; q < NQ; ++q) {
-                        acc0[i][2 * q + 0] = __ffma2_rn(w2, make_float2(v4[q].x, v4[q].y), acc0[i][2 * q + 0]);
-                        acc0[i][2 * q + 1] = __ffma2_rn(w2, make_float2(v4[q].z, v4[q].w), acc0[i][2 * q + 1]);
-                    }
-                    if constexpr (TWO) {
-                        const float wd = -w * dd;
-                        S[i] += wd;
-                        const float2 wd2 = make_float2(wd, wd);
+                    for (int i = 0; i < kAggRows; ++i) {
+                        const int dy = r - RB - i;
+                        if (dy < -RB || dy > RB) continue;
+                        const float dd = sIp[i] - sq;
+                        const float w = ex2_fast(fmaf(-dd, dd, kx + ky[dy + RB]));
+                        if constexpr (FIRST) Z[i] += w;
+                        const float2 w2 = make_float2(w, w);
 #pragma unroll
                         for (int q = 0; q < NQ; ++q) {
-                            acc1[i][2 * q + 0] = __ffma2_rn(wd2, make_float2(v4[q].x, v4[q].y), acc1[i][2 * q + 0]);
-                            acc1[i][2 * q + 1] = __ffma2_rn(wd2, make_float2(v4[q].z, v4[q].w), acc1[i][2 * q + 1]);
+                            acc0[i][2 * q + 0] = __ffma2_rn(w2, make_float2(v4[q].x, v4[q].y), acc0[i][2 * q + 0]);
+                            acc0[i][2 * q + 1] = __ffma2_rn(w2, make_float2(v4[q].z, v4[q].w), acc0[i][2 * q + 1]);
+                        }
+                        if constexpr (TWO) {
+                            const float wd = -w * dd;
+                            if constexpr (FIRST) S[i] += wd;
+                            const float2 wd2 = make_float2(wd, wd);
+#pragma unroll
+                            for (int q = 0; q < NQ; ++q) {
+                                acc1[i][2 * q + 0] = __ffma2_rn(wd2, make_float2(v4[q].x, v4[q].y), acc1[i][2 * q + 0]);
+                                acc1[i][2 * q + 1] = __ffma2_rn(wd2, make_float2(v4[q].z, v4[q].w), acc1[i][2 * q + 1]);
+                            }
                         }
                     }
                 }
             }
+        };
+        if constexpr (MODE == AGG_GC) {
+            accumulate(std::false_type());   // (Z and S serve the other two modes only)
+        } else if (kc == 0) {
+            accumulate(std::true_type());
+#pragma unroll
+            for (int i = 0; i < kAggRows; ++i) invZ[i] = 1.f / Z[i];
+        } else {
+            accumulate(std::false_type());
         }
 
         // chunk epilogue
 #pragma unroll
         for (int i = 0; i < kAggRows; ++i) {
             if (!pin[i]) continue;
-            const float invZ = 1.f / Z[i];
             const size_t pix = (size_t)py[i] * W + px;
             if constexpr (MODE == AGG_FWD) {
                 float z[DC], mc = st0[i];
 #pragma unroll
                 for (int k = 0; k < DC; ++k) {
-                    z[k] = -(lane(acc0[i][k >> 1], k) * invZ) * a.kT;
+                    z[k] = -(lane(acc0[i][k >> 1], k) * invZ[i]) * a.kT;
                     if (d0 + k < D) mc = fmaxf(mc, z[k]);
                 }
                 const float sc = exp2f(st0[i] - mc);
@@ -525,9 +543,9 @@ __global__ void __launch_bounds__(agg_threads(MODE), MODE == AGG_FWD ? 3 : MODE 
                 for (int k = 0; k < DC; ++k) {
                     const int d = d0 + k;
                     if (d >= D) break;
-                    const float E = lane(acc0[i][k >> 1], k) * invZ;
+                    const float E = lane(acc0[i][k >> 1], k) * invZ[i];
                     const float P = exp2f(-E * a.kT - st1[i]);
-                    const float hv = -st0[i] * a.invT * P * ((float)d - st2[i]) * invZ;
+                    const float hv = -st0[i] * a.invT * P * ((float)d - st2[i]) * invZ[i];
                     a.h[((size_t)b * D + d) * HW + pix] = hv;
                     beta[i] = fmaf(hv, E, beta[i]);
                     tacc[i] = fmaf(hv, lane(acc1[i][k >> 1], k), tacc[i]);
