@@ -661,21 +661,33 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
                         }
                         Wta st = ws[0][k];
                         if (si == 1) st = ws[1][k];
+                        float cmin = e[0];
 #pragma unroll
-                        for (int dd = 0; dd < DC; ++dd) {
-                            if (dd >= dn) break;
-                            const float v = e[dd];
-                            const int d = d0 + dd;
-                            if (v < st.best) {
-                                if constexpr (B2) st.sec = st.best;
-                                st.best = v;
-                                st.bd = d;
-                                st.bm1 = st.prev;
-                            } else {
-                                if constexpr (B2) st.sec = fminf(st.sec, v);
-                                if (d == st.bd + 1) st.bp1 = v;
+                        for (int dd = 1; dd < DC; ++dd) cmin = fminf(cmin, e[dd]);
+                        if (dn == DC && !(cmin < st.best)) {
+                            // no new best in this full chunk: the walk below would only set E(d* + 1)
+                            // when d* is the previous chunk's last disparity, fold the chunk into
+                            // the smallest E over d != d*, and leave its last value as prev
+                            if (st.bd == d0 - 1) st.bp1 = e[0];
+                            if constexpr (B2) st.sec = fminf(st.sec, cmin);
+                            st.prev = e[DC - 1];
+                        } else {
+#pragma unroll
+                            for (int dd = 0; dd < DC; ++dd) {
+                                if (dd >= dn) break;
+                                const float v = e[dd];
+                                const int d = d0 + dd;
+                                if (v < st.best) {
+                                    if constexpr (B2) st.sec = st.best;
+                                    st.best = v;
+                                    st.bd = d;
+                                    st.bm1 = st.prev;
+                                } else {
+                                    if constexpr (B2) st.sec = fminf(st.sec, v);
+                                    if (d == st.bd + 1) st.bp1 = v;
+                                }
+                                st.prev = v;
                             }
-                            st.prev = v;
                         }
                         if (si == 0) ws[0][k] = st;
                         else ws[1][k] = st;
