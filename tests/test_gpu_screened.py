@@ -178,6 +178,17 @@ def test_screened_hd_workload_equals_simt(preset):
     assert_same(outs[0], outs[1])
 
 
+@pytest.mark.parametrize("W,H,D,win,bil", [(1280, 720, 100, 7, 9), (1000, 610, 45, 11, 13)])
+def test_screened_several_tiles_per_cta(W, H, D, win, bil):
+    """More tiles than SMs (the persistent kernel takes several in turn, each next tile's images
+    staged during the current one's refinement), a search range off the 32-disparity chunk,
+    ragged tiles at the right and bottom: still the SIMT form bit for bit."""
+    ref, tgt, shift = pair(W, H, 7, W + D)
+    a = run(ref, tgt, shift, D, win, bil, 3.0, 10.0, sg.STEREO_FUSED_SIMT)
+    b = run(ref, tgt, shift, D, win, bil, 3.0, 10.0, sg.STEREO_FUSED_TENSOR)
+    assert_same(a, b)
+
+
 def test_tensor_form_rejected_where_it_does_not_apply():
     with pytest.raises(sg.StereoError) as e:
         sg.Stereo(64, 48, 16, win=9, bil=15, fused_form=sg.STEREO_FUSED_TENSOR)
