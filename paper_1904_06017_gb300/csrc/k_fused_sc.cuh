@@ -692,15 +692,88 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
                         if (si == 0) ws[0][k] = st;
                         else ws[1][k] = st;
                     };
-                    put(0, 0);
-                    put(1, 1);
-                    __syncwarp();
-                    run(hb, 0);
-                    __syncwarp();
-                    put(2, 0);
-                    __syncwarp();
-                    if (hb == 0) run(0, 1);
-                    __syncwarp();
+                    // A full chunk in which no pixel of the warp gets a new best skips the E
+                    // blocks: each pixel's minimum over the chunk comes from its quad (lane (g, t4)
+                    // holds disparities 8 nb + 2 t4 + {0, 1} of pixels g and g + 8), and the lane
+                    // that keeps the pixel's WTA state (pixel m = g + 8 h: state 0 of patch hb,
+                    // state 1 of patch 2) receives it, and the chunk's first value E(d0) (lane 4 g,
+                    // nb = 0) and last value E(d0 + 31) (lane 4 g + 3, nb = 3), by shuffles; the
+                    // state then takes what run() would give it for such a chunk
+                    bool walk = dn < DC;
+                    if (!walk) {
+                        float c[3][2];
+#pragma unroll
+                        for (int i = 0; i < 3; ++i)
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                float v = fminf(acc[i][0][2 * h], acc[i][0][2 * h + 1]);
+#pragma unroll
+                                for (int nb = 1; nb < 4; ++nb) v = fminf(v, fminf(acc[i][nb][2 * h], acc[i][nb][2 * h + 1]));
+                                v = fminf(v, __shfl_xor_sync(0xffffffffu, v, 1));
+                                c[i][h] = fminf(v, __shfl_xor_sync(0xffffffffu, v, 2));
+                            }
+                        const int src = 4 * (m & 7), hm = m >> 3;
+                        auto pick = [&](const float (&x)[3][2], int patch) {
+                            // x[patch][hm] of the shuffled values, with static indices
+                            const float a0 = hm ? x[0][1] : x[0][0], a1 = hm ? x[1][1] : x[1][0];
+                            const float a2 = hm ? x[2][1] : x[2][0];
+                            return patch == 2 ? a2 : patch == 1 ? a1 : a0;
+                        };
+                        float xm[3][2];
+#pragma unroll
+                        for (int i = 0; i < 3; ++i)
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) xm[i][h] = __shfl_sync(0xffffffffu, c[i][h], src);
+                        Wta s0 = ws[0][0], s1 = ws[0][1];
+                        if (si == 1) {
+                            s0 = ws[1][0];
+                            s1 = ws[1][1];
+                        }
+                        const float m0 = pick(xm, hb), m1 = pick(xm, 2);
+                        walk = __any_sync(0xffffffffu, m0 < s0.best || (hb == 0 && m1 < s1.best));
+                        if (!walk) {
+                            float xl[3][2], xf[3][2];
+#pragma unroll
+                            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                                for (int h = 0; h < 2; ++h) {
+                                    xl[i][h] = __shfl_sync(0xffffffffu, acc[i][3][2 * h + 1], src + 3);
+                                    xf[i][h] = 0.f;
+                                }
+                            if (__any_sync(0xffffffffu, s0.bd == d0 - 1 || (hb == 0 && s1.bd == d0 - 1))) {
+#pragma unroll
+                                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                                    for (int h = 0; h < 2; ++h) xf[i][h] = __shfl_sync(0xffffffffu, acc[i][0][2 * h], src);
+                            }
+                            if (s0.bd == d0 - 1) s0.bp1 = pick(xf, hb);
+                            if constexpr (B2) s0.sec = fminf(s0.sec, m0);
+                            s0.prev = pick(xl, hb);
+                            if (hb == 0) {
+                                if (s1.bd == d0 - 1) s1.bp1 = pick(xf, 2);
+                                if constexpr (B2) s1.sec = fminf(s1.sec, m1);
+                                s1.prev = pick(xl, 2);
+                            }
+                            if (si == 0) {
+                                ws[0][0] = s0;
+                                ws[0][1] = s1;
+                            } else {
+                                ws[1][0] = s0;
+                                ws[1][1] = s1;
+                            }
+                        }
+                    }
+                    if (walk) {
+                        put(0, 0);
+                        put(1, 1);
+                        __syncwarp();
+                        run(hb, 0);
+                        __syncwarp();
+                        put(2, 0);
+                        __syncwarp();
+                        if (hb == 0) run(0, 1);
+                        __syncwarp();
+                    }
                 } else {
                     // the screening update, straight from the fragments: lane (g, t4) holds
                     // disparities 8 nb + 2 t4 + {0, 1} (nb = 0..3) of pixels g and g + 8, and the
