@@ -453,6 +453,7 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
     __shared__ int s_flag;
     __shared__ int s_rlo, s_rhi;
     __shared__ int s_next, s_claimed, s_staged;   // the work item claimed ahead, its copies issued
+    __shared__ int s_dend;                        // the tile's screening chunks start below this
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t4 = lane & 3;      // fragment row group and column pair
@@ -497,6 +498,17 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
         if (tid == 0) {
             s_rlo = 0x7fffffff;
             s_rhi = -1;
+        }
+        if (!PLAIN && warp == 0) {
+            // For d >= df = max(0, u + m - L + 1) every cost behind pixel (u, v) repeats its value at
+            // df (L: the row table's shortest column-0 run over v +- m), so a chunk that starts past
+            // the tile's largest df + 1 changes no candidate range (they are clipped at df + 1): the
+            // screening stops before it.  (The 16-bit form's running WTA would take the same cut,
+            // its values tying E(df), without best2; there the extra live state costs more.)
+            int lm = 0x7fffffff;
+            for (int v = y0 + lane; v < min(y0 + TY, a.H); v += 32) lm = min(lm, __ldg(&a.row_tab[v].w));
+            lm = __reduce_min_sync(0xffffffffu, lm);
+            if (lane == 0) s_dend = min(a.D, max(0, min(x0 + TX, a.W) - 1 + a.m - lm + 1) + 2);
         }
 
         if (!sc_stage(pd, a, sref, stgt, &s_bar, &s_flag, x0, y0, iter, tid, issued)) return;
@@ -562,7 +574,8 @@ k_fused_sc(const __grid_constant__ PairDesc single, const PairDesc *__restrict__
                 ws[si][k] = Wta{inf, inf, inf, inf, inf, -1};
             }
 
-        for (int d0 = 0; d0 < (B2 && !PLAIN ? 0 : a.D); d0 += DC) {
+        const int dend = B2 ? 0 : s_dend;   // the screened form's bound (set before sc_stage's barrier)
+        for (int d0 = 0; d0 < (PLAIN ? a.D : dend); d0 += DC) {
             // ---- costs of the chunk, 32 disparities, times 2^8, FP16, swizzled
             switch (rw) {
             case 1: cost_chunk<RB, DC, 1, T, TX, TY, kThreads, 0, kScBand, true, kScCSh, 0, 0, kScSeg>(a, sref, stgt, cb16, vband, sstr, sstt, x0, y0, d0, tid); break;
