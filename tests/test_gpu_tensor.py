@@ -120,6 +120,43 @@ def test_tensor_form_best_and_second_cost(dtype):
     assert err <= GAP[dtype] / 2
 
 
+def _with_best2(ref, tgtw, shift, D, win, bil, dtype, best2):
+    H, W = ref.shape
+    pitch = pitch_of(W)
+    disp = torch.full((H, W), float("nan"), dtype=torch.float32, device="cuda")
+    wta = torch.full((H, W), -7, dtype=torch.int32, device="cuda")
+    valid = torch.full((H, W), 9, dtype=torch.uint8, device="cuda")
+    b2 = torch.empty((H, W, 2), dtype=torch.float32, device="cuda") if best2 else None
+    with sg.Stereo(W, H, D, win=win, bil=bil, sigma0=3.0, sigma1=10.0, pitch=pitch, cost_dtype=dtype) as st:
+        st.cost_aggregate_wta(dev_img(ref, pitch), dev_img(tgtw, pitch), dev_f32(shift), disp, wta, valid,
+                              best2=b2)
+        st.check_device_status()
+    return disp.cpu().numpy(), wta.cpu().numpy(), valid.cpu().numpy()
+
+
+@pytest.mark.parametrize("dtype", [sg.STEREO_F16, sg.STEREO_BF16])
+@pytest.mark.parametrize("W,win,bil", [(150, 9, 11), (600, 5, 7), (300, 7, 13)])
+def test_tensor_form_best2_keeps_the_wta(dtype, W, win, bil):
+    """The 16-bit form's best2 instance carries the smallest E over d != d* beside the running
+    WTA; the WTA itself must not move.  On target rows that repeat their column-0 value over runs
+    of 1 column to the whole row (long tails of tied costs), both instances must give the same
+    disparity, WTA and validity maps bit for bit."""
+    H, D = 70, 96
+    rng = np.random.default_rng(21 + W + bil)
+    ref = synth.texture(rng, H, W)
+    tgt = np.empty_like(ref)
+    tgt[:, :W - 3] = ref[:, 3:]
+    tgt[:, W - 3:] = ref[:, -1:]
+    runs = np.minimum(rng.choice([1, 2, 5, 7, 8, 9, 31, 32, 33, 100, 255, 256, 257, 520, W], size=H), W)
+    for v in range(H):
+        tgt[v, :runs[v]] = tgt[v, 0]
+    shift = np.zeros(H, np.float32)
+    a = _with_best2(ref, tgt, shift, D, win, bil, dtype, False)
+    b = _with_best2(ref, tgt, shift, D, win, bil, dtype, True)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y, equal_nan=x.dtype.kind == "f")
+
+
 def test_best2_needs_a_form_that_carries_it():
     """bil = 15 leaves FP16 storage on the SIMT form, which has no best2 instantiation."""
     W, H, D = 70, 40, 24
