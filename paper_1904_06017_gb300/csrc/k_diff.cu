@@ -244,49 +244,119 @@ __global__ void __launch_bounds__(256) k_dstats(const float *__restrict__ img, i
     if (isd) isd[o] = sv > 0.f ? __frcp_rn(sv) : 0.f;   // the cost adjoint's 1 / s_b, once per position
 }
 
-// eq. (c) for a 32 x 8 pixel tile and kCostDC disparities: the centred reference window
-// times the target window, corrected by the target mean through sum_i (a_i - mu_a).  Along a
-// block row the target values of the DC disparities slide by one column per step, so they
-// are kept in a register window that takes one new shared-memory load per step.
-template <int RW>
-__global__ void __launch_bounds__(256) k_dcost(const float *__restrict__ ref, const float *__restrict__ tw,
-                                               const float *__restrict__ mur, const float *__restrict__ sdr,
-                                               const float *__restrict__ mut, const float *__restrict__ sdt,
-                                               float *__restrict__ cost, int W, int H, int D, int nchunk)
+// eq. (c) for a 64 x 8 pixel tile and kCostDC disparities: the centred reference window
+// times the target window, corrected by the target mean through sum_i (a_i - mu_a).  Thread
+// (tx, ty) owns the four pixels (x0 + tx + 32 j, y0 + 2 ty + h), j, h in {0, 1}, the columns
+// j = 0, 1 as the two lanes of packed f32x2 operations: both images are staged as pairs
+// (value at column c, value at column c + 32), so a warp's pair loads are consecutive 8-byte
+// words.  Along an image row the target pairs of the DC disparities slide by one column per
+// step and are kept in a register window that takes one new load per step; each image row of
+// the tile's halo serves both pixel rows of the thread (window rows dy and dy - 1).  Every
+// pixel and disparity takes the same terms in the same order (dy, then dx) as a scalar loop.
+constexpr int kCostTX = 64, kCostTY = 8, kCostThreads = 16 * kCostTY;
+__host__ __device__ constexpr int dcost_rw_pairs(int rw) { return 32 + 2 * rw; }
+__host__ __device__ constexpr int dcost_tw_pairs(int rw) { return 32 + 2 * rw + kCostDC - 1; }
+__host__ __device__ constexpr int dcost_rows(int rw) { return kCostTY + 2 * rw; }
+constexpr int kCostSW = kCostTX + kCostDC - 1;   // target statistics per tile row
+__host__ __device__ constexpr size_t dcost_smem(int rw)
 {
-    constexpr int DC = kCostDC, rw = RW;
-    extern __shared__ float s[];
-    const int sw = 32 + 2 * rw, sh = 8 + 2 * rw, st = 32 + 2 * rw + DC - 1;
-    float *rs = s, *ts = s + sw * sh;
+    return (size_t)(dcost_rw_pairs(rw) + dcost_tw_pairs(rw)) * dcost_rows(rw) * sizeof(float2) +
+           (size_t)2 * kCostTY * kCostSW * sizeof(float);
+}
+
+template <int RW>
+__global__ void __launch_bounds__(kCostThreads, 3) k_dcost(const float *__restrict__ ref, const float *__restrict__ tw,
+                                                  const float *__restrict__ mur, const float *__restrict__ sdr,
+                                                  const float *__restrict__ mut, const float *__restrict__ sdt,
+                                                  float *__restrict__ cost, int W, int H, int D, int nchunk)
+{
+    constexpr int DC = kCostDC, rw = RW, w = 2 * RW + 1;
+    constexpr int PRW = dcost_rw_pairs(RW), PTW = dcost_tw_pairs(RW), SH = dcost_rows(RW);
+    extern __shared__ float2 s2[];
+    float2 *pr = s2, *pt = s2 + SH * PRW;        // [SH][PRW], [SH][PTW]
+    float *smb = reinterpret_cast<float *>(pt + SH * PTW), *ssb = smb + kCostTY * kCostSW;   // [TY][SW]
     const int b = blockIdx.z / nchunk, d0 = (blockIdx.z % nchunk) * DC;
-    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8;
+    const int x0 = blockIdx.x * kCostTX, y0 = blockIdx.y * kCostTY;
     const size_t HW = (size_t)H * W;
     const float *R = ref + b * HW, *T = tw + b * HW;
-    for (int i = threadIdx.x; i < sw * sh; i += 256) {
-        const int r = i / sw, c = i - r * sw;
-        rs[i] = R[(size_t)clampi(y0 - rw + r, 0, H - 1) * W + clampi(x0 - rw + c, 0, W - 1)];
-    }
-    const int tc0 = x0 - d0 - (DC - 1) - rw;     // image column of ts column 0
-    for (int i = threadIdx.x; i < st * sh; i += 256) {
-        const int r = i / st, c = i - r * st;
-        ts[i] = T[(size_t)clampi(y0 - rw + r, 0, H - 1) * W + clampi(tc0 + c, 0, W - 1)];
+    // Staging: every load of a thread is issued before its first shared-memory store, so the
+    // loads are in flight together rather than one L2 round trip per entry.
+    const int tc0 = x0 - d0 - (DC - 1) - rw;     // image column of pt column 0
+    const int We = W + D - 1, sc0 = x0 - d0 + D - DC;
+    constexpr int NPR = (SH * PRW + kCostThreads - 1) / kCostThreads;
+    constexpr int NPT = (SH * PTW + kCostThreads - 1) / kCostThreads;
+    constexpr int NSB = (kCostTY * kCostSW + kCostThreads - 1) / kCostThreads;
+    {
+        float2 vr[NPR], vt[NPT], vs[NSB];
+#pragma unroll
+        for (int it = 0; it < NPR; ++it) {
+            const int i = threadIdx.x + it * kCostThreads, r = i / PRW, c = i - r * PRW;
+            const float *row = R + (size_t)clampi(y0 - rw + r, 0, H - 1) * W;
+            const int x = x0 - rw + c;
+            if (i < SH * PRW) vr[it] = make_float2(row[clampi(x, 0, W - 1)], row[clampi(x + 32, 0, W - 1)]);
+        }
+#pragma unroll
+        for (int it = 0; it < NPT; ++it) {
+            const int i = threadIdx.x + it * kCostThreads, r = i / PTW, c = i - r * PTW;
+            const float *row = T + (size_t)clampi(y0 - rw + r, 0, H - 1) * W;
+            if (i < SH * PTW) vt[it] = make_float2(row[clampi(tc0 + c, 0, W - 1)], row[clampi(tc0 + c + 32, 0, W - 1)]);
+        }
+        // the target statistics the tile's epilogue reads: row v, columns u - d + D - 1 of the
+        // extended grid, entry (u - x0) - (d - d0) + DC - 1
+#pragma unroll
+        for (int it = 0; it < NSB; ++it) {
+            const int i = threadIdx.x + it * kCostThreads, r = i / kCostSW, c = i - r * kCostSW;
+            const int v = y0 + r, xe = sc0 + c;
+            const bool ok = i < kCostTY * kCostSW && v < H && xe >= 0 && xe < We;
+            const size_t so = ((size_t)b * H + (ok ? v : 0)) * We + (ok ? xe : 0);
+            vs[it] = ok ? make_float2(mut[so], sdt[so]) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int it = 0; it < NPR; ++it) {
+            const int i = threadIdx.x + it * kCostThreads;
+            if (i < SH * PRW) pr[i] = vr[it];
+        }
+#pragma unroll
+        for (int it = 0; it < NPT; ++it) {
+            const int i = threadIdx.x + it * kCostThreads;
+            if (i < SH * PTW) pt[i] = vt[it];
+        }
+#pragma unroll
+        for (int it = 0; it < NSB; ++it) {
+            const int i = threadIdx.x + it * kCostThreads;
+            if (i < kCostTY * kCostSW) {
+                smb[i] = vs[it].x;
+                ssb[i] = vs[it].y;
+            }
+        }
     }
     __syncthreads();
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int u = x0 + tx, v = y0 + ty;
-    if (u >= W || v >= H) return;
-    const size_t pix = b * HW + (size_t)v * W + u;
-    const float ma = mur[pix], sa = sdr[pix];
-    constexpr int w = 2 * RW + 1;
-    float acc[DC];
+    const int u0 = x0 + tx, v0 = y0 + 2 * ty;
+    auto inside = [&](int h, int j) { return u0 + 32 * j < W && v0 + h < H; };
+    float2 ma[2];
 #pragma unroll
-    for (int k = 0; k < DC; ++k) acc[k] = 0.f;
-    float asum = 0.f;
-#pragma unroll 1
-    for (int dy = 0; dy < w; ++dy) {
-        const float *rrow = rs + (ty + dy) * sw + tx;
-        const float *trow = ts + (ty + dy) * st + tx + (DC - 1);
-        float win[DC];                      // win[k] = trow[dx - k]
+    for (int h = 0; h < 2; ++h) {
+        float m2[2] = {0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+            if (inside(h, j)) m2[j] = mur[b * HW + (size_t)(v0 + h) * W + u0 + 32 * j];
+        ma[h] = make_float2(m2[0], m2[1]);
+    }
+    float2 acc[2][DC], asum[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        asum[h] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < DC; ++k) acc[h][k] = make_float2(0.f, 0.f);
+    }
+    // image row y of the thread's halo (tile row 2 ty + y): window row y of pixel row 0 and
+    // window row y - 1 of pixel row 1
+    auto row = [&](int y, auto h0_c, auto h1_c) {
+        constexpr bool H0 = decltype(h0_c)::value, H1 = decltype(h1_c)::value;
+        const float2 *rrow = pr + (2 * ty + y) * PRW + tx;
+        const float2 *trow = pt + (2 * ty + y) * PTW + tx + (DC - 1);
+        float2 win[DC];                      // win[k] = trow[dx - k]
 #pragma unroll
         for (int k = 0; k < DC; ++k) win[k] = trow[-k];
 #pragma unroll
@@ -296,24 +366,46 @@ __global__ void __launch_bounds__(256) k_dcost(const float *__restrict__ ref, co
                 for (int k = DC - 1; k > 0; --k) win[k] = win[k - 1];
                 win[0] = trow[dx];
             }
-            const float a = rrow[dx] - ma;
-            asum += a;
+            const float2 r = rrow[dx];
+            if constexpr (H0) {
+                const float2 a = __fadd2_rn(r, make_float2(-ma[0].x, -ma[0].y));
+                asum[0] = __fadd2_rn(asum[0], a);
 #pragma unroll
-            for (int k = 0; k < DC; ++k) acc[k] = fmaf(a, win[k], acc[k]);
+                for (int k = 0; k < DC; ++k) acc[0][k] = __ffma2_rn(a, win[k], acc[0][k]);
+            }
+            if constexpr (H1) {
+                const float2 a = __fadd2_rn(r, make_float2(-ma[1].x, -ma[1].y));
+                asum[1] = __fadd2_rn(asum[1], a);
+#pragma unroll
+                for (int k = 0; k < DC; ++k) acc[1][k] = __ffma2_rn(a, win[k], acc[1][k]);
+            }
         }
-    }
-    const int We = W + D - 1;
+    };
+    row(0, std::true_type(), std::false_type());
+#pragma unroll 1
+    for (int y = 1; y < w; ++y) row(y, std::true_type(), std::true_type());
+    row(w, std::false_type(), std::true_type());
+
     const float n = (float)(w * w);
 #pragma unroll
-    for (int k = 0; k < DC; ++k) {
-        const int d = d0 + k;
-        if (d >= D) break;
-        const size_t so = ((size_t)b * H + v) * We + (u - d + D - 1);
-        const float mb = mut[so], sb = sdt[so];
-        float c = 1.f;
-        if (sa > 0.f && sb > 0.f) c = 1.f - fmaf(-mb, asum, acc[k]) / (n * sa * sb);
-        cost[((size_t)b * D + d) * HW + (size_t)v * W + u] = c;
-    }
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            if (!inside(h, j)) continue;
+            const int u = u0 + 32 * j, v = v0 + h;
+            const float sav = sdr[b * HW + (size_t)v * W + u], as = j ? asum[h].y : asum[h].x;
+#pragma unroll
+            for (int k = 0; k < DC; ++k) {
+                const int d = d0 + k;
+                if (d >= D) break;
+                const int e = (2 * ty + h) * kCostSW + tx + 32 * j - k + DC - 1;
+                const float mb = smb[e], sb = ssb[e];
+                const float ak = j ? acc[h][k].y : acc[h][k].x;
+                float c = 1.f;
+                if (sav > 0.f && sb > 0.f) c = 1.f - fmaf(-mb, as, ak) / (n * sav * sb);
+                cost[((size_t)b * D + d) * HW + (size_t)v * W + u] = c;
+            }
+        }
 }
 
 // ------------------------------------------------------------------ aggregation stencil
@@ -368,6 +460,7 @@ __global__ void __launch_bounds__(agg_threads(MODE), MODE == AGG_FWD ? 3 : MODE 
     extern __shared__ float4 smem4[];
     float4 *Vbuf = smem4;                                     // [1 or 2][NQ][TH][TW]
     float *sI = (float *)(Vbuf + (DB ? 2 : 1) * NQ * TH * TW); // [TH][TW]
+    float *scst = sI + TH * TW;                                  // AGG_GC: [DC][agg_ty][agg_tx], c(x, d)
     const int b = blockIdx.z, x0 = blockIdx.x * kAggTX, y0 = blockIdx.y * kAggTY;
     constexpr int WCOL = kAggTX / 32;               // warp columns of the tile
     const int warp = threadIdx.x >> 5;
@@ -391,12 +484,33 @@ __global__ void __launch_bounds__(agg_threads(MODE), MODE == AGG_FWD ? 3 : MODE 
                 }
             }
         }
+        if constexpr (MODE == AGG_GC) {
+            // the centre pixels' costs of the chunk, read by the chunk's epilogue
+            for (int i = threadIdx.x; i < DC * kAggTY * kAggTX; i += kAggThreads) {
+                const int k = i / (kAggTY * kAggTX), rc = i - k * (kAggTY * kAggTX);
+                const int r = rc / kAggTX, c = rc - r * kAggTX, y = y0 + r, x = x0 + c, d = d0 + k;
+                const bool ok = y < H && x < W && d < D;
+                cp_async4(scst + i, ok ? a.cost + ((size_t)b * D + d) * HW + (size_t)y * W + x : a.cost, ok);
+            }
+        }
         cp_async_commit();
     };
     if constexpr (DB) issue_chunk(0, Vbuf);
-    for (int i = threadIdx.x; i < TH * TW; i += kAggThreads) {
-        const int r = i / TW, c = i - r * TW, y = y0 - RB + r, x = x0 - RB + c;
-        sI[i] = (y >= 0 && y < H && x >= 0 && x < W) ? img[(size_t)y * W + x] * a.kappa : kFar;
+    {
+        // every load of a thread before its first store: the loads are in flight together
+        constexpr int NI = (TH * TW + kAggThreads - 1) / kAggThreads;
+        float vi[NI];
+#pragma unroll
+        for (int it = 0; it < NI; ++it) {
+            const int i = threadIdx.x + it * kAggThreads, r = i / TW, c = i - r * TW;
+            const int y = y0 - RB + r, x = x0 - RB + c;
+            vi[it] = (i < TH * TW && y >= 0 && y < H && x >= 0 && x < W) ? img[(size_t)y * W + x] * a.kappa : kFar;
+        }
+#pragma unroll
+        for (int it = 0; it < NI; ++it) {
+            const int i = threadIdx.x + it * kAggThreads;
+            if (i < TH * TW) sI[i] = vi[it];
+        }
     }
     float ky[2 * RB + 1];
 #pragma unroll
@@ -557,7 +671,8 @@ __global__ void __launch_bounds__(agg_threads(MODE), MODE == AGG_FWD ? 3 : MODE 
                     if (d >= D) break;
                     const size_t o = ((size_t)b * D + d) * HW + pix;
                     a.gc[o] = lane(acc0[i][k >> 1], k);
-                    tacc[i] = fmaf(a.cost[o], lane(acc1[i][k >> 1], k), tacc[i]);
+                    const float cx = scst[(k * kAggTY + kAggRows * ty + i) * kAggTX + tx];
+                    tacc[i] = fmaf(cx, lane(acc1[i][k >> 1], k), tacc[i]);
                 }
             }
         }
@@ -592,8 +707,11 @@ __global__ void __launch_bounds__(agg_threads(MODE), MODE == AGG_FWD ? 3 : MODE 
     float *sb = (float *)Vbuf;
     for (int i = threadIdx.x; i < TH * TW; i += kAggThreads) {
         const int r = i / TW, c = i - r * TW, y = y0 - RB + r, x = x0 - RB + c;
-        sb[i] = (y >= 0 && y < H && x >= 0 && x < W) ? a.beta[b * HW + (size_t)y * W + x] : 0.f;
+        const bool in = y >= 0 && y < H && x >= 0 && x < W;
+        cp_async4(sb + i, in ? a.beta + b * HW + (size_t)y * W + x : a.beta, in);
     }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
     float sbeta[kAggRows];
 #pragma unroll
@@ -968,7 +1086,8 @@ cudaError_t launch_agg_rb(const AggArgs &a, int B, cudaStream_t st)
 {
     constexpr int TW = agg_tx(MODE) + 2 * RB, TH = agg_ty(MODE) + 2 * RB;
     constexpr int NB = agg_dbuf(MODE) ? 2 : 1;
-    const size_t smem = (size_t)TW * TH * (NB * sizeof(float4) * (kAggDC / 4) + sizeof(float));
+    const size_t smem = (size_t)TW * TH * (NB * sizeof(float4) * (kAggDC / 4) + sizeof(float)) +
+                        (MODE == AGG_GC ? (size_t)kAggDC * agg_tx(MODE) * agg_ty(MODE) * sizeof(float) : 0);
     cudaError_t e = cudaFuncSetAttribute(k_dagg<MODE, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -1086,11 +1205,11 @@ extern "C" int stereo_softargmin_fwd(const stereo_diff_params *p, const float *r
     k_dstats<<<dim3((d.We + 31) / 32, (d.H + 7) / 8, B), 256, ssm, st>>>(w.tw, d.W, d.H, d.We, -(d.D - 1),
                                                                          d.rw, w.mut, w.sdt, w.isdt);
     const int nchunk = (d.D + kCostDC - 1) / kCostDC;
-    const size_t csm = ((size_t)(32 + 2 * d.rw) + (32 + 2 * d.rw + kCostDC - 1)) * (8 + 2 * d.rw) * sizeof(float);
+    const size_t csm = dcost_smem(d.rw);
     {
-        const dim3 grid((d.W + 31) / 32, (d.H + 7) / 8, B * nchunk);
+        const dim3 grid((d.W + kCostTX - 1) / kCostTX, (d.H + kCostTY - 1) / kCostTY, B * nchunk);
 #define SGB_DCOST(R)                                                                                  \
-    k_dcost<R><<<grid, 256, csm, st>>>(ref, w.tw, w.mur, w.sdr, w.mut, w.sdt, w.cost, d.W, d.H, d.D, nchunk)
+    k_dcost<R><<<grid, kCostThreads, csm, st>>>(ref, w.tw, w.mur, w.sdr, w.mut, w.sdt, w.cost, d.W, d.H, d.D, nchunk)
         switch (d.rw) {
         case 0: SGB_DCOST(0); break;
         case 1: SGB_DCOST(1); break;
