@@ -215,9 +215,21 @@ __global__ void __launch_bounds__(256) k_dstats(const float *__restrict__ img, i
     const int sw = 32 + 2 * rw, sh = 8 + 2 * rw;
     const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8, b = blockIdx.z;
     const float *im = img + (size_t)b * H * W;
-    for (int i = threadIdx.x; i < sw * sh; i += 256) {
-        const int r = i / sw, c = i - r * sw;
-        s[i] = im[(size_t)clampi(y0 - rw + r, 0, H - 1) * W + clampi(x0 + off - rw + c, 0, W - 1)];
+    {
+        // at most (32 + 14) x (8 + 14) entries: every load of a thread before its first store
+        constexpr int NI = (46 * 22 + 255) / 256;
+        float vi[NI];
+#pragma unroll
+        for (int it = 0; it < NI; ++it) {
+            const int i = threadIdx.x + 256 * it, r = i / sw, c = i - r * sw;
+            vi[it] = i < sw * sh ? im[(size_t)clampi(y0 - rw + r, 0, H - 1) * W + clampi(x0 + off - rw + c, 0, W - 1)]
+                                 : 0.f;
+        }
+#pragma unroll
+        for (int it = 0; it < NI; ++it) {
+            const int i = threadIdx.x + 256 * it;
+            if (i < sw * sh) s[i] = vi[it];
+        }
     }
     __syncthreads();
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -734,11 +746,14 @@ __global__ void __launch_bounds__(agg_threads(MODE), MODE == AGG_FWD ? 3 : MODE 
             }
         }
     }
+    float t1v[kAggRows];   // (all loads before the first store)
+#pragma unroll
+    for (int i = 0; i < kAggRows; ++i) t1v[i] = pin[i] ? a.t1[b * HW + (size_t)py[i] * W + px] : 0.f;
 #pragma unroll
     for (int i = 0; i < kAggRows; ++i) {
         if (!pin[i]) continue;
         const size_t o = b * HW + (size_t)py[i] * W + px;
-        a.gw[o] = a.gw_scale * (a.t1[o] + tacc[i] - sbeta[i]);
+        a.gw[o] = a.gw_scale * (t1v[i] + tacc[i] - sbeta[i]);
     }
 }
 
