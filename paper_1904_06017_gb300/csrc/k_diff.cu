@@ -766,7 +766,8 @@ struct CbArgs {
     float inv_n;
 };
 
-// Extended reference positions X in [-rw, W-1+rw] x [-rw, H-1+rw], a 32 x 8 tile per block.
+// Extended reference positions X in [-rw, W-1+rw] x [-rw, H-1+rw], a 32 x kCbTY tile per block
+// (a thread owns two of its rows, 8 apart).
 // kCbDC disparities at a time: the four window-pair terms A, A mu_a, C, C mu_b of the pairs q
 // in the tile's halo are staged and box-summed with running sums (along rows, then along
 // columns); the d-independent terms of the reference gradient are summed over d per q and
@@ -776,6 +777,7 @@ struct CbArgs {
 // warp meets a distinct entry; the two steps of a round are ordered by a warp barrier, the
 // rounds by the block's), and the tile's rows of partial sums are written once at the end.
 constexpr int kCbDC = 2;
+constexpr int kCbTY = 16;   // extended rows per tile (two per thread, 8 apart)
 
 // Running box sums of one half of a plane row: out[x] = sum_{j < WN} in[x + j], x < 16.
 template <int WN>
@@ -808,32 +810,43 @@ __device__ __forceinline__ void row_box(const float *in, float *out)
 }
 
 template <int RW>
-__global__ void __launch_bounds__(256, 3) k_dcost_bwd(const CbArgs a)
+__global__ void __launch_bounds__(256, 2) k_dcost_bwd(const CbArgs a)
 {
-    constexpr int QW = 32 + 2 * RW, QH = 8 + 2 * RW, NQ = QW * QH, NS = (NQ + 255) / 256;
+    constexpr int TY = kCbTY, RPT = TY / 8;                     // tile rows; rows per thread (8 apart)
+    constexpr int QW = 32 + 2 * RW, QH = TY + 2 * RW, NQ = QW * QH, NS = (NQ + 255) / 256;
     constexpr int WN = 2 * RW + 1, DC = kCbDC, NP = 4 * DC;   // planes: 4 terms x DC disparities
     constexpr int SW = QW | 1, SP = SW * QH;                    // staged row stride (odd), plane size
     constexpr int HW_ = 33, HP = HW_ * QH;                      // row-summed row stride (odd), plane size
     extern __shared__ float cb_smem[];
     float *st = cb_smem;                       // [NP][QH][SW]
     float *hb = st + NP * SP;                  // [NP][QH][33]
-    float *vb = hb + NP * HP;                  // [NP][8][32]
-    float *gts = vb + NP * 256;                // [8][32 + D - 1] partial diagonal sums
+    float *vb = hb + NP * HP;                  // [NP][TY][32]
+    float *gts = vb + NP * TY * 32;            // [TY][32 + D - 1] partial diagonal sums
     const int b = blockIdx.z;
     const int W = a.W, H = a.H, D = a.D;
     const size_t HW = (size_t)H * W;
-    const int X0 = blockIdx.x * 32 - RW, Y0 = blockIdx.y * 8 - RW;   // image coords of the tile origin
+    const int X0 = blockIdx.x * 32 - RW, Y0 = blockIdx.y * TY - RW;   // image coords of the tile origin
     float qmu[NS], qisa[NS], sAmb[NS], sB[NS], sBmu[NS];
     size_t vbase[NS], sbase[NS];       // cost / gc entry of (q, d = 0); statistics entry of (q, 0)
     int qofs[NS];                      // q's offset inside a staged plane
     bool qin[NS];
+    // The halo's pairs q are taken in 32-column slabs (a warp's lanes on one staged row of the
+    // first slab), then the 2 RW columns to its right.
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         const int j = threadIdx.x + 256 * s;
-        const int r = j / QW, c = j % QW;
+        int r, c;
+        if (j < QH * 32) {
+            r = j >> 5;
+            c = j & 31;
+        } else {
+            const int j2 = j - QH * 32;
+            r = RW > 0 ? j2 / (2 * RW) : 0;
+            c = RW > 0 ? 32 + j2 % (2 * RW) : 0;
+        }
         const int qy = Y0 - RW + r, qx = X0 - RW + c;
         qin[s] = j < NQ && qy >= 0 && qy < H && qx >= 0 && qx < W;
-        qofs[s] = r * SW + c;
+        qofs[s] = j < NQ ? r * SW + c : 0;
         const size_t qo = qin[s] ? (size_t)qy * W + qx : 0;
         vbase[s] = (size_t)b * D * HW + qo;
         sbase[s] = qin[s] ? ((size_t)b * H + qy) * a.We + qx + D - 1 : 0;
@@ -843,15 +856,22 @@ __global__ void __launch_bounds__(256, 3) k_dcost_bwd(const CbArgs a)
         sAmb[s] = sB[s] = sBmu[s] = 0.f;
     }
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int X = X0 + tx, Y = Y0 + ty;
-    const bool xin = X <= W - 1 + RW && Y <= H - 1 + RW;
-    const int yc = clampi(Y, 0, H - 1);
-    const float rv = a.ref[b * HW + (size_t)yc * W + clampi(X, 0, W - 1)];
-    const float *twrow = a.tw + b * HW + (size_t)yc * W;
+    const int X = X0 + tx;
+    float rv[RPT], gacc[RPT];
+    bool xin[RPT];
+    const float *twrow[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        const int Y = Y0 + ty + 8 * i;
+        xin[i] = X <= W - 1 + RW && Y <= H - 1 + RW;
+        const int yc = clampi(Y, 0, H - 1);
+        rv[i] = a.ref[b * HW + (size_t)yc * W + clampi(X, 0, W - 1)];
+        twrow[i] = a.tw + b * HW + (size_t)yc * W;
+        gacc[i] = 0.f;
+    }
     const int GW = cb_diag_w(D);
     if (a.gpart)
-        for (int i = threadIdx.x; i < 8 * GW; i += 256) gts[i] = 0.f;   // (the first round's barriers order these)
-    float gacc = 0.f;
+        for (int i = threadIdx.x; i < TY * GW; i += 256) gts[i] = 0.f;   // (the first round's barriers order these)
     // the loads of a round are issued one round ahead, so that they are in flight while the
     // previous round's box sums run
     float g[NS][DC], cc[NS][DC], sb[NS][DC], mb[NS][DC];
@@ -904,17 +924,17 @@ __global__ void __launch_bounds__(256, 3) k_dcost_bwd(const CbArgs a)
             row_box16<WN>(st + p * SP + row * SW + 16 * half, hb + p * HP + row * HW_ + 16 * half);
         }
         __syncthreads();
-        // ---- box sums along columns: one running sum per (plane, column) over the 8 tile rows
+        // ---- box sums along columns: one running sum per (plane, column) over the TY tile rows
         for (int t = threadIdx.x; t < NP * 32; t += 256) {
             const int p = t >> 5, xc = t & 31;
             const float *col = hb + p * HP + xc;
-            float *out = vb + p * 256 + xc;
+            float *out = vb + p * TY * 32 + xc;
             float s = 0.f;
 #pragma unroll
             for (int i = 0; i < WN; ++i) s += col[i * HW_];
             out[0] = s;
 #pragma unroll
-            for (int y = 1; y < 8; ++y) {
+            for (int y = 1; y < TY; ++y) {
                 s += col[(y + WN - 1) * HW_] - col[(y - 1) * HW_];
                 out[y * 32] = s;
             }
@@ -923,12 +943,16 @@ __global__ void __launch_bounds__(256, 3) k_dcost_bwd(const CbArgs a)
 #pragma unroll
         for (int k = 0; k < DC; ++k) {
             const int d = d0 + k;
-            const float bA = vb[(0 * DC + k) * 256 + ty * 32 + tx], bAm = vb[(1 * DC + k) * 256 + ty * 32 + tx];
-            const float bC = vb[(2 * DC + k) * 256 + ty * 32 + tx], bCm = vb[(3 * DC + k) * 256 + ty * 32 + tx];
-            if (xin && d < D) {
-                const float t = twrow[clampi(X - d, 0, W - 1)];
-                if (a.gpart) gts[ty * GW + tx - d + D - 1] += fmaf(rv, bA, -bAm) + fmaf(t, bC, -bCm);
-                gacc = fmaf(t, bA, gacc);
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) {
+                const int o = (ty + 8 * i) * 32 + tx;
+                const float bA = vb[(0 * DC + k) * TY * 32 + o], bAm = vb[(1 * DC + k) * TY * 32 + o];
+                const float bC = vb[(2 * DC + k) * TY * 32 + o], bCm = vb[(3 * DC + k) * TY * 32 + o];
+                if (xin[i] && d < D) {
+                    const float t = twrow[i][clampi(X - d, 0, W - 1)];
+                    if (a.gpart) gts[(ty + 8 * i) * GW + tx - d + D - 1] += fmaf(rv[i], bA, -bAm) + fmaf(t, bC, -bCm);
+                    gacc[i] = fmaf(t, bA, gacc[i]);
+                }
             }
             __syncwarp();   // lane x at d + 1 meets the entry of lane x - 1 at d
         }
@@ -939,8 +963,8 @@ __global__ void __launch_bounds__(256, 3) k_dcost_bwd(const CbArgs a)
     if (a.gpart) {
         // this tile's partial diagonal sums, one row per tile row inside the extended grid
         const int nbx = cb_tiles_x(a.Wr);
-        for (int i = threadIdx.x; i < 8 * GW; i += 256) {
-            const int r = i / GW, j = i - r * GW, row = blockIdx.y * 8 + r;
+        for (int i = threadIdx.x; i < TY * GW; i += 256) {
+            const int r = i / GW, j = i - r * GW, row = blockIdx.y * TY + r;
             if (row < a.Hr) a.gpart[(((size_t)b * a.Hr + row) * nbx + blockIdx.x) * GW + j] = gts[i];
         }
     }
@@ -958,18 +982,23 @@ __global__ void __launch_bounds__(256, 3) k_dcost_bwd(const CbArgs a)
         row_box<WN>(st + p * SP + row * SW, hb + p * HP + row * HW_);
     }
     __syncthreads();
-    float bx[3];
 #pragma unroll
-    for (int qn = 0; qn < 3; ++qn) {
-        const float *col = hb + qn * HP + ty * HW_ + tx;
-        float sum = 0.f;
+    for (int i = 0; i < RPT; ++i) {
+        float bx[3];
 #pragma unroll
-        for (int i = 0; i < WN; ++i) sum += col[i * HW_];
-        bx[qn] = sum;
+        for (int qn = 0; qn < 3; ++qn) {
+            const float *col = hb + qn * HP + (ty + 8 * i) * HW_ + tx;
+            float sum = 0.f;
+#pragma unroll
+            for (int j = 0; j < WN; ++j) sum += col[j * HW_];
+            bx[qn] = sum;
+        }
+        const int Y = Y0 + ty + 8 * i;
+        if (xin[i])
+            a.grefx[((size_t)b * a.Hr + (Y + RW)) * a.Wr + (X + RW)] = gacc[i] - bx[0] + fmaf(rv[i], bx[1], -bx[2]);
     }
-    if (xin)
-        a.grefx[((size_t)b * a.Hr + (Y + RW)) * a.Wr + (X + RW)] = gacc - bx[0] + fmaf(rv, bx[1], -bx[2]);
 }
+
 
 // Target positions Xt in [-rw-(D-1), W-1+rw] (column c = Xt + rw + D - 1): the sum over d of
 // Gamma(Xt + d, d), as the partial sums of the cost adjoint's tiles whose columns reach it
@@ -1129,12 +1158,12 @@ cudaError_t launch_agg(const AggArgs &a, int rb, int B, cudaStream_t st)
 template <int RW>
 cudaError_t launch_cb_rw(const CbArgs &a, int B, cudaStream_t st)
 {
-    constexpr int QW = 32 + 2 * RW, QH = 8 + 2 * RW, NP = 4 * kCbDC;
-    const size_t smem = ((size_t)NP * ((QW | 1) * QH + 33 * QH + 8 * 32) + 8 * cb_diag_w(a.D)) * sizeof(float);
+    constexpr int QW = 32 + 2 * RW, QH = kCbTY + 2 * RW, NP = 4 * kCbDC;
+    const size_t smem = ((size_t)NP * ((QW | 1) * QH + 33 * QH + kCbTY * 32) + kCbTY * cb_diag_w(a.D)) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_dcost_bwd<RW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((a.Wr + 31) / 32, (a.Hr + 7) / 8, B);
+    dim3 grid((a.Wr + 31) / 32, (a.Hr + kCbTY - 1) / kCbTY, B);
     k_dcost_bwd<RW><<<grid, 256, smem, st>>>(a);
     return cudaGetLastError();
 }
