@@ -37,9 +37,11 @@
 namespace sgb {
 namespace {
 
-constexpr int kAggRows = 4;          // pixels per thread in k_dagg (a column segment)
 
 enum { AGG_FWD = 0, AGG_H = 1, AGG_GC = 2 };
+// pixels per thread in k_dagg (a column segment): the forward pass, with one accumulator set,
+// takes 8, so that each staged neighbour row serves twice the weights
+__host__ __device__ constexpr int agg_rows(int mode) { return mode == AGG_FWD ? 8 : 4; }
 
 // k_dagg tiles: the recomputing backward pass (AGG_H) double-buffers its disparity chunks on
 // 64 x 24 tiles of 12 warps (one block per SM); the other two stream each chunk into one
@@ -47,7 +49,10 @@ enum { AGG_FWD = 0, AGG_H = 1, AGG_GC = 2 };
 __host__ __device__ constexpr bool agg_dbuf(int mode) { return mode == AGG_H; }
 __host__ __device__ constexpr int agg_tx(int mode) { return agg_dbuf(mode) ? 64 : 32; }
 __host__ __device__ constexpr int agg_ty(int mode) { return agg_dbuf(mode) ? 24 : 32; }
-__host__ __device__ constexpr int agg_threads(int mode) { return agg_dbuf(mode) ? 384 : 256; }
+__host__ __device__ constexpr int agg_threads(int mode)
+{
+    return agg_dbuf(mode) ? 384 : 32 * (agg_tx(mode) / 32) * agg_ty(mode) / agg_rows(mode);
+}
 constexpr int kAggDC = 8;            // disparities per chunk in k_dagg
 constexpr int kCostDC = 16;          // disparities per block in k_dcost
 constexpr float kFar = 1e18f;        // scaled intensity of an out-of-image neighbour: weight 0
@@ -457,14 +462,15 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// One tile per block (agg_tx x agg_ty); thread (tx, ty) owns the pixels (x0 + tx, y0 + 4 ty + i),
-// i < 4, and kAggDC disparities at a time.  The weights of eq. (omega_s) are formed as
+// One tile per block (agg_tx x agg_ty); thread (tx, ty) owns the pixels (x0 + tx, y0 + R ty + i),
+// i < R = agg_rows(MODE), and kAggDC disparities at a time.  The weights of eq. (omega_s) are formed as
 // exp2(kx + ky - (sI_p - sI_q)^2) with sI = kappa I; an out-of-image neighbour has
 // sI = kFar and a zero value, so its weight and every product with it are exactly 0.
 template <int MODE, int RB>
 __global__ void __launch_bounds__(agg_threads(MODE), MODE == AGG_FWD ? 3 : MODE == AGG_GC ? 2 : 1) k_dagg(const AggArgs a)
 {
-    constexpr int DC = kAggDC, NQ = DC / 4, NR = kAggRows + 2 * RB;
+    constexpr int ROWS = agg_rows(MODE);
+    constexpr int DC = kAggDC, NQ = DC / 4, NR = ROWS + 2 * RB;
     constexpr bool DB = agg_dbuf(MODE);
     constexpr int kAggTX = agg_tx(MODE), kAggTY = agg_ty(MODE), kAggThreads = agg_threads(MODE);
     constexpr int TW = kAggTX + 2 * RB, TH = kAggTY + 2 * RB;
@@ -530,19 +536,19 @@ __global__ void __launch_bounds__(agg_threads(MODE), MODE == AGG_FWD ? 3 : MODE 
     __syncthreads();
 
     const int px = x0 + tx;
-    float sIp[kAggRows];
-    int py[kAggRows];
-    bool pin[kAggRows];
+    float sIp[ROWS];
+    int py[ROWS];
+    bool pin[ROWS];
 #pragma unroll
-    for (int i = 0; i < kAggRows; ++i) {
-        py[i] = y0 + kAggRows * ty + i;
+    for (int i = 0; i < ROWS; ++i) {
+        py[i] = y0 + ROWS * ty + i;
         pin[i] = px < W && py[i] < H;
-        sIp[i] = sI[(kAggRows * ty + i + RB) * TW + tx + RB];
+        sIp[i] = sI[(ROWS * ty + i + RB) * TW + tx + RB];
     }
     // per-pixel state across chunks
-    float st0[kAggRows], st1[kAggRows], st2[kAggRows], st3[kAggRows];
+    float st0[ROWS], st1[ROWS], st2[ROWS], st3[ROWS];
 #pragma unroll
-    for (int i = 0; i < kAggRows; ++i) {
+    for (int i = 0; i < ROWS; ++i) {
         st0[i] = st1[i] = st2[i] = st3[i] = 0.f;
         if constexpr (MODE == AGG_FWD) st0[i] = -INFINITY;   // running max of -E kT
         if (MODE == AGG_H && pin[i]) {
@@ -552,14 +558,14 @@ __global__ void __launch_bounds__(agg_threads(MODE), MODE == AGG_FWD ? 3 : MODE 
             st2[i] = a.lbar[o];                              // soft-argmin without the shift
         }
     }
-    float S[kAggRows];          // sum_q w (sI_q - sI_p), the same in every chunk
-    float Z[kAggRows];          // sum_q w, the same in every chunk
-    float invZ[kAggRows];
+    float S[ROWS];          // sum_q w (sI_q - sI_p), the same in every chunk
+    float Z[ROWS];          // sum_q w, the same in every chunk
+    float invZ[ROWS];
     // Z and S depend on no disparity: the first chunk sums them (the same terms in the same
     // order as any chunk would) and later chunks reuse them
-    float beta[kAggRows], tacc[kAggRows];
+    float beta[ROWS], tacc[ROWS];
 #pragma unroll
-    for (int i = 0; i < kAggRows; ++i) S[i] = beta[i] = tacc[i] = 0.f;
+    for (int i = 0; i < ROWS; ++i) S[i] = beta[i] = tacc[i] = 0.f;
 
     for (int d0 = 0, kc = 0; d0 < D; d0 += DC, ++kc) {
         const float4 *V = Vbuf + (DB ? (kc & 1) * NQ * TH * TW : 0);
@@ -577,9 +583,9 @@ __global__ void __launch_bounds__(agg_threads(MODE), MODE == AGG_FWD ? 3 : MODE 
         __syncthreads();
 
         // accumulators in pairs of disparities (packed f32x2 FMAs)
-        float2 acc0[kAggRows][DC / 2], acc1[kAggRows][TWO ? DC / 2 : 1];
+        float2 acc0[ROWS][DC / 2], acc1[ROWS][TWO ? DC / 2 : 1];
 #pragma unroll
-        for (int i = 0; i < kAggRows; ++i) {
+        for (int i = 0; i < ROWS; ++i) {
             if (kc == 0) {
                 Z[i] = 0.f;
                 if constexpr (TWO) S[i] = 0.f;
@@ -598,13 +604,13 @@ __global__ void __launch_bounds__(agg_threads(MODE), MODE == AGG_FWD ? 3 : MODE 
                 const int col = tx + RB + dx;
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
-                    const int srow = kAggRows * ty + r;
+                    const int srow = ROWS * ty + r;
                     const float sq = sI[srow * TW + col];
                     float4 v4[NQ];
 #pragma unroll
                     for (int q = 0; q < NQ; ++q) v4[q] = V[(q * TH + srow) * TW + col];
 #pragma unroll
-                    for (int i = 0; i < kAggRows; ++i) {
+                    for (int i = 0; i < ROWS; ++i) {
                         const int dy = r - RB - i;
                         if (dy < -RB || dy > RB) continue;
                         const float dd = sIp[i] - sq;
@@ -635,14 +641,14 @@ __global__ void __launch_bounds__(agg_threads(MODE), MODE == AGG_FWD ? 3 : MODE 
         } else if (kc == 0) {
             accumulate(std::true_type());
 #pragma unroll
-            for (int i = 0; i < kAggRows; ++i) invZ[i] = 1.f / Z[i];
+            for (int i = 0; i < ROWS; ++i) invZ[i] = 1.f / Z[i];
         } else {
             accumulate(std::false_type());
         }
 
         // chunk epilogue
 #pragma unroll
-        for (int i = 0; i < kAggRows; ++i) {
+        for (int i = 0; i < ROWS; ++i) {
             if (!pin[i]) continue;
             const size_t pix = (size_t)py[i] * W + px;
             if constexpr (MODE == AGG_FWD) {
@@ -683,7 +689,7 @@ __global__ void __launch_bounds__(agg_threads(MODE), MODE == AGG_FWD ? 3 : MODE 
                     if (d >= D) break;
                     const size_t o = ((size_t)b * D + d) * HW + pix;
                     a.gc[o] = lane(acc0[i][k >> 1], k);
-                    const float cx = scst[(k * kAggTY + kAggRows * ty + i) * kAggTX + tx];
+                    const float cx = scst[(k * kAggTY + ROWS * ty + i) * kAggTX + tx];
                     tacc[i] = fmaf(cx, lane(acc1[i][k >> 1], k), tacc[i]);
                 }
             }
@@ -693,7 +699,7 @@ __global__ void __launch_bounds__(agg_threads(MODE), MODE == AGG_FWD ? 3 : MODE 
 
     if constexpr (MODE == AGG_FWD) {
 #pragma unroll
-        for (int i = 0; i < kAggRows; ++i) {
+        for (int i = 0; i < ROWS; ++i) {
             if (!pin[i]) continue;
             const size_t o = b * HW + (size_t)py[i] * W + px;
             const float lbar = st2[i] / st1[i];
@@ -706,7 +712,7 @@ __global__ void __launch_bounds__(agg_threads(MODE), MODE == AGG_FWD ? 3 : MODE 
     }
     if constexpr (MODE == AGG_H) {
 #pragma unroll
-        for (int i = 0; i < kAggRows; ++i) {
+        for (int i = 0; i < ROWS; ++i) {
             if (!pin[i]) continue;
             const size_t o = b * HW + (size_t)py[i] * W + px;
             a.beta[o] = beta[i];
@@ -725,19 +731,19 @@ __global__ void __launch_bounds__(agg_threads(MODE), MODE == AGG_FWD ? 3 : MODE 
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    float sbeta[kAggRows];
+    float sbeta[ROWS];
 #pragma unroll
-    for (int i = 0; i < kAggRows; ++i) sbeta[i] = 0.f;
+    for (int i = 0; i < ROWS; ++i) sbeta[i] = 0.f;
 #pragma unroll 1
     for (int dx = -RB; dx <= RB; ++dx) {
         const float kx = a.k0 * (float)(dx * dx);
         const int col = tx + RB + dx;
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
-            const int srow = kAggRows * ty + r;
+            const int srow = ROWS * ty + r;
             const float sq = sI[srow * TW + col], bq = sb[srow * TW + col];
 #pragma unroll
-            for (int i = 0; i < kAggRows; ++i) {
+            for (int i = 0; i < ROWS; ++i) {
                 const int dy = r - RB - i;
                 if (dy < -RB || dy > RB) continue;
                 const float dd = sIp[i] - sq;
@@ -746,11 +752,11 @@ __global__ void __launch_bounds__(agg_threads(MODE), MODE == AGG_FWD ? 3 : MODE 
             }
         }
     }
-    float t1v[kAggRows];   // (all loads before the first store)
+    float t1v[ROWS];   // (all loads before the first store)
 #pragma unroll
-    for (int i = 0; i < kAggRows; ++i) t1v[i] = pin[i] ? a.t1[b * HW + (size_t)py[i] * W + px] : 0.f;
+    for (int i = 0; i < ROWS; ++i) t1v[i] = pin[i] ? a.t1[b * HW + (size_t)py[i] * W + px] : 0.f;
 #pragma unroll
-    for (int i = 0; i < kAggRows; ++i) {
+    for (int i = 0; i < ROWS; ++i) {
         if (!pin[i]) continue;
         const size_t o = b * HW + (size_t)py[i] * W + px;
         a.gw[o] = a.gw_scale * (t1v[i] + tacc[i] - sbeta[i]);
