@@ -96,7 +96,7 @@ struct Dims {
 };
 
 struct Ws {
-    float *tw, *mur, *sdr, *mut, *sdt, *isdt, *cost, *lse, *lbar;      // forward (isdt: 1 / sdt, 0 where flat)
+    float *tw, *mur, *sdr, *mut, *isdt, *cost, *lse, *lbar;      // forward (isdt: 1 / s_b, 0 where flat)
     float *h, *gc, *beta, *t1, *gw, *gpart, *grefx, *gtwx;      // backward
 };
 
@@ -114,7 +114,6 @@ size_t layout(const Dims &d, char *base, Ws *w)
     take(&o->mur, B * img);
     take(&o->sdr, B * img);
     take(&o->mut, B * (size_t)d.H * d.We);
-    take(&o->sdt, B * (size_t)d.H * d.We);
     take(&o->isdt, B * (size_t)d.H * d.We);
     take(&o->cost, B * vol);
     take(&o->lse, B * img);
@@ -211,7 +210,8 @@ __global__ void __launch_bounds__(256) k_dwarp(const float *__restrict__ tgt, co
 }
 
 // Window mean and population standard deviation over (2rw+1)^2 clamp-to-edge reads, on an
-// output grid of Wout columns whose column xo is centred on image column xo + off.
+// output grid of Wout columns whose column xo is centred on image column xo + off (sd and its
+// reciprocal isd are each written when their pointer is not null).
 __global__ void __launch_bounds__(256) k_dstats(const float *__restrict__ img, int W, int H, int Wout, int off,
                                                 int rw, float *__restrict__ mu, float *__restrict__ sd,
                                                 float *__restrict__ isd)
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(256) k_dstats(const float *__restrict__ img, i
     const size_t o = ((size_t)b * H + v) * Wout + xo;
     mu[o] = c0 + m;
     const float sv = sqrtf(q / n);
-    sd[o] = sv;
+    if (sd) sd[o] = sv;
     if (isd) isd[o] = sv > 0.f ? __frcp_rn(sv) : 0.f;   // the cost adjoint's 1 / s_b, once per position
 }
 
@@ -284,7 +284,7 @@ __host__ __device__ constexpr size_t dcost_smem(int rw)
 template <int RW>
 __global__ void __launch_bounds__(kCostThreads, 3) k_dcost(const float *__restrict__ ref, const float *__restrict__ tw,
                                                   const float *__restrict__ mur, const float *__restrict__ sdr,
-                                                  const float *__restrict__ mut, const float *__restrict__ sdt,
+                                                  const float *__restrict__ mut, const float *__restrict__ isdt,
                                                   float *__restrict__ cost, int W, int H, int D, int nchunk)
 {
     constexpr int DC = kCostDC, rw = RW, w = 2 * RW + 1;
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(kCostThreads, 3) k_dcost(const float *__restri
             const int v = y0 + r, xe = sc0 + c;
             const bool ok = i < kCostTY * kCostSW && v < H && xe >= 0 && xe < We;
             const size_t so = ((size_t)b * H + (ok ? v : 0)) * We + (ok ? xe : 0);
-            vs[it] = ok ? make_float2(mut[so], sdt[so]) : make_float2(0.f, 0.f);
+            vs[it] = ok ? make_float2(mut[so], isdt[so]) : make_float2(0.f, 0.f);   // (mu_b, 1 / s_b)
         }
 #pragma unroll
         for (int it = 0; it < NPR; ++it) {
@@ -411,15 +411,16 @@ __global__ void __launch_bounds__(kCostThreads, 3) k_dcost(const float *__restri
             if (!inside(h, j)) continue;
             const int u = u0 + 32 * j, v = v0 + h;
             const float sav = sdr[b * HW + (size_t)v * W + u], as = j ? asum[h].y : asum[h].x;
+            const float ia = sav > 0.f ? 1.f / (n * sav) : 0.f;   // 1 / (n s_a), once per pixel
 #pragma unroll
             for (int k = 0; k < DC; ++k) {
                 const int d = d0 + k;
                 if (d >= D) break;
                 const int e = (2 * ty + h) * kCostSW + tx + 32 * j - k + DC - 1;
-                const float mb = smb[e], sb = ssb[e];
+                const float mb = smb[e], isb = ssb[e];
                 const float ak = j ? acc[h][k].y : acc[h][k].x;
                 float c = 1.f;
-                if (sav > 0.f && sb > 0.f) c = 1.f - fmaf(-mb, as, ak) / (n * sav * sb);
+                if (ia > 0.f && isb > 0.f) c = 1.f - fmaf(-mb, as, ak) * ia * isb;
                 cost[((size_t)b * D + d) * HW + (size_t)v * W + u] = c;
             }
         }
@@ -881,7 +882,18 @@ __global__ void __launch_bounds__(256, 2) k_dcost_bwd(const CbArgs a)
     // the loads of a round are issued one round ahead, so that they are in flight while the
     // previous round's box sums run
     float g[NS][DC], cc[NS][DC], sb[NS][DC], mb[NS][DC];
+    // the target values t(X - d) of the tile rows, loaded a round ahead too (but for the widest
+    // window, whose registers they would spill)
+    constexpr bool TPF = RW < 7;
+    float tn[RPT][DC];
     auto load_round = [&](int d0) {
+        if constexpr (TPF) {
+#pragma unroll
+            for (int i = 0; i < RPT; ++i)
+#pragma unroll
+                for (int k = 0; k < DC; ++k)
+                    tn[i][k] = (xin[i] && d0 + k < D) ? twrow[i][clampi(X - d0 - k, 0, W - 1)] : 0.f;
+        }
 #pragma unroll
         for (int s = 0; s < NS; ++s)
 #pragma unroll
@@ -920,6 +932,13 @@ __global__ void __launch_bounds__(256, 2) k_dcost_bwd(const CbArgs a)
                 st[(3 * DC + k) * SP + qofs[s]] = C * mb[s][k];
             }
         }
+        float tc[RPT][DC];
+        if constexpr (TPF) {
+#pragma unroll
+            for (int i = 0; i < RPT; ++i)
+#pragma unroll
+                for (int k = 0; k < DC; ++k) tc[i][k] = tn[i][k];
+        }
         if (d0 + DC < D) load_round(d0 + DC);
         __syncthreads();
         // ---- box sums along rows: one running sum per (plane, halo row, half row); with the
@@ -955,7 +974,7 @@ __global__ void __launch_bounds__(256, 2) k_dcost_bwd(const CbArgs a)
                 const float bA = vb[(0 * DC + k) * TY * 32 + o], bAm = vb[(1 * DC + k) * TY * 32 + o];
                 const float bC = vb[(2 * DC + k) * TY * 32 + o], bCm = vb[(3 * DC + k) * TY * 32 + o];
                 if (xin[i] && d < D) {
-                    const float t = twrow[i][clampi(X - d, 0, W - 1)];
+                    const float t = TPF ? tc[i][k] : twrow[i][clampi(X - d, 0, W - 1)];
                     if (a.gpart) gts[(ty + 8 * i) * GW + tx - d + D - 1] += fmaf(rv[i], bA, -bAm) + fmaf(t, bC, -bCm);
                     gacc[i] = fmaf(t, bA, gacc[i]);
                 }
@@ -1253,13 +1272,13 @@ extern "C" int stereo_softargmin_fwd(const stereo_diff_params *p, const float *r
     k_dstats<<<dim3((d.W + 31) / 32, (d.H + 7) / 8, B), 256, ssm, st>>>(ref, d.W, d.H, d.W, 0, d.rw, w.mur,
                                                                         w.sdr, nullptr);
     k_dstats<<<dim3((d.We + 31) / 32, (d.H + 7) / 8, B), 256, ssm, st>>>(w.tw, d.W, d.H, d.We, -(d.D - 1),
-                                                                         d.rw, w.mut, w.sdt, w.isdt);
+                                                                         d.rw, w.mut, nullptr, w.isdt);
     const int nchunk = (d.D + kCostDC - 1) / kCostDC;
     const size_t csm = dcost_smem(d.rw);
     {
         const dim3 grid((d.W + kCostTX - 1) / kCostTX, (d.H + kCostTY - 1) / kCostTY, B * nchunk);
 #define SGB_DCOST(R)                                                                                  \
-    k_dcost<R><<<grid, kCostThreads, csm, st>>>(ref, w.tw, w.mur, w.sdr, w.mut, w.sdt, w.cost, d.W, d.H, d.D, nchunk)
+    k_dcost<R><<<grid, kCostThreads, csm, st>>>(ref, w.tw, w.mur, w.sdr, w.mut, w.isdt, w.cost, d.W, d.H, d.D, nchunk)
         switch (d.rw) {
         case 0: SGB_DCOST(0); break;
         case 1: SGB_DCOST(1); break;
