@@ -212,17 +212,18 @@ __global__ void __launch_bounds__(256) k_dwarp(const float *__restrict__ tgt, co
 // Window mean and population standard deviation over (2rw+1)^2 clamp-to-edge reads, on an
 // output grid of Wout columns whose column xo is centred on image column xo + off (sd and its
 // reciprocal isd are each written when their pointer is not null).
+template <int RW>
 __global__ void __launch_bounds__(256) k_dstats(const float *__restrict__ img, int W, int H, int Wout, int off,
-                                                int rw, float *__restrict__ mu, float *__restrict__ sd,
+                                                float *__restrict__ mu, float *__restrict__ sd,
                                                 float *__restrict__ isd)
 {
     extern __shared__ float s[];
-    const int sw = 32 + 2 * rw, sh = 8 + 2 * rw;
+    constexpr int rw = RW, sw = 32 + 2 * RW, sh = 8 + 2 * RW, w = 2 * RW + 1;
     const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8, b = blockIdx.z;
     const float *im = img + (size_t)b * H * W;
     {
-        // at most (32 + 14) x (8 + 14) entries: every load of a thread before its first store
-        constexpr int NI = (46 * 22 + 255) / 256;
+        // every load of a thread before its first store
+        constexpr int NI = (sw * sh + 255) / 256;
         float vi[NI];
 #pragma unroll
         for (int it = 0; it < NI; ++it) {
@@ -240,18 +241,22 @@ __global__ void __launch_bounds__(256) k_dstats(const float *__restrict__ img, i
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int xo = x0 + tx, v = y0 + ty;
     if (xo >= Wout || v >= H) return;
-    const int w = 2 * rw + 1;
     const float n = (float)(w * w);
     // relative to the centre value: a block whose values are all equal gets sd = 0 exactly
-    const float c0 = s[(ty + rw) * sw + tx + rw];
+    const float *blk = s + ty * sw + tx;
+    const float c0 = blk[rw * sw + rw];
     float sum = 0.f;
+#pragma unroll 1
     for (int dy = 0; dy < w; ++dy)
-        for (int dx = 0; dx < w; ++dx) sum += s[(ty + dy) * sw + tx + dx] - c0;
+#pragma unroll
+        for (int dx = 0; dx < w; ++dx) sum += blk[dy * sw + dx] - c0;
     const float m = sum / n;
     float q = 0.f;
+#pragma unroll 1
     for (int dy = 0; dy < w; ++dy)
+#pragma unroll
         for (int dx = 0; dx < w; ++dx) {
-            const float a = (s[(ty + dy) * sw + tx + dx] - c0) - m;
+            const float a = (blk[dy * sw + dx] - c0) - m;
             q = fmaf(a, a, q);
         }
     const size_t o = ((size_t)b * H + v) * Wout + xo;
@@ -259,6 +264,18 @@ __global__ void __launch_bounds__(256) k_dstats(const float *__restrict__ img, i
     const float sv = sqrtf(q / n);
     if (sd) sd[o] = sv;
     if (isd) isd[o] = sv > 0.f ? __frcp_rn(sv) : 0.f;   // the cost adjoint's 1 / s_b, once per position
+}
+
+void launch_dstats(int rw, dim3 grid, size_t smem, cudaStream_t st, const float *img, int W, int H, int Wout, int off,
+                   float *mu, float *sd, float *isd)
+{
+    switch (rw) {
+#define SGB_DSTATS(R)                                                                  \
+    case R: k_dstats<R><<<grid, 256, smem, st>>>(img, W, H, Wout, off, mu, sd, isd); break;
+    SGB_DSTATS(0) SGB_DSTATS(1) SGB_DSTATS(2) SGB_DSTATS(3) SGB_DSTATS(4) SGB_DSTATS(5) SGB_DSTATS(6)
+    default: k_dstats<7><<<grid, 256, smem, st>>>(img, W, H, Wout, off, mu, sd, isd); break;
+#undef SGB_DSTATS
+    }
 }
 
 // eq. (c) for a 64 x 8 pixel tile and kCostDC disparities: the centred reference window
@@ -1269,10 +1286,10 @@ extern "C" int stereo_softargmin_fwd(const stereo_diff_params *p, const float *r
     const int B = d.B;
     k_dwarp<<<dim3((d.W + 255) / 256, d.H, B), 256, 0, st>>>(tgt, shift, w.tw, d.W, d.H, d.warp_mode);
     const size_t ssm = (size_t)(32 + 2 * d.rw) * (8 + 2 * d.rw) * sizeof(float);
-    k_dstats<<<dim3((d.W + 31) / 32, (d.H + 7) / 8, B), 256, ssm, st>>>(ref, d.W, d.H, d.W, 0, d.rw, w.mur,
-                                                                        w.sdr, nullptr);
-    k_dstats<<<dim3((d.We + 31) / 32, (d.H + 7) / 8, B), 256, ssm, st>>>(w.tw, d.W, d.H, d.We, -(d.D - 1),
-                                                                         d.rw, w.mut, nullptr, w.isdt);
+    launch_dstats(d.rw, dim3((d.W + 31) / 32, (d.H + 7) / 8, B), ssm, st, ref, d.W, d.H, d.W, 0, w.mur, w.sdr,
+                  nullptr);
+    launch_dstats(d.rw, dim3((d.We + 31) / 32, (d.H + 7) / 8, B), ssm, st, w.tw, d.W, d.H, d.We, -(d.D - 1), w.mut,
+                  nullptr, w.isdt);
     const int nchunk = (d.D + kCostDC - 1) / kCostDC;
     const size_t csm = dcost_smem(d.rw);
     {
